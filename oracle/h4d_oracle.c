@@ -1,0 +1,718 @@
+/*
+ * h4d_oracle.c -- FP64 CPU oracle of the H4D grand-canonical method (arXiv:2307.11447).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the CPU-baseline leg
+ * of the benchmark, never by the CUDA library.  Everything is double precision, written
+ * for a reader checking it against the paper:
+ *   Sec. II.A   constant-velocity altitude protocol (Eq. 2), NVE time evolution,
+ *               symmetric two-end momentum reversal, pair-exchange Metropolis rule
+ *               (Eqs. 3-8).
+ *   Sec. II.B.1 flying ions keep their 3D positions during NEMD.
+ *   Sec. II.B.2 short-range 4D Coulomb with altitude screening (Eqs. 9-11).
+ *   Sec. II.D   truncated-shifted LJ (Eq. 19), Coulomb (Eq. 20), Lorentz-Berthelot,
+ *               rigid water.
+ *   SI Sec. S5  altitude schedules w_v and w_x (Eqs. S6-S7).
+ * Readings of points the paper leaves open (which energies Delta H compares, flyer momenta,
+ * step ordering, reversal details, move choice, Coulomb shift, thermostat) are stated
+ * at the code that takes them.
+ *
+ * Parity status: pinned by the not-gpu tests (closed forms, brute force, finite
+ * differences, 3D recovery, NVE drift, exact reversibility, ideal-gas laws).
+ */
+#include "h4d_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------------------ */
+/* Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of a multiply-xor      */
+/* bijection keyed by a Weyl sequence.                                                   */
+/* ------------------------------------------------------------------------------------ */
+static void mulhilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
+  __uint128_t prod = (__uint128_t)a * (__uint128_t)b;
+  *hi = (uint64_t)(prod >> 64);
+  *lo = (uint64_t)prod;
+}
+
+void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+  uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint64_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    uint64_t hi0, lo0, hi1, lo1;
+    mulhilo64(0xD2E7470EE14C6C93ULL, c0, &hi0, &lo0);
+    mulhilo64(0xCA5A826395121157ULL, c2, &hi1, &lo1);
+    uint64_t n0 = hi1 ^ c1 ^ k0;
+    uint64_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B97F4A7C15ULL;
+    k1 += 0xBB67AE8584CAA73BULL;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static void draw(const orc_params* p, uint64_t c0, uint64_t c1, uint64_t purpose, uint64_t out[4]) {
+  uint64_t ctr[4] = {c0, c1, purpose, 0};
+  uint64_t key[2] = {p->seed, p->replica};
+  orc_philox4x64_10(ctr, key, out);
+}
+
+/* uniform in [0,1) and in (0,1] from the top 53 bits */
+static double u01(uint64_t r) { return (double)(r >> 11) * 0x1.0p-53; }
+static double u01_open(uint64_t r) { return (double)((r >> 11) + 1) * 0x1.0p-53; }
+/* uniform integer in [0, n) from the top 32 bits (multiply-shift) */
+static int32_t pick(uint64_t r, int32_t n) {
+  return (int32_t)(((r >> 32) * (uint64_t)n) >> 32);
+}
+/* standard normal, Box-Muller cosine branch */
+static double gauss_cos(uint64_t ra, uint64_t rb) {
+  return sqrt(-2.0 * log(u01_open(ra))) * cos(2.0 * M_PI * u01(rb));
+}
+static double gauss_sin(uint64_t ra, uint64_t rb) {
+  return sqrt(-2.0 * log(u01_open(ra))) * sin(2.0 * M_PI * u01(rb));
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* System layout                                                                         */
+/* ------------------------------------------------------------------------------------ */
+int orc_atom_type(const orc_params* p, int a) {
+  int nsolv = 3 * p->n_water;
+  if (a < nsolv) return (a % 3 == 0) ? 2 : 3;
+  return (a - nsolv) & 1;
+}
+
+static int excluded(const orc_params* p, int i, int j) {
+  int nsolv = 3 * p->n_water;
+  return i < nsolv && j < nsolv && (i / 3) == (j / 3);
+}
+
+static double mass_of(const orc_params* p, int a) { return p->mass[orc_atom_type(p, a)]; }
+
+static double minimg(double d, double L) { return d - L * nearbyint(d / L); }
+
+static double wrap(double x, double L) {
+  double y = x - L * floor(x / L);
+  if (y >= L) y -= L; /* guards x/L rounding up to the next integer */
+  return y;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Pair potential                                                                        */
+/* ------------------------------------------------------------------------------------ */
+/* LJ truncated and shifted at rc_lj (Eq. 19) with Lorentz-Berthelot mixing (Sec. II.D.2);
+ * Coulomb short-range part K q_i q_j erfc(alpha r)/r (Eqs. 9, 20), shifted to zero at
+ * rc_coul (reading: energy shifted like the LJ, force unshifted), multiplied by the
+ * altitude screening g (Eq. 11).  r is the 4D distance of Sec. II.A. */
+void orc_pair(const orc_params* p, int ti, int tj, double r, double g, double* u, double* dudr) {
+  double uu = 0.0, du = 0.0;
+  double sig = 0.5 * (p->sig[ti] + p->sig[tj]);
+  double eps = sqrt(p->eps[ti] * p->eps[tj]);
+  if (eps > 0.0 && r < p->rc_lj) {
+    double sr6 = pow(sig / r, 6.0);
+    double sc6 = pow(sig / p->rc_lj, 6.0);
+    uu += 4.0 * eps * (sr6 * sr6 - sr6) - 4.0 * eps * (sc6 * sc6 - sc6);
+    du += 4.0 * eps * (-12.0 * sr6 * sr6 + 6.0 * sr6) / r;
+  }
+  double qq = p->q[ti] * p->q[tj];
+  if (qq != 0.0 && r < p->rc_coul) {
+    double a = p->alpha;
+    double kq = p->kcoul * qq * g;
+    uu += kq * (erfc(a * r) / r - erfc(a * p->rc_coul) / p->rc_coul);
+    du += kq * (-erfc(a * r) / (r * r) - 2.0 * a / sqrt(M_PI) * exp(-a * a * r * r) / r);
+  }
+  *u = uu;
+  *dudr = du;
+}
+
+/* mean altitude of the flyers (Sec. II.B.2: the screening uses the average altitude) */
+static double mean_flyer_w(int n, const double* w, const uint8_t* fly) {
+  if (!w || !fly) return 0.0;
+  double s = 0.0;
+  int m = 0;
+  for (int i = 0; i < n; ++i)
+    if (fly[i] == 1) { s += w[i]; ++m; }
+  return m ? s / m : 0.0;
+}
+
+/* screening of Eq. 11: f_ij = 1 only when exactly one of i, j flies; other pairs keep
+ * their unscreened interaction (reading of the f_ij definition) */
+static double screen(const orc_params* p, const uint8_t* fly, int i, int j, double wbar) {
+  if (!fly) return 1.0;
+  int fi = fly[i] == 1, fj = fly[j] == 1;
+  return (fi != fj) ? exp(-p->kappa_sr * wbar) : 1.0;
+}
+
+/* one pair: accumulate energy and forces; absent atoms (fly == 2) are skipped */
+static double pair_term(const orc_params* p, const double* x, const double* w, const uint8_t* fly,
+                        double wbar, int i, int j, double* F) {
+  if (fly && (fly[i] == 2 || fly[j] == 2)) return 0.0;
+  if (excluded(p, i, j)) return 0.0;
+  double d[3];
+  double r2 = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    d[c] = minimg(x[3 * j + c] - x[3 * i + c], p->L);
+    r2 += d[c] * d[c];
+  }
+  double dw = w ? (w[i] - w[j]) : 0.0;
+  double r4 = sqrt(r2 + dw * dw);
+  double rmax = p->rc_lj > p->rc_coul ? p->rc_lj : p->rc_coul;
+  if (r4 >= rmax) return 0.0;
+  double u, dudr;
+  orc_pair(p, orc_atom_type(p, i), orc_atom_type(p, j), r4, screen(p, fly, i, j, wbar), &u, &dudr);
+  if (F) {
+    /* F_i = -du/dx_i = u'(r4) (x_j - x_i)/r4 ; F_j = -F_i (3D components only) */
+    for (int c = 0; c < 3; ++c) {
+      double f = dudr * d[c] / r4;
+      F[3 * i + c] += f;
+      F[3 * j + c] -= f;
+    }
+  }
+  return u;
+}
+
+static double energy_brute(const orc_params* p, int n, const double* x, const double* w,
+                           const uint8_t* fly, double* F) {
+  double wbar = mean_flyer_w(n, w, fly);
+  double U = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) U += pair_term(p, x, w, fly, wbar, i, j, F);
+  return U;
+}
+
+/* plain cell list with cells no smaller than the largest cut-off; a 3D criterion is a
+ * valid superset in 4D because r4 >= r */
+static double energy_cells(const orc_params* p, int n, const double* x, const double* w,
+                           const uint8_t* fly, double* F) {
+  double rmax = p->rc_lj > p->rc_coul ? p->rc_lj : p->rc_coul;
+  int nc = (int)floor(p->L / rmax);
+  if (nc < 3) return energy_brute(p, n, x, w, fly, F);
+  double wbar = mean_flyer_w(n, w, fly);
+  int ncell = nc * nc * nc;
+  int* head = (int*)malloc(sizeof(int) * ncell);
+  int* next = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+  for (int c = 0; c < ncell; ++c) head[c] = -1;
+  for (int i = n - 1; i >= 0; --i) {
+    int cx = (int)(x[3 * i + 0] / p->L * nc) % nc;
+    int cy = (int)(x[3 * i + 1] / p->L * nc) % nc;
+    int cz = (int)(x[3 * i + 2] / p->L * nc) % nc;
+    int c = (cx * nc + cy) * nc + cz;
+    next[i] = head[c];
+    head[c] = i;
+  }
+  double U = 0.0;
+  for (int cx = 0; cx < nc; ++cx)
+    for (int cy = 0; cy < nc; ++cy)
+      for (int cz = 0; cz < nc; ++cz) {
+        int c = (cx * nc + cy) * nc + cz;
+        for (int dx = -1; dx <= 1; ++dx)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dz = -1; dz <= 1; ++dz) {
+              int ex = (cx + dx + nc) % nc, ey = (cy + dy + nc) % nc, ez = (cz + dz + nc) % nc;
+              int e = (ex * nc + ey) * nc + ez;
+              for (int i = head[c]; i >= 0; i = next[i])
+                for (int j = head[e]; j >= 0; j = next[j])
+                  if (i < j) U += pair_term(p, x, w, fly, wbar, i, j, F);
+            }
+      }
+  free(head);
+  free(next);
+  return U;
+}
+
+double orc_energy_forces(const orc_params* p, int n, const double* x, const double* w,
+                         const uint8_t* fly, double* F) {
+  if (F) memset(F, 0, sizeof(double) * 3 * (size_t)n);
+  return p->use_cells ? energy_cells(p, n, x, w, fly, F) : energy_brute(p, n, x, w, fly, F);
+}
+
+/* energy of the pairs that involve at least one flyer, the flyers at altitude wf */
+static double flyer_energy(const orc_params* p, int n, const double* x, const uint8_t* fly, double wf,
+                           double* wbuf) {
+  for (int i = 0; i < n; ++i) wbuf[i] = (fly[i] == 1) ? wf : 0.0;
+  double wbar = wf;
+  double U = 0.0;
+  for (int i = 0; i < n; ++i) {
+    if (fly[i] != 1) continue;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      if (fly[j] == 1 && j < i) continue; /* flyer-flyer pair counted once */
+      U += pair_term(p, x, wbuf, fly, wbar, i, j, NULL);
+    }
+  }
+  return U;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Fixed-point neighbour criterion (definition shared by name with the GPU path):        */
+/* X = floor(x/L * 2^32) mod 2^32 per coordinate; (i,j) is a list pair iff              */
+/* sum_c ((int32)(X_i - X_j))^2 <= floor((r_list/L * 2^32)^2).                           */
+/* ------------------------------------------------------------------------------------ */
+static uint32_t fixpt(double x, double L) {
+  double s = floor(wrap(x, L) / L * 4294967296.0);
+  return (uint32_t)((uint64_t)s & 0xffffffffULL);
+}
+
+int64_t orc_neighbor_pairs(int n, const double* x, double L, double r_list, int32_t* out_i,
+                           int32_t* out_j, int64_t cap) {
+  double s = r_list / L * 4294967296.0;
+  uint64_t T = (uint64_t)(s * s);
+  int64_t m = 0;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      uint64_t d2 = 0;
+      for (int c = 0; c < 3; ++c) {
+        int64_t d = (int32_t)(fixpt(x[3 * i + c], L) - fixpt(x[3 * j + c], L));
+        d2 += (uint64_t)(d * d);
+      }
+      if (d2 <= T) {
+        if (m < cap) { out_i[m] = i; out_j[m] = j; }
+        ++m;
+      }
+    }
+  return m;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Protocol: altitude of a flyer at step k (Eq. 2 and SI Eqs. S6-S7).                    */
+/* Insertion runs w_max -> 0, deletion 0 -> w_max; the deletion schedule is the time     */
+/* reverse of the insertion schedule.                                                    */
+/* ------------------------------------------------------------------------------------ */
+double orc_altitude(const orc_params* p, int insertion, int k) {
+  /* Deletion runs the insertion schedule backwards in time: w_del(t) = w_ins(t_f + t_i - t).
+   * Reading: the deletion forms printed in Eqs. S6-S7 are swapped between w_v and w_x (as
+   * printed, neither is the time reverse of its insertion form, and the text describes
+   * a removal that is fast early for w_v); the time-reverse definition restores the
+   * symmetric schedules that Sec. II.A requires for detailed balance. */
+  int kk = insertion ? k : p->n_f - k;
+  double xi = (double)kk / (double)p->n_f; /* x_i = (t - t_i)/(t_f - t_i) of the insertion */
+  double n = p->sched_n;
+  double s; /* w / w_max */
+  if (p->schedule == ORC_SCHED_WV) s = 1.0 - pow(xi, n);      /* Eq. S6, insertion */
+  else if (p->schedule == ORC_SCHED_WX) s = pow(1.0 - xi, n); /* Eq. S7, insertion */
+  else s = 1.0 - xi;                                          /* Eq. 2: constant v_f */
+  return p->w_max * s;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Velocity Verlet with RATTLE for rigid waters                                          */
+/* ------------------------------------------------------------------------------------ */
+double orc_kinetic(const orc_params* p, int n, const double* v, const uint8_t* fly) {
+  double K = 0.0;
+  for (int i = 0; i < n; ++i) {
+    if (fly && fly[i]) continue;
+    double m = mass_of(p, i);
+    K += 0.5 * m * p->mvv2e * (v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] + v[3 * i + 2] * v[3 * i + 2]);
+  }
+  return K;
+}
+
+static void kick(const orc_params* p, int n, double* v, const double* F, const uint8_t* fly, double h) {
+  for (int i = 0; i < n; ++i) {
+    if (fly && fly[i]) continue; /* flyers keep their 3D state (Sec. II.B.1) */
+    double a = h / (mass_of(p, i) * p->mvv2e);
+    for (int c = 0; c < 3; ++c) v[3 * i + c] += a * F[3 * i + c];
+  }
+}
+
+static void drift(const orc_params* p, int n, double* x, const double* v, const uint8_t* fly, double h) {
+  for (int i = 0; i < n; ++i) {
+    if (fly && fly[i]) continue;
+    for (int c = 0; c < 3; ++c) x[3 * i + c] = wrap(x[3 * i + c] + h * v[3 * i + c], p->L);
+  }
+}
+
+/* the three distance constraints of a rigid water: (O,H1), (O,H2), (H1,H2) */
+static void water_constraint(const orc_params* p, int k, int* a, int* b, double* d) {
+  static const int A[3] = {0, 0, 1}, B[3] = {1, 2, 2};
+  *a = A[k];
+  *b = B[k];
+  *d = (k < 2) ? p->d_oh : p->d_hh;
+}
+
+/* SHAKE position stage of RATTLE (Andersen 1983): after an unconstrained drift, iterate
+ * pairwise corrections along the old bond vectors until every bond length holds; the
+ * same impulse corrects the half-step velocities. xold holds positions before the drift. */
+static void shake(const orc_params* p, double* x, double* v, const double* xold, double h) {
+  for (int m = 0; m < p->n_water; ++m) {
+    for (int it = 0; it < 1000; ++it) {
+      double worst = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        int a, b;
+        double d;
+        water_constraint(p, k, &a, &b, &d);
+        int ia = 3 * m + a, ib = 3 * m + b;
+        double rn[3], ro[3], rn2 = 0.0, dot = 0.0;
+        for (int c = 0; c < 3; ++c) {
+          rn[c] = minimg(x[3 * ia + c] - x[3 * ib + c], p->L);
+          ro[c] = minimg(xold[3 * ia + c] - xold[3 * ib + c], p->L);
+          rn2 += rn[c] * rn[c];
+          dot += rn[c] * ro[c];
+        }
+        double diff = rn2 - d * d;
+        double rel = fabs(diff) / (d * d);
+        if (rel > worst) worst = rel;
+        double ima = 1.0 / mass_of(p, ia), imb = 1.0 / mass_of(p, ib);
+        double gk = diff / (2.0 * dot * (ima + imb));
+        for (int c = 0; c < 3; ++c) {
+          x[3 * ia + c] = wrap(x[3 * ia + c] - gk * ima * ro[c], p->L);
+          x[3 * ib + c] = wrap(x[3 * ib + c] + gk * imb * ro[c], p->L);
+          v[3 * ia + c] -= gk * ima * ro[c] / h;
+          v[3 * ib + c] += gk * imb * ro[c] / h;
+        }
+      }
+      if (worst < 1e-14) break;
+    }
+  }
+}
+
+/* RATTLE velocity stage: remove the bond-parallel relative velocity of every constraint */
+static void rattle_v(const orc_params* p, const double* x, double* v) {
+  for (int m = 0; m < p->n_water; ++m) {
+    for (int it = 0; it < 1000; ++it) {
+      double worst = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        int a, b;
+        double d;
+        water_constraint(p, k, &a, &b, &d);
+        int ia = 3 * m + a, ib = 3 * m + b;
+        double r[3], dv = 0.0;
+        for (int c = 0; c < 3; ++c) {
+          r[c] = minimg(x[3 * ia + c] - x[3 * ib + c], p->L);
+          dv += r[c] * (v[3 * ia + c] - v[3 * ib + c]);
+        }
+        if (fabs(dv) / (d * d) > worst) worst = fabs(dv) / (d * d);
+        double ima = 1.0 / mass_of(p, ia), imb = 1.0 / mass_of(p, ib);
+        double kk = dv / (d * d * (ima + imb));
+        for (int c = 0; c < 3; ++c) {
+          v[3 * ia + c] -= kk * ima * r[c];
+          v[3 * ib + c] += kk * imb * r[c];
+        }
+      }
+      if (worst < 1e-15) break;
+    }
+  }
+}
+
+/* one velocity-Verlet step. Reading of the step order (not stated in the paper): kick with
+ * F(x, w_k), drift, move the altitude to w_{k+1}, force F(x, w_{k+1}), kick.  This map is
+ * exactly time-reversible under v -> -v with the reversed schedule. */
+static void vv_step(const orc_params* p, int n, double* x, double* v, double* F, const uint8_t* fly,
+                    double* w, double w_next, double* xold) {
+  double h = p->dt;
+  kick(p, n, v, F, fly, 0.5 * h);
+  if (p->n_water) memcpy(xold, x, sizeof(double) * 3 * (size_t)(3 * p->n_water));
+  drift(p, n, x, v, fly, h);
+  if (p->n_water) shake(p, x, v, xold, h);
+  if (w && fly)
+    for (int i = 0; i < n; ++i) w[i] = (fly[i] == 1) ? w_next : 0.0;
+  orc_energy_forces(p, n, x, w, fly, F);
+  kick(p, n, v, F, fly, 0.5 * h);
+  if (p->n_water) rattle_v(p, x, v);
+}
+
+static int n_atoms(const orc_params* p, int n_pairs) { return 3 * p->n_water + 2 * n_pairs; }
+
+double orc_nve(const orc_params* p, orc_state* s, int64_t n_steps, double* e_trace) {
+  int n = n_atoms(p, s->n_pairs);
+  double* F = (double*)calloc(3 * (size_t)(n + 1), sizeof(double));
+  double* xold = (double*)calloc(3 * (size_t)(n + 1), sizeof(double));
+  double U = orc_energy_forces(p, n, s->x, NULL, NULL, F);
+  for (int64_t k = 0; k < n_steps; ++k) {
+    vv_step(p, n, s->x, s->v, F, NULL, NULL, 0.0, xold);
+    if (e_trace) {
+      U = orc_energy_forces(p, n, s->x, NULL, NULL, NULL);
+      e_trace[k] = U + orc_kinetic(p, n, s->v, NULL);
+    }
+  }
+  U = orc_energy_forces(p, n, s->x, NULL, NULL, NULL);
+  free(F);
+  free(xold);
+  return U;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Thermostat for equilibrium MD: CSVR (Bussi, Donadio, Parrinello, JCP 126, 014101      */
+/* (2007), Eq. A7).  The chi-square variate with (dof-1) degrees uses the gamma sampler */
+/* of Marsaglia and Tsang (ACM TOMS 26, 363 (2000)).                                    */
+/* ------------------------------------------------------------------------------------ */
+static double chi2_draw(const orc_params* p, uint64_t step, double dof) {
+  double k = 0.5 * dof; /* gamma shape; chi2(dof) = 2 Gamma(dof/2, 1) */
+  if (k <= 0.0) return 0.0;
+  double boost = 1.0;
+  if (k < 1.0) k += 1.0; /* shape < 1 handled by the standard boost U^(1/k) */
+  double d = k - 1.0 / 3.0, c = 1.0 / sqrt(9.0 * d);
+  double g = d;
+  for (uint64_t attempt = 0; attempt < 4096; ++attempt) {
+    uint64_t r[4];
+    draw(p, step, attempt, ORC_PUR_GAMMA, r);
+    double z = gauss_cos(r[0], r[1]);
+    double t = 1.0 + c * z;
+    if (t <= 0.0) continue;
+    t = t * t * t;
+    double u = u01_open(r[2]);
+    if (log(u) < 0.5 * z * z + d - d * t + d * log(t)) {
+      g = d * t;
+      if (0.5 * dof < 1.0) boost = pow(u01_open(r[3]), 1.0 / (0.5 * dof));
+      break;
+    }
+  }
+  return 2.0 * g * boost;
+}
+
+static void csvr(const orc_params* p, int n, double* v, uint64_t step) {
+  double dof = 3.0 * n - 3.0 * p->n_water;
+  if (dof < 1.0 || p->tau_t <= 0.0) return;
+  double K = orc_kinetic(p, n, v, NULL);
+  if (K <= 0.0) return;
+  double Kbar = 0.5 * dof / p->beta;
+  double c = exp(-p->dt / p->tau_t);
+  uint64_t r[4];
+  draw(p, step, 0, ORC_PUR_THERMO, r);
+  double R1 = gauss_cos(r[0], r[1]);
+  double S = chi2_draw(p, step, dof - 1.0);
+  double Knew = K + (1.0 - c) * (Kbar * (S + R1 * R1) / dof - K) +
+                2.0 * R1 * sqrt(Kbar * K * (1.0 - c) * c / dof);
+  double alpha = sqrt(Knew / K);
+  if (R1 + sqrt(dof * K * c / (Kbar * (1.0 - c))) < 0.0) alpha = -alpha;
+  for (int i = 0; i < 3 * n; ++i) v[i] *= alpha;
+}
+
+void orc_md(const orc_params* p, orc_state* s, int64_t n_steps) {
+  int n = n_atoms(p, s->n_pairs);
+  double* F = (double*)calloc(3 * (size_t)(n + 1), sizeof(double));
+  double* xold = (double*)calloc(3 * (size_t)(n + 1), sizeof(double));
+  orc_energy_forces(p, n, s->x, NULL, NULL, F);
+  for (int64_t k = 0; k < n_steps; ++k) {
+    vv_step(p, n, s->x, s->v, F, NULL, NULL, 0.0, xold);
+    csvr(p, n, s->v, s->step_ctr);
+    s->step_ctr++;
+  }
+  free(F);
+  free(xold);
+}
+
+/* Maxwell-Boltzmann velocities (Sec. II.A): three normals per atom from the atom's own
+ * counter; waters then lose their bond-parallel components (RATTLE projection). */
+static void mb_velocity(const orc_params* p, int type, const uint64_t r[4], double v[3]) {
+  double sd = sqrt(1.0 / (p->beta * p->mass[type] * p->mvv2e));
+  v[0] = sd * gauss_cos(r[0], r[1]);
+  v[1] = sd * gauss_sin(r[0], r[1]);
+  v[2] = sd * gauss_cos(r[2], r[3]);
+}
+
+void orc_init_velocities(const orc_params* p, orc_state* s) {
+  int n = n_atoms(p, s->n_pairs);
+  for (int i = 0; i < n; ++i) {
+    uint64_t r[4];
+    draw(p, (uint64_t)i, 0, ORC_PUR_VINIT, r);
+    mb_velocity(p, orc_atom_type(p, i), r, &s->v[3 * i]);
+  }
+  if (p->n_water) rattle_v(p, s->x, s->v);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* NEMD along the altitude schedule (Sec. II.A, II.B.1)                                  */
+/* ------------------------------------------------------------------------------------ */
+static double nemd(const orc_params* p, int n, double* x, double* v, const uint8_t* fly, int insertion) {
+  double* F = (double*)calloc(3 * (size_t)n, sizeof(double));
+  double* w = (double*)calloc((size_t)n, sizeof(double));
+  double* wbuf = (double*)calloc((size_t)n, sizeof(double));
+  double* xold = (double*)calloc(3 * (size_t)n, sizeof(double));
+  double w0 = orc_altitude(p, insertion, 0);
+  for (int i = 0; i < n; ++i) w[i] = (fly[i] == 1) ? w0 : 0.0;
+  orc_energy_forces(p, n, x, w, fly, F);
+  double wprot = 0.0;
+  for (int k = 0; k < p->n_f; ++k) {
+    double wk = orc_altitude(p, insertion, k), wk1 = orc_altitude(p, insertion, k + 1);
+    /* the protocol work of step k is taken at the drifted positions, where the altitude
+     * switches from w_k to w_{k+1} */
+    double h = p->dt;
+    kick(p, n, v, F, fly, 0.5 * h);
+    if (p->n_water) memcpy(xold, x, sizeof(double) * 9 * (size_t)p->n_water);
+    drift(p, n, x, v, fly, h);
+    if (p->n_water) shake(p, x, v, xold, h);
+    wprot += flyer_energy(p, n, x, fly, wk1, wbuf) - flyer_energy(p, n, x, fly, wk, wbuf);
+    for (int i = 0; i < n; ++i) w[i] = (fly[i] == 1) ? wk1 : 0.0;
+    orc_energy_forces(p, n, x, w, fly, F);
+    kick(p, n, v, F, fly, 0.5 * h);
+    if (p->n_water) rattle_v(p, x, v);
+  }
+  free(F);
+  free(w);
+  free(wbuf);
+  free(xold);
+  return wprot;
+}
+
+double orc_nemd_path(const orc_params* p, orc_state* s, const int32_t* flyers, int n_flyers,
+                     int insertion, double* U_end) {
+  int n = n_atoms(p, s->n_pairs);
+  uint8_t* fly = (uint8_t*)calloc((size_t)n, 1);
+  for (int k = 0; k < n_flyers; ++k) fly[flyers[k]] = 1;
+  double wprot = nemd(p, n, s->x, s->v, fly, insertion);
+  if (U_end) {
+    double* w = (double*)calloc((size_t)n, sizeof(double));
+    double wf = orc_altitude(p, insertion, p->n_f);
+    for (int i = 0; i < n; ++i) w[i] = fly[i] ? wf : 0.0;
+    *U_end = orc_energy_forces(p, n, s->x, w, fly, NULL);
+    free(w);
+  }
+  free(fly);
+  return wprot;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* One pair-exchange trial                                                               */
+/* ------------------------------------------------------------------------------------ */
+static void flip_all(double* v, int n) {
+  for (int i = 0; i < 3 * n; ++i) v[i] = -v[i];
+}
+
+/* Trial t of this chain.  Draw table (counter {t, block, TRIAL, 0}):
+ *   block 0: [0] top bit = insertion, [1] top bit = reverse momenta before NEMD,
+ *            [2] top bit = reverse after the decision, [3] acceptance uniform in (0,1]
+ *   block 1: deletion: [0] cation index, [1] anion index (uniform in [0,N));
+ *            insertion: [0..2] cation x,y,z and [3] anion x as 32-bit box fractions
+ *   block 2: insertion: [0..1] anion y,z
+ *   blocks 3-4: Maxwell-Boltzmann velocities of the inserted cation and anion
+ * Readings: insertion and deletion are proposed with probability 1/2 each; the cation
+ * and the anion are chosen independently (Eq. 3 squares 1/(N+1)); the momentum
+ * reversal flips every velocity with probability 1/2 before NEMD and again after the
+ * decision, and a rejection restores the state saved after the first flip.
+ * Delta H compares the equilibrium Hamiltonians of the two end states: for insertion
+ * H_{N+1}(end, all 3D) - H_N(start, flyers absent); for deletion the reverse.  The
+ * flyers' kinetic energy is left out: insertion draws it from Maxwell-Boltzmann and a
+ * deletion discards it, so it cancels against the e^{-beta K}/N_k factors of Eqs. 3-4.
+ */
+int orc_trial(const orc_params* p, orc_state* s, orc_record* rec) {
+  uint64_t t = s->trial_ctr++;
+  uint64_t b0[4], b1[4], b2[4], b3[4], b4[4];
+  draw(p, t, 0, ORC_PUR_TRIAL, b0);
+  draw(p, t, 1, ORC_PUR_TRIAL, b1);
+  draw(p, t, 2, ORC_PUR_TRIAL, b2);
+  draw(p, t, 3, ORC_PUR_TRIAL, b3);
+  draw(p, t, 4, ORC_PUR_TRIAL, b4);
+  int insertion = (int)(b0[0] >> 63);
+  int flip_start = (int)(b0[1] >> 63), flip_end = (int)(b0[2] >> 63);
+  double ln_u = log(u01_open(b0[3]));
+  int N = s->n_pairs;
+  int base = 3 * p->n_water;
+  int n = n_atoms(p, N);
+  double V = p->L * p->L * p->L;
+
+  memset(rec, 0, sizeof(*rec));
+  rec->move = insertion;
+  rec->n_before = N;
+  rec->n_after = N;
+  rec->cation = rec->anion = -1;
+  rec->ln_u = ln_u;
+
+  if (flip_start) flip_all(s->v, n);
+  if ((!insertion && N == 0) || (insertion && N >= s->cap_pairs)) {
+    rec->status = insertion ? 2 : 1;
+    if (flip_end) flip_all(s->v, n);
+    return 0;
+  }
+
+  int ntot = insertion ? n + 2 : n;
+  double* xs = (double*)malloc(sizeof(double) * 3 * (size_t)ntot);
+  double* vs = (double*)malloc(sizeof(double) * 3 * (size_t)ntot);
+  memcpy(xs, s->x, sizeof(double) * 3 * (size_t)n);
+  memcpy(vs, s->v, sizeof(double) * 3 * (size_t)n);
+  uint8_t* fly = (uint8_t*)calloc((size_t)ntot, 1);
+  double* w0 = (double*)calloc((size_t)ntot, sizeof(double));
+  double Ustart, Uend, Kstart, Kend;
+  int ci, ai;
+
+  if (insertion) {
+    ci = base + 2 * N;
+    ai = ci + 1;
+    double h = p->L / 4294967296.0;
+    s->x[3 * ci + 0] = (double)(uint32_t)(b1[0] >> 32) * h;
+    s->x[3 * ci + 1] = (double)(uint32_t)(b1[1] >> 32) * h;
+    s->x[3 * ci + 2] = (double)(uint32_t)(b1[2] >> 32) * h;
+    s->x[3 * ai + 0] = (double)(uint32_t)(b1[3] >> 32) * h;
+    s->x[3 * ai + 1] = (double)(uint32_t)(b2[0] >> 32) * h;
+    s->x[3 * ai + 2] = (double)(uint32_t)(b2[1] >> 32) * h;
+    double sdc = sqrt(1.0 / (p->beta * p->mass[0] * p->mvv2e));
+    double sda = sqrt(1.0 / (p->beta * p->mass[1] * p->mvv2e));
+    s->v[3 * ci + 0] = sdc * gauss_cos(b3[0], b3[1]);
+    s->v[3 * ci + 1] = sdc * gauss_sin(b3[0], b3[1]);
+    s->v[3 * ci + 2] = sdc * gauss_cos(b3[2], b3[3]);
+    s->v[3 * ai + 0] = sda * gauss_sin(b3[2], b3[3]);
+    s->v[3 * ai + 1] = sda * gauss_cos(b4[0], b4[1]);
+    s->v[3 * ai + 2] = sda * gauss_sin(b4[0], b4[1]);
+    fly[ci] = fly[ai] = 1;
+    /* H_start: the N-pair system, flyers absent */
+    Ustart = orc_energy_forces(p, n, s->x, NULL, NULL, NULL);
+    Kstart = orc_kinetic(p, ntot, s->v, fly);
+    rec->w_prot = nemd(p, ntot, s->x, s->v, fly, 1);
+    /* H_end: the N+1-pair system, everyone in 3D */
+    Uend = orc_energy_forces(p, ntot, s->x, NULL, NULL, NULL);
+    Kend = orc_kinetic(p, ntot, s->v, fly);
+  } else {
+    int c = pick(b1[0], N), a = pick(b1[1], N);
+    rec->cation = c;
+    rec->anion = a;
+    ci = base + 2 * c;
+    ai = base + 2 * a + 1;
+    fly[ci] = fly[ai] = 1;
+    Ustart = orc_energy_forces(p, n, s->x, NULL, NULL, NULL);
+    Kstart = orc_kinetic(p, n, s->v, fly);
+    rec->w_prot = nemd(p, n, s->x, s->v, fly, 0);
+    /* H_end: the N-1-pair system, flyers absent */
+    uint8_t* gone = (uint8_t*)calloc((size_t)n, 1);
+    gone[ci] = gone[ai] = 2;
+    Uend = orc_energy_forces(p, n, s->x, NULL, gone, NULL);
+    Kend = orc_kinetic(p, n, s->v, fly);
+    free(gone);
+  }
+  double dH = (Uend + Kend) - (Ustart + Kstart);
+  rec->dH = dH;
+  /* Eqs. 6 and 8 with Lambda_s = 1; Delta M is defined in the insertion direction */
+  double x_acc;
+  if (insertion) {
+    rec->beta_dM = p->beta * dH - 2.0 * log(V / (double)(N + 1));
+    x_acc = -rec->beta_dM + p->beta_mu;
+  } else {
+    rec->beta_dM = -p->beta * dH - 2.0 * log(V / (double)N);
+    x_acc = rec->beta_dM - p->beta_mu;
+  }
+  rec->x_acc = x_acc;
+  int accept = isfinite(dH) && (ln_u < x_acc);
+  if (!isfinite(dH)) rec->status = 3;
+  if (accept) {
+    if (insertion) {
+      s->n_pairs = N + 1;
+    } else {
+      /* swap-with-last removal keeps the interleaved cation/anion layout */
+      int lc = base + 2 * (N - 1), la = lc + 1;
+      for (int k = 0; k < 3; ++k) {
+        s->x[3 * ci + k] = s->x[3 * lc + k];
+        s->v[3 * ci + k] = s->v[3 * lc + k];
+        s->x[3 * ai + k] = s->x[3 * la + k];
+        s->v[3 * ai + k] = s->v[3 * la + k];
+      }
+      s->n_pairs = N - 1;
+    }
+  } else {
+    memcpy(s->x, xs, sizeof(double) * 3 * (size_t)n);
+    memcpy(s->v, vs, sizeof(double) * 3 * (size_t)n);
+  }
+  rec->accepted = accept;
+  rec->n_after = s->n_pairs;
+  if (flip_end) flip_all(s->v, n_atoms(p, s->n_pairs));
+  free(xs);
+  free(vs);
+  free(fly);
+  free(w0);
+  return 0;
+}
+
+int orc_run_cycles(const orc_params* p, orc_state* s, int64_t n_cycles, int64_t n_eq, orc_record* recs) {
+  for (int64_t c = 0; c < n_cycles; ++c) {
+    if (n_eq > 0) orc_md(p, s, n_eq);
+    orc_trial(p, s, &recs[c]);
+  }
+  return 0;
+}

@@ -1,0 +1,131 @@
+/*
+ * h4d_oracle.h -- FP64 CPU oracle for the hybrid 4D NEMD/MC (H4D) grand-canonical
+ * method of Kim, Belloni and Rotenberg, "Grand-canonical molecular dynamics
+ * simulations powered by a hybrid 4D nonequilibrium MD/MC method" (arXiv:2307.11447).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This header and h4d_oracle.c are the slow, plain,
+ * double-precision statement of what the GPU library computes.  Only the test suite,
+ * the smoke check and the CPU-baseline leg of the benchmark may load it.  It shares no
+ * code, header, table or constant generator with the CUDA library, and the CUDA
+ * library never calls it.
+ *
+ * Conventions (all readings of the paper are listed in the design doc as well):
+ *   - atoms [0, 3*n_water) are rigid waters stored O,H,H; ions follow, stored as
+ *     interleaved pairs: ion 2k is cation k (type 0), ion 2k+1 is anion k (type 1);
+ *     water O is type 2 and H is type 3.
+ *   - positions are kept wrapped into [0, L); every displacement uses the minimum image.
+ *   - the random stream is Philox4x64-10 keyed by (seed, replica); every draw has a
+ *     fixed (counter, purpose) address so that any implementation of the same method
+ *     draws the same numbers independent of evaluation order.
+ */
+#ifndef H4D_ORACLE_H
+#define H4D_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_MAXT 4
+
+/* Philox purposes (counter word 2) */
+#define ORC_PUR_TRIAL 1u
+#define ORC_PUR_GAMMA 2u
+#define ORC_PUR_THERMO 3u
+#define ORC_PUR_VINIT 4u
+
+/* altitude schedules: constant velocity (Eq. 2), w_v (Eq. S6), w_x (Eq. S7) */
+#define ORC_SCHED_LINEAR 0
+#define ORC_SCHED_WV 1
+#define ORC_SCHED_WX 2
+
+typedef struct {
+  double L;        /* cubic box edge */
+  double beta;     /* 1/kT */
+  double beta_mu;  /* beta * mu of the ion pair (Lambda_s = 1) */
+  /* pair potential: truncated-shifted LJ (Eq. 19, Lorentz-Berthelot), erfc Coulomb (Eq. 9, 20) */
+  double rc_lj, rc_coul, alpha, kcoul, kappa_sr;
+  int32_t ntypes, pad0;
+  double q[ORC_MAXT], sig[ORC_MAXT], eps[ORC_MAXT], mass[ORC_MAXT];
+  double mvv2e;    /* converts mass*velocity^2 into energy units */
+  /* protocol */
+  double dt, w_max, tau_t;
+  int32_t n_f, schedule;
+  double sched_n;  /* exponent n of Eqs. S6-S7 */
+  /* rigid water geometry (SPC/E-like) */
+  double d_oh, d_hh;
+  int32_t n_water, use_cells;
+  uint64_t seed, replica;
+} orc_params;
+
+typedef struct {
+  int32_t n_pairs, cap_pairs;
+  double *x, *v;       /* [(3*n_water + 2*cap_pairs) * 3] */
+  uint64_t trial_ctr;  /* trials done by this chain (Philox counter of trial draws) */
+  uint64_t step_ctr;   /* equilibrium MD steps done (Philox counter of thermostat draws) */
+} orc_state;
+
+typedef struct {
+  int32_t move;       /* 1 insertion, 0 deletion */
+  int32_t accepted;
+  int32_t n_before, n_after;
+  int32_t status;     /* 0 ok, 1 deletion from empty system, 2 capacity, 3 non-finite energy */
+  int32_t cation, anion;  /* chosen pair (deletion) or -1 */
+  int32_t pad;
+  double dH;          /* H_end - H_start in energy units */
+  double beta_dM;     /* beta * Delta M, insertion-direction convention (Eqs. 6, 8) */
+  double w_prot;      /* protocol work sum_k [U(w_{k+1}) - U(w_k)] at fixed positions */
+  double ln_u;        /* log of the uniform acceptance draw */
+  double x_acc;       /* exponent compared with ln_u */
+} orc_record;
+
+void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+
+/* pair energy and derivative at 4D distance r4 between types ti, tj with
+ * short-range screening factor g (Eq. 11) applied to the Coulomb part */
+void orc_pair(const orc_params* p, int ti, int tj, double r4, double g, double* u, double* dudr);
+
+int orc_atom_type(const orc_params* p, int a);
+
+/* total potential energy and 3D forces of n atoms at altitudes w (NULL = all zero),
+ * flyers marked in fly (NULL = none); F may be NULL. Brute force O(n^2) unless
+ * p->use_cells, in which case a plain cell list produces the same sum. */
+double orc_energy_forces(const orc_params* p, int n, const double* x, const double* w,
+                         const uint8_t* fly, double* F);
+
+/* number of list pairs (i<j) under the fixed-point neighbour criterion; writes up to
+ * cap pairs, sorted by (i, j) */
+int64_t orc_neighbor_pairs(int n, const double* x, double L, double r_list,
+                           int32_t* out_i, int32_t* out_j, int64_t cap);
+
+/* altitude of a flyer at NEMD step k of n_f */
+double orc_altitude(const orc_params* p, int insertion, int k);
+
+/* kinetic energy of atoms (optionally skipping flyers) */
+double orc_kinetic(const orc_params* p, int n, const double* v, const uint8_t* fly);
+
+/* plain NVE velocity-Verlet steps (w = 0); returns final potential energy */
+double orc_nve(const orc_params* p, orc_state* s, int64_t n_steps, double* e_trace);
+
+/* equilibrium MD steps with the CSVR thermostat */
+void orc_md(const orc_params* p, orc_state* s, int64_t n_steps);
+
+/* one NEMD path with the flyers given, forward schedule (insertion or deletion);
+ * used for the reversibility pin; returns the protocol work */
+double orc_nemd_path(const orc_params* p, orc_state* s, const int32_t* flyers, int n_flyers,
+                     int insertion, double* U_end);
+
+/* one H4D pair-exchange trial (Sec. II.A) */
+int orc_trial(const orc_params* p, orc_state* s, orc_record* rec);
+
+/* n_cycles GCMD cycles: n_eq equilibrium MD steps then one trial (Fig. 1) */
+int orc_run_cycles(const orc_params* p, orc_state* s, int64_t n_cycles, int64_t n_eq,
+                   orc_record* recs);
+
+/* draw initial Maxwell-Boltzmann velocities for all atoms */
+void orc_init_velocities(const orc_params* p, orc_state* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,289 @@
+"""ctypes binding of the FP64 CPU oracle (h4d_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by ``__graft_entry__.smoke()`` and by the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py``.  The GPU library never
+imports this module and this module never imports the GPU library.
+
+Every function takes plain numpy arrays; configurations are the parameter dictionaries
+of ``paper_2307_11447_gb300.workloads`` (parameter values and seeded inputs only).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "h4d_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+MAXT = 4
+SCHED = {"linear": 0, "wv": 1, "wx": 2}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host C compiler (no GPU, no CUDA)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        )
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("L", ctypes.c_double),
+        ("beta", ctypes.c_double),
+        ("beta_mu", ctypes.c_double),
+        ("rc_lj", ctypes.c_double),
+        ("rc_coul", ctypes.c_double),
+        ("alpha", ctypes.c_double),
+        ("kcoul", ctypes.c_double),
+        ("kappa_sr", ctypes.c_double),
+        ("ntypes", ctypes.c_int32),
+        ("pad0", ctypes.c_int32),
+        ("q", ctypes.c_double * MAXT),
+        ("sig", ctypes.c_double * MAXT),
+        ("eps", ctypes.c_double * MAXT),
+        ("mass", ctypes.c_double * MAXT),
+        ("mvv2e", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("w_max", ctypes.c_double),
+        ("tau_t", ctypes.c_double),
+        ("n_f", ctypes.c_int32),
+        ("schedule", ctypes.c_int32),
+        ("sched_n", ctypes.c_double),
+        ("d_oh", ctypes.c_double),
+        ("d_hh", ctypes.c_double),
+        ("n_water", ctypes.c_int32),
+        ("use_cells", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("replica", ctypes.c_uint64),
+    ]
+
+
+class _State(ctypes.Structure):
+    _fields_ = [
+        ("n_pairs", ctypes.c_int32),
+        ("cap_pairs", ctypes.c_int32),
+        ("x", ctypes.POINTER(ctypes.c_double)),
+        ("v", ctypes.POINTER(ctypes.c_double)),
+        ("trial_ctr", ctypes.c_uint64),
+        ("step_ctr", ctypes.c_uint64),
+    ]
+
+
+RECORD_DTYPE = np.dtype(
+    [
+        ("move", np.int32),
+        ("accepted", np.int32),
+        ("n_before", np.int32),
+        ("n_after", np.int32),
+        ("status", np.int32),
+        ("cation", np.int32),
+        ("anion", np.int32),
+        ("pad", np.int32),
+        ("dH", np.float64),
+        ("beta_dM", np.float64),
+        ("w_prot", np.float64),
+        ("ln_u", np.float64),
+        ("x_acc", np.float64),
+    ]
+)
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        d = ctypes.c_double
+        pd = ctypes.POINTER(ctypes.c_double)
+        pu8 = ctypes.POINTER(ctypes.c_uint8)
+        pi32 = ctypes.POINTER(ctypes.c_int32)
+        pu64 = ctypes.POINTER(ctypes.c_uint64)
+        P = ctypes.POINTER(Params)
+        S = ctypes.POINTER(_State)
+        _lib.orc_philox4x64_10.argtypes = [pu64, pu64, pu64]
+        _lib.orc_pair.argtypes = [P, ctypes.c_int, ctypes.c_int, d, d, pd, pd]
+        _lib.orc_energy_forces.argtypes = [P, ctypes.c_int, pd, pd, pu8, pd]
+        _lib.orc_energy_forces.restype = d
+        _lib.orc_neighbor_pairs.argtypes = [ctypes.c_int, pd, d, d, pi32, pi32, ctypes.c_int64]
+        _lib.orc_neighbor_pairs.restype = ctypes.c_int64
+        _lib.orc_altitude.argtypes = [P, ctypes.c_int, ctypes.c_int]
+        _lib.orc_altitude.restype = d
+        _lib.orc_kinetic.argtypes = [P, ctypes.c_int, pd, pu8]
+        _lib.orc_kinetic.restype = d
+        _lib.orc_nve.argtypes = [P, S, ctypes.c_int64, pd]
+        _lib.orc_nve.restype = d
+        _lib.orc_md.argtypes = [P, S, ctypes.c_int64]
+        _lib.orc_nemd_path.argtypes = [P, S, pi32, ctypes.c_int, ctypes.c_int, pd]
+        _lib.orc_nemd_path.restype = d
+        _lib.orc_trial.argtypes = [P, S, ctypes.c_void_p]
+        _lib.orc_run_cycles.argtypes = [P, S, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
+        _lib.orc_init_velocities.argtypes = [P, S]
+        _lib.orc_atom_type.argtypes = [P, ctypes.c_int]
+    return _lib
+
+
+def _ptr(a, ct=ctypes.c_double):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def make_params(cfg: dict, **override) -> Params:
+    """Build the oracle's parameter block from a workload dictionary."""
+    c = dict(cfg)
+    c.update(override)
+    p = Params()
+    p.L = float(c["L"])
+    p.beta = float(c["beta"])
+    p.beta_mu = float(c.get("beta_mu", 0.0))
+    p.rc_lj = float(c["rc_lj"])
+    p.rc_coul = float(c["rc_coul"])
+    p.alpha = float(c["alpha"])
+    p.kcoul = float(c["kcoul"])
+    p.kappa_sr = float(c.get("kappa_sr", 0.0))
+    p.ntypes = len(c["q"])
+    for k in range(len(c["q"])):
+        p.q[k] = c["q"][k]
+        p.sig[k] = c["sig"][k]
+        p.eps[k] = c["eps"][k]
+        p.mass[k] = c["mass"][k]
+    p.mvv2e = float(c.get("mvv2e", 1.0))
+    p.dt = float(c["dt"])
+    p.w_max = float(c["w_max"])
+    p.tau_t = float(c.get("tau_t", 0.0))
+    p.n_f = int(c["n_f"])
+    p.schedule = SCHED[c.get("schedule", "linear")] if isinstance(c.get("schedule", "linear"), str) else int(c["schedule"])
+    p.sched_n = float(c.get("sched_n", 1.0))
+    p.d_oh = float(c.get("d_oh", 0.0))
+    p.d_hh = float(c.get("d_hh", 0.0))
+    p.n_water = int(c.get("n_water", 0))
+    p.use_cells = int(c.get("use_cells", 0))
+    p.seed = int(c.get("seed", 0))
+    p.replica = int(c.get("replica", 0))
+    return p
+
+
+class State:
+    """A chain's state: positions and velocities of 3*n_water + 2*cap_pairs atoms."""
+
+    def __init__(self, p: Params, x: np.ndarray, v: np.ndarray | None, n_pairs: int, cap_pairs: int):
+        n_cap = 3 * p.n_water + 2 * cap_pairs
+        self.x = np.zeros((n_cap, 3), np.float64)
+        self.v = np.zeros((n_cap, 3), np.float64)
+        n = 3 * p.n_water + 2 * n_pairs
+        self.x[:n] = np.asarray(x, np.float64).reshape(-1, 3)[:n]
+        if v is not None:
+            self.v[:n] = np.asarray(v, np.float64).reshape(-1, 3)[:n]
+        self.s = _State()
+        self.s.n_pairs = n_pairs
+        self.s.cap_pairs = cap_pairs
+        self.s.x = _ptr(self.x)
+        self.s.v = _ptr(self.v)
+        self.s.trial_ctr = 0
+        self.s.step_ctr = 0
+        self.n_water = p.n_water
+
+    @property
+    def n_pairs(self) -> int:
+        return self.s.n_pairs
+
+    @property
+    def n_atoms(self) -> int:
+        return 3 * self.n_water + 2 * self.s.n_pairs
+
+    def positions(self) -> np.ndarray:
+        return self.x[: self.n_atoms].copy()
+
+    def velocities(self) -> np.ndarray:
+        return self.v[: self.n_atoms].copy()
+
+
+def philox(ctr, key) -> np.ndarray:
+    c = np.asarray(ctr, np.uint64)
+    k = np.asarray(key, np.uint64)
+    out = np.zeros(4, np.uint64)
+    lib().orc_philox4x64_10(_ptr(c, ctypes.c_uint64), _ptr(k, ctypes.c_uint64), _ptr(out, ctypes.c_uint64))
+    return out
+
+
+def pair(p: Params, ti: int, tj: int, r4: float, g: float = 1.0):
+    u = ctypes.c_double()
+    du = ctypes.c_double()
+    lib().orc_pair(ctypes.byref(p), ti, tj, r4, g, ctypes.byref(u), ctypes.byref(du))
+    return u.value, du.value
+
+
+def energy_forces(p: Params, x: np.ndarray, w: np.ndarray | None = None, fly: np.ndarray | None = None):
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    n = x.shape[0]
+    F = np.zeros((n, 3), np.float64)
+    wa = None if w is None else np.ascontiguousarray(w, np.float64)
+    fa = None if fly is None else np.ascontiguousarray(fly, np.uint8)
+    U = lib().orc_energy_forces(ctypes.byref(p), n, _ptr(x), _ptr(wa), _ptr(fa, ctypes.c_uint8), _ptr(F))
+    return U, F
+
+
+def neighbor_pairs(x: np.ndarray, L: float, r_list: float):
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    n = x.shape[0]
+    m = lib().orc_neighbor_pairs(n, _ptr(x), L, r_list, None, None, 0)
+    oi = np.zeros(max(m, 1), np.int32)
+    oj = np.zeros(max(m, 1), np.int32)
+    lib().orc_neighbor_pairs(n, _ptr(x), L, r_list, _ptr(oi, ctypes.c_int32), _ptr(oj, ctypes.c_int32), m)
+    return oi[:m], oj[:m]
+
+
+def altitude(p: Params, insertion: bool, k: int) -> float:
+    return lib().orc_altitude(ctypes.byref(p), int(insertion), int(k))
+
+
+def kinetic(p: Params, v: np.ndarray, fly: np.ndarray | None = None) -> float:
+    v = np.ascontiguousarray(v, np.float64).reshape(-1, 3)
+    fa = None if fly is None else np.ascontiguousarray(fly, np.uint8)
+    return lib().orc_kinetic(ctypes.byref(p), v.shape[0], _ptr(v), _ptr(fa, ctypes.c_uint8))
+
+
+def nve(p: Params, st: State, n_steps: int, trace: bool = False):
+    tr = np.zeros(n_steps, np.float64) if trace else None
+    U = lib().orc_nve(ctypes.byref(p), ctypes.byref(st.s), n_steps, _ptr(tr))
+    return (U, tr) if trace else U
+
+
+def md(p: Params, st: State, n_steps: int) -> None:
+    lib().orc_md(ctypes.byref(p), ctypes.byref(st.s), n_steps)
+
+
+def nemd_path(p: Params, st: State, flyers, insertion: bool):
+    f = np.ascontiguousarray(flyers, np.int32)
+    U = ctypes.c_double()
+    w = lib().orc_nemd_path(ctypes.byref(p), ctypes.byref(st.s), _ptr(f, ctypes.c_int32), f.size, int(insertion), ctypes.byref(U))
+    return w, U.value
+
+
+def trial(p: Params, st: State) -> np.ndarray:
+    rec = np.zeros(1, RECORD_DTYPE)
+    lib().orc_trial(ctypes.byref(p), ctypes.byref(st.s), rec.ctypes.data)
+    return rec[0]
+
+
+def run_cycles(p: Params, st: State, n_cycles: int, n_eq: int) -> np.ndarray:
+    recs = np.zeros(n_cycles, RECORD_DTYPE)
+    lib().orc_run_cycles(ctypes.byref(p), ctypes.byref(st.s), n_cycles, n_eq, recs.ctypes.data)
+    return recs
+
+
+def init_velocities(p: Params, st: State) -> None:
+    lib().orc_init_velocities(ctypes.byref(p), ctypes.byref(st.s))
+
+
+def atom_type(p: Params, a: int) -> int:
+    return lib().orc_atom_type(ctypes.byref(p), a)

@@ -1,0 +1,157 @@
+"""Workload definitions and seeded synthetic inputs.
+
+This module holds parameter values and random initial configurations only; none of the
+method's arithmetic lives here.  Both the CUDA path and the CPU oracle take their inputs
+from it.
+
+Systems (units: LJ reduced units with k_B T = 1 for the LJ electrolyte; Angstrom, fs,
+amu, kJ/mol and e for aqueous NaCl):
+
+* ``lj250``  -- 250 ions (125 +1 / 125 -1), sigma = eps = m = 1, LJ cut-off 2.5,
+  Bjerrum length 2 (Coulomb prefactor 2 at k_B T = 1), erfc(0.3 r)/r Coulomb cut at 4,
+  density 0.2, dt 0.005, w_max 4, linear altitude protocol over 100 steps.
+* ``lj4000`` -- the same electrolyte with 4000 ions at density 0.3, 500 NEMD steps.
+* ``batched256`` -- 256 independent LJ-electrolyte replicas, ion counts uniform in
+  [100, 1000] (even), densities uniform in [0.1, 0.4].
+* ``nacl_aq`` -- 3000 rigid SPC/E-geometry waters + 55 Na+ + 55 Cl- at L = 45 A.
+
+Initial positions are uniform random with overlap rejection (minimum distance 0.8 sigma,
+or 2.0 A between atoms of different molecules); the configurations are then equilibrated
+by the method's own MD.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# --------------------------------------------------------------------------------------
+# LJ electrolyte (RPM-like): type 0 cation (+1), type 1 anion (-1)
+# --------------------------------------------------------------------------------------
+LJ_PHYSICS = dict(
+    system="lj",
+    beta=1.0,
+    rc_lj=2.5,
+    rc_coul=4.0,
+    alpha=0.3,
+    kcoul=2.0,  # Bjerrum length 2 sigma at k_B T = 1
+    kappa_sr=0.0,
+    q=[1.0, -1.0],
+    sig=[1.0, 1.0],
+    eps=[1.0, 1.0],
+    mass=[1.0, 1.0],
+    mvv2e=1.0,
+    dt=0.005,
+    w_max=4.0,
+    tau_t=0.1,
+    schedule="linear",
+    sched_n=1.0,
+    n_water=0,
+    d_oh=0.0,
+    d_hh=0.0,
+    skin=0.3,
+    min_dist=0.8,
+)
+
+# --------------------------------------------------------------------------------------
+# Aqueous NaCl: type 0 Na+, 1 Cl-, 2 O (SPC/E), 3 H
+# --------------------------------------------------------------------------------------
+KT_298 = 2.47772  # kJ/mol at 298 K
+AQ_PHYSICS = dict(
+    system="aq",
+    beta=1.0 / KT_298,
+    rc_lj=10.0,
+    rc_coul=10.0,
+    alpha=0.25,
+    kcoul=1389.35458,  # kJ A / (mol e^2)
+    kappa_sr=1.0,
+    q=[1.0, -1.0, -0.8476, 0.4238],
+    sig=[2.16, 4.83, 3.166, 0.0],
+    eps=[1.475, 0.0535, 0.650, 0.0],
+    mass=[22.99, 35.45, 15.9994, 1.008],
+    mvv2e=1.0e4,  # amu A^2 / fs^2 -> kJ/mol
+    dt=1.0,
+    w_max=3.0,
+    tau_t=100.0,
+    schedule="linear",
+    sched_n=1.0,
+    d_oh=1.0,
+    d_hh=2.0 * math.sin(math.radians(109.47) / 2.0),
+    skin=1.0,
+    min_dist=2.0,
+)
+
+
+def box_for(n_ions: int, rho: float) -> float:
+    return (n_ions / rho) ** (1.0 / 3.0)
+
+
+def lj_config(n_ions: int, rho: float, n_f: int, **extra) -> dict:
+    cfg = dict(LJ_PHYSICS)
+    cfg.update(n_ions=n_ions, n_pairs=n_ions // 2, rho=rho, L=box_for(n_ions, rho), n_f=n_f)
+    cfg.update(extra)
+    return cfg
+
+
+# The five workloads.  beta_mu values are the pair chemical potentials used for the
+# grand-canonical runs (estimated with fixed-N work sampling and the BAR equation).
+CONFIGS = {
+    "lj250": lj_config(250, 0.2, 100, trials=200, n_eq=1000, cap_pairs=256, beta_mu=-6.0),
+    "lj4000": lj_config(4000, 0.3, 500, trials=10000, n_eq=1000, cap_pairs=2304, chains=304,
+                        beta_mu=-6.0),
+}
+
+
+def _pick_far(rng, L, placed, n_new, min_dist, max_tries=200000):
+    """Random sequential placement with a minimum-image overlap check on a cell grid."""
+    pos = np.zeros((n_new, 3))
+    nc = max(1, int(L // min_dist))
+    cell = {}
+    for p in placed:
+        key = tuple((np.floor(p / L * nc).astype(int)) % nc)
+        cell.setdefault(key, []).append(p)
+    k = 0
+    tries = 0
+    while k < n_new:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("could not place atoms without overlap")
+        r = rng.random(3) * L
+        c = np.floor(r / L * nc).astype(int) % nc
+        ok = True
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    for q in cell.get(((c[0] + dx) % nc, (c[1] + dy) % nc, (c[2] + dz) % nc), ()):
+                        d = r - q
+                        d -= L * np.round(d / L)
+                        if d @ d < min_dist * min_dist:
+                            ok = False
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if not ok:
+                break
+        if ok:
+            pos[k] = r
+            cell.setdefault(tuple(c), []).append(r)
+            k += 1
+    return pos
+
+
+def lj_positions(n_pairs: int, L: float, seed: int, min_dist: float = 0.8) -> np.ndarray:
+    """Uniform random ion positions (interleaved cation/anion) with overlap rejection."""
+    rng = np.random.default_rng(seed)
+    return _pick_far(rng, L, [], 2 * n_pairs, min_dist)
+
+
+def batched_replicas(n_rep: int = 256, seed: int = 7, n_min: int = 100, n_max: int = 1000,
+                     rho_min: float = 0.1, rho_max: float = 0.4):
+    """Ion counts uniform in [n_min, n_max] rounded to even and densities uniform in
+    [rho_min, rho_max], one (n_ions, rho, L) triple per replica."""
+    rng = np.random.default_rng(seed)
+    n = rng.integers(n_min // 2, n_max // 2 + 1, size=n_rep) * 2
+    rho = rng.uniform(rho_min, rho_max, size=n_rep)
+    return [(int(n[i]), float(rho[i]), box_for(int(n[i]), float(rho[i]))) for i in range(n_rep)]
