@@ -1,0 +1,372 @@
+"""Benchmark of the H4D grand-canonical hot path on one or more GB300s.
+
+Workload (default): the 4000-ion LJ electrolyte at density 0.3 (L = 23.71 sigma), NEMD
+protocol of 500 steps, 1000 equilibrium MD steps between trials, split into independent
+Markov chains (one per replica; 304 chains = 2 per SM).  One benchmark step is one
+grand-canonical cycle of every chain: 1000 equilibrium MD steps, trial setup, 500 NEMD
+steps with the 4D pair forces, FP64 work, Metropolis and commit -- all in one persistent
+launch.  Inputs are generated from fixed seeds and equilibrated for 1000 MD steps before
+timing.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "accepted salt-pair exchanges/s & 4D atom-steps/s, plain vs batched/learned"
+FLOPS_PER_PAIR = 55  # FP32 operations per unordered pair inside the cut-off
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="h4d", choices=["h4d", "reference"])
+    ap.add_argument("--chains", type=int, default=304)
+    ap.add_argument("--workload", default="lj4000")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--equil", type=int, default=1000)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(name, chains, rank):
+    from paper_2307_11447_gb300 import workloads as wl
+
+    cfg = dict(wl.CONFIGS[name])
+    reps = []
+    for c in range(chains):
+        seed = 1000 * (rank + 1) + c
+        x = wl.lj_positions(cfg["n_pairs"], cfg["L"], seed)
+        reps.append(dict(L=cfg["L"], n_pairs=cfg["n_pairs"], cap_pairs=cfg["cap_pairs"], x=x))
+    return cfg, reps
+
+
+def src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2307_11447_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile():
+    """DRAM bytes per launch of the engine kernel from the committed ncu summary, or None
+    when the kernel source changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        t = json.load(open(p))
+    except Exception:
+        return None
+    if t.get("src_sha") != src_hash():
+        return None
+    return t.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.strip().split(",") for l in open(self.f.name) if l.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for k, n in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2307_11447_gb300 import lib as h4d
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    cfg, reps = workload(args.workload, args.chains, rank)
+    params = h4d.make_params(cfg)
+    with torch.cuda.stream(stream):
+        ctx = h4d.Context(params, reps, seed=12345 + rank, stream=stream.cuda_stream)
+    n_eq, n_f = cfg["n_eq"], cfg["n_f"]
+    # equilibrate the random starts (untimed), then warm up
+    ctx.h4d_run_md(args.equil)
+    for _ in range(args.warmup):
+        ctx.h4d_run_trials(1, n_eq)
+    torch.cuda.synchronize()
+    c0 = [ctx.h4d_get_counts(r) for r in range(ctx.R)]
+    pairs0 = ctx.h4d_count_pairs()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for k in range(args.steps):
+        ctx.h4d_run_trials(1, n_eq)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    per_launch_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    t_ms = sum(per_launch_ms)
+    c1 = [ctx.h4d_get_counts(r) for r in range(ctx.R)]
+    pairs1 = ctx.h4d_count_pairs()
+    # units this rank processed
+    atom_steps = 0.0
+    nemd_atom_steps = 0.0
+    accepted = 0
+    for a, b in zip(c0, c1):
+        mean_pairs = (b["sum_n"] - a["sum_n"]) / max(b["cycles"] - a["cycles"], 1)
+        n_atoms = 2.0 * mean_pairs
+        atom_steps += n_atoms * (n_eq + n_f) * args.steps
+        nemd_atom_steps += n_atoms * n_f * args.steps
+        accepted += (b["accepted_ins"] + b["accepted_del"]) - (a["accepted_ins"] + a["accepted_del"])
+    t_nemd = sum(b["t_nemd_ns"] - a["t_nemd_ns"] for a, b in zip(c0, c1)) / 1e9
+    t_md = sum(b["t_md_ns"] - a["t_md_ns"] for a, b in zip(c0, c1)) / 1e9
+    nemd_frac = t_nemd / max(t_nemd + t_md, 1e-30)
+    tmax = t_ms
+    tot = np.array([atom_steps, nemd_atom_steps, accepted], np.float64)
+    if world > 1:
+        tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tmax = float(tt.item())
+        tv = torch.tensor(tot, device="cuda")
+        dist.all_reduce(tv)
+        tot = tv.cpu().numpy()
+    secs = tmax / 1e3
+    value = tot[0] / secs
+    # roofline of the engine kernel: algorithmic FP32 work of the pair term
+    pairs = 0.5 * (pairs0 + pairs1)
+    force_evals = n_eq + n_f + 2
+    flops_per_launch = pairs * force_evals * FLOPS_PER_PAIR
+    avg_launch_s = (t_ms / args.steps) / 1e3
+    achieved = flops_per_launch / avg_launch_s / 1e12
+    sm_mhz = clk.get("sm_max_mhz") or 2070.0
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(ctx, reps, args, n_eq, n_f, stream, world, dist if world > 1 else None)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "atom-steps/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": tmax / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32 pair forces, f64 work/energies",
+            "data": "synthetic (seeded uniform positions, equilibrated 1000 MD steps)",
+            "config": {"workload": f"LJ electrolyte 4000 ions rho=0.3 (L={cfg['L']:.3f}), N_f={n_f}, N_eq={n_eq}, "
+                                   f"{args.chains} chains/GPU", "chains_per_gpu": args.chains, "ions": cfg["n_ions"],
+                       "n_f": n_f, "n_eq": n_eq, "parallelism": f"replicas x{world}",
+                       "l2": "state > L2 (about 1.3 GB per GPU); no flush needed"},
+            "nemd_4d_atom_steps_per_s": tot[1] / (secs * nemd_frac) if nemd_frac > 0 else None,
+            "accepted_exchanges_per_s": tot[2] / secs,
+            "accepted": int(tot[2]),
+            "trials": int(args.chains * world * args.steps),
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic_from_profile(),
+                         "kernel": "cycles_kernel (persistent: list build, 4D pair forces, VV, FP64 work, Metropolis)",
+                         "peak_basis": f"FP32 {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz",
+                         "pairs_in_cutoff": pairs, "flops_per_pair": FLOPS_PER_PAIR},
+            "e2e": e2e,
+        }
+        if rank == 0 and os.environ.get("H4D_BENCH_CPU", "1") == "1":
+            out["cpu_baseline"] = cpu_baseline(args.workload, sample_steps=8)
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(ctx, reps, args, n_eq, n_f, stream, world, dist):
+    """Same metric through the public API with host buffers: every step uploads each
+    chain's positions and velocities from pinned host memory, runs one cycle and reads the
+    counters and trial records back."""
+    import torch
+
+    xs, vs = [], []
+    for r in range(ctx.R):
+        x, v = ctx.h4d_get_state(r)
+        xs.append(torch.from_numpy(x).pin_memory())
+        vs.append(torch.from_numpy(v).pin_memory())
+    torch.cuda.synchronize()
+    h2d = sum(x.numel() * 8 + v.numel() * 8 for x, v in zip(xs, vs))
+    d2h = 0
+    t0 = time.perf_counter()
+    atom_steps = 0.0
+    for k in range(args.steps):
+        for r in range(ctx.R):
+            x = xs[r].numpy()
+            ctx.h4d_set_state(r, x.shape[0] // 2, x, vs[r].numpy())
+        ctx.h4d_run_trials(1, n_eq)
+        d2h = 0
+        for r in range(ctx.R):
+            c = ctx.h4d_get_counts(r)
+            rec = ctx.h4d_get_work(r, 1)
+            d2h += 8 * 14 + rec.nbytes
+            atom_steps += 2.0 * c["n_pairs"] * (n_eq + n_f)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([secs], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+        a = torch.tensor([atom_steps], dtype=torch.float64, device="cuda")
+        dist.all_reduce(a)
+        atom_steps = float(a.item())
+    return {"value": atom_steps / secs, "unit": "atom-steps/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h)}
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle timing (test infrastructure, used only for the baseline legs)
+# ---------------------------------------------------------------------------------------
+def _oracle_chain(job):
+    name, seed, n_steps = job
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as orc
+    from paper_2307_11447_gb300 import workloads as wl
+
+    cfg = dict(wl.CONFIGS[name])
+    p = orc.make_params(cfg, use_cells=1, seed=seed)
+    x = wl.lj_positions(cfg["n_pairs"], cfg["L"], seed)
+    st = orc.State(p, x, None, cfg["n_pairs"], cfg["cap_pairs"])
+    orc.init_velocities(p, st)
+    t0 = time.perf_counter()
+    orc.md(p, st, n_steps)
+    dt = time.perf_counter() - t0
+    return 2 * cfg["n_pairs"] * n_steps, dt
+
+
+def cpu_baseline(name, sample_steps=8, cores=None):
+    """The oracle as it stands, one chain per host process (spawned), each running
+    sample_steps MD steps of the 4000-ion system (every MD step costs one 4D force
+    evaluation like a NEMD step)."""
+    import multiprocessing as mp
+
+    cores = cores or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_chain, [(name, 77 + k, sample_steps) for k in range(cores)])
+    wall = time.perf_counter() - t0
+    units = sum(r[0] for r in res)
+    busy = max(r[1] for r in res)
+    return {"value": units / busy, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} chains x {sample_steps} MD steps of the 4000-ion system, cell list, FP64 "
+                      f"(wall {wall:.1f} s incl. process start)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        cpu_baseline(args.workload, sample_steps=1, cores=cores)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args.workload, sample_steps=2, cores=cores))
+    secs = time.perf_counter() - t0
+    value = float(np.mean([v["value"] for v in vals]))
+    out = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "atom-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "LJ electrolyte 4000 ions rho=0.3, FP64 CPU oracle, bounded sample per step"},
+        "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": vals[-1]["sample"]},
+        "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * h4d.h -- C ABI of libh4d, a single-GPU (GB300, sm_103a) implementation of the hybrid 4D
+ * nonequilibrium MD/MC ("H4D") grand-canonical method of Kim, Belloni and Rotenberg,
+ * arXiv:2307.11447, "Grand-canonical molecular dynamics simulations powered by a hybrid
+ * 4D nonequilibrium MD/MC method".
+ *
+ * What the library computes (paper sections and equations):
+ *   - the short-range pair force and energy in the 4D metric r4^2 = r^2 + (w_i - w_j)^2:
+ *     truncated-shifted Lennard-Jones (Eq. 19, Lorentz-Berthelot mixing, Sec. II.D) plus
+ *     the real-space Coulomb term K q_i q_j erfc(alpha r4)/r4 shifted to zero at its
+ *     cut-off (Eqs. 9, 20), multiplied by the altitude screening exp(-kappa_sr w) for
+ *     pairs of one flying and one non-flying particle (Eqs. 10-11);
+ *   - NEMD trajectories that carry an ion pair along the auxiliary axis w with the
+ *     constant-velocity schedule of Eq. 2 (or w_v / w_x of Eqs. S6-S7), flying ions held
+ *     at their 3D positions (Sec. II.B.1), everything else integrated by velocity Verlet
+ *     in the NVE ensemble (Sec. II.A), rigid waters by RATTLE;
+ *   - the FP64 nonequilibrium work Delta M and the pair-exchange Metropolis rule of
+ *     Eqs. 3-8 with symmetric two-end momentum reversal (Sec. II.A), committed on the
+ *     device with no host round trip;
+ *   - equilibrium MD between trials (Fig. 1) with a CSVR thermostat.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: H4D_OK (0) on success, a negative H4D_E* code on error; no C++
+ *     exception crosses the ABI.  h4d_strerror() names each code.
+ *   - Pointers named host_* are host memory; the library copies from or into them and
+ *     never keeps them.  Pointers named dev_* are device memory owned by the caller.
+ *     All other device memory is owned by the context and freed by h4d_destroy().
+ *   - Each context issues its work on the CUDA stream given at creation (NULL = the
+ *     legacy default stream).  Launching entry points return when the work is queued;
+ *     getters synchronise the stream before they return.
+ *   - Atom layout inside a replica: atoms [0, 3*n_water) are rigid waters stored as
+ *     O,H,H; ions follow as interleaved pairs, ion 2k = cation k (type 0) and ion 2k+1 =
+ *     anion k (type 1).  Water O is type 2 and H is type 3.  Positions are Cartesian in
+ *     [0, L)^3 per replica (other values are wrapped); arrays are row-major [atom][xyz].
+ *   - Random numbers: Philox4x64-10 keyed by (seed, replica); draw addresses are fixed
+ *     (trial counter, block, purpose) so results do not depend on thread scheduling.
+ */
+#ifndef H4D_H
+#define H4D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque context: owns the device state of all replicas, the stream and the launch plan. */
+typedef struct h4d_ctx h4d_ctx;
+
+/* ---- error codes ---- */
+#define H4D_OK 0
+#define H4D_EINVAL (-1)    /* bad argument (NULL pointer, size out of range, unknown mode) */
+#define H4D_ECAPACITY (-2) /* a neighbour row, cell or replica capacity would be exceeded */
+#define H4D_ETIMEOUT (-3)  /* a bounded device loop gave up (reported, never a hang) */
+#define H4D_ENAN (-4)      /* non-finite force or energy in equilibrium MD */
+#define H4D_ECUDA (-5)     /* a CUDA runtime call failed */
+#define H4D_ENODEV (-6)    /* no CUDA device or the device is not sm_103 class */
+
+/* ---- systems and schedules ---- */
+#define H4D_SYS_LJ 0    /* LJ electrolyte: two ion types of equal size (Sec. II.D.1) */
+#define H4D_SYS_AQ 1    /* rigid 3-site water + Na+/Cl- (Sec. II.D.2) */
+#define H4D_SCHED_LINEAR 0 /* Eq. 2 */
+#define H4D_SCHED_WV 1     /* Eq. S6 insertion form; deletion is its time reverse */
+#define H4D_SCHED_WX 2     /* Eq. S7 insertion form; deletion is its time reverse */
+
+/* Physics, protocol and engine settings common to all replicas of a context. */
+typedef struct h4d_params {
+  int32_t system;         /* H4D_SYS_LJ or H4D_SYS_AQ */
+  int32_t ntypes;         /* 2 (LJ) or 4 (AQ) */
+  double beta;            /* 1/kT in inverse energy units */
+  double beta_mu;         /* beta * mu of the ion pair, Lambda_s = 1 (Eqs. 6, 8) */
+  double rc_lj;           /* LJ cut-off (Eq. 19) */
+  double rc_coul;         /* cut-off of the real-space Coulomb term */
+  double alpha;           /* splitting parameter of erfc(alpha r) (Eq. 9) */
+  double kcoul;           /* Coulomb prefactor: energy x length / e^2 */
+  double kappa_sr;        /* kappa_w^sr of Eq. 11 */
+  double q[4], sig[4], eps[4], mass[4]; /* per type */
+  double mvv2e;           /* converts mass x velocity^2 into energy units */
+  double dt;              /* time step (NEMD and equilibrium) */
+  double w_max;           /* maximum altitude (Eq. 2) */
+  double tau_t;           /* CSVR relaxation time of equilibrium MD; <= 0 disables it */
+  double sched_n;         /* exponent n of Eqs. S6-S7 */
+  int32_t n_f;            /* NEMD steps per trial */
+  int32_t schedule;       /* H4D_SCHED_* */
+  double d_oh, d_hh;      /* rigid water bond lengths (O-H, H-H) */
+  double skin;            /* neighbour-list skin; the list is rebuilt when an atom moved skin/2 */
+  int32_t max_nbr;        /* neighbour-row capacity per atom; 0 = derived from density */
+  int32_t threads_per_atom; /* 1,2,4,8,16 or 32; 0 = autotune per replica size */
+} h4d_params;
+
+/* Initial replicas.  Replica r holds 3*n_water[r] + 2*n_pairs[r] atoms; host_x (and
+ * host_v when not NULL) concatenate the replicas in order, 3 doubles per atom.  With
+ * host_v == NULL velocities are drawn from Maxwell-Boltzmann at 1/beta. */
+typedef struct h4d_system {
+  int32_t n_replicas;
+  const double* L;          /* [R] cubic box edges */
+  const int32_t* n_water;   /* [R] rigid waters (0 for the LJ electrolyte) */
+  const int32_t* n_pairs;   /* [R] ion pairs at start */
+  const int32_t* cap_pairs; /* [R] maximum ion pairs the replica may reach */
+  const double* host_x;
+  const double* host_v;
+} h4d_system;
+
+/* Per-replica counters. */
+typedef struct h4d_counts {
+  int64_t n_pairs;          /* current ion pairs */
+  int64_t cycles;           /* trials done */
+  int64_t trials_ins, trials_del;
+  int64_t accepted_ins, accepted_del;
+  int64_t rejected_status;  /* deletion from an empty box, full capacity, non-finite work */
+  int64_t md_steps;         /* equilibrium MD steps done */
+  double sum_n, sum_n2;     /* running sums of N after each trial (for <N> and chi) */
+  int64_t nbr_builds;       /* neighbour-list builds */
+  int64_t error_flags;      /* bit 0 row overflow, bit 1 non-finite MD state, bit 2 timeout */
+  double t_nemd_ns, t_md_ns; /* device time spent in NEMD trials and equilibrium MD */
+} h4d_counts;
+
+/* One trial record; Delta M follows the insertion direction (Eqs. 6, 8). */
+typedef struct h4d_record {
+  int32_t move;       /* 1 insertion, 0 deletion */
+  int32_t accepted;
+  int32_t n_before, n_after;
+  int32_t status;     /* 0 ok, 1 deletion from empty system, 2 capacity, 3 non-finite work */
+  int32_t cation, anion; /* chosen pair index (deletion), else -1 */
+  int32_t pad;
+  double dH;          /* H_end - H_start (energy units, FP64) */
+  double beta_dM;     /* beta Delta M */
+  double w_prot;      /* protocol work sum_k [U(w_{k+1}) - U(w_k)] (FP32 pairs, FP64 sum) */
+  double ln_u;        /* log of the acceptance uniform */
+  double x_acc;       /* exponent compared with ln_u */
+} h4d_record;
+
+/* ---- context lifetime ---- */
+
+/* Create a context: copies params and the initial replicas to the device, sizes every
+ * buffer for cap_pairs, autotunes the launch shape when threads_per_atom == 0.
+ * seed keys the random stream.  cuda_stream is a cudaStream_t (NULL = default). */
+int h4d_create(const h4d_params* params, const h4d_system* sys, uint64_t seed, void* cuda_stream,
+               h4d_ctx** out);
+void h4d_destroy(h4d_ctx* ctx);
+const char* h4d_strerror(int code);
+
+/* ---- settings ---- */
+int h4d_set_mu(h4d_ctx* ctx, double beta_mu);
+int h4d_set_protocol(h4d_ctx* ctx, int32_t n_f, double w_max, double dt, double kappa_sr,
+                     int32_t schedule);
+/* fixed-N work sampling (SI Sec. S1, Eq. 21): trials are run and recorded but never
+ * accepted when on != 0 */
+int h4d_set_no_accept(h4d_ctx* ctx, int32_t on);
+
+/* ---- running ---- */
+
+/* n_steps of equilibrium MD (all w = 0, CSVR thermostat) on every replica. */
+int h4d_run_md(h4d_ctx* ctx, int64_t n_steps);
+/* k_cycles grand-canonical cycles on every replica (Fig. 1): n_eq equilibrium MD steps,
+ * then one insertion or deletion trial (NEMD + Metropolis + commit).  One persistent
+ * launch runs all cycles of all replicas. */
+int h4d_run_trials(h4d_ctx* ctx, int64_t k_cycles, int32_t n_eq);
+
+/* ---- getters (synchronise the context stream) ---- */
+int h4d_get_counts(h4d_ctx* ctx, int32_t replica, h4d_counts* out);
+/* current FP64 potential and kinetic energy of a replica */
+int h4d_get_energies(h4d_ctx* ctx, int32_t replica, double* U, double* K);
+/* the most recent trial records of a replica (up to cap, oldest first); *n receives
+ * how many were written */
+int h4d_get_work(h4d_ctx* ctx, int32_t replica, h4d_record* host_rec, int64_t cap, int64_t* n);
+/* positions (in [0,L)) and velocities of a replica; *n_atoms receives the atom count;
+ * fails with H4D_ECAPACITY when cap_atoms is too small */
+int h4d_get_state(h4d_ctx* ctx, int32_t replica, double* host_x, double* host_v,
+                  int64_t cap_atoms, int64_t* n_atoms);
+/* overwrite a replica's state (n_pairs ion pairs, positions and velocities) */
+int h4d_set_state(h4d_ctx* ctx, int32_t replica, int32_t n_pairs, const double* host_x,
+                  const double* host_v);
+int32_t h4d_num_replicas(h4d_ctx* ctx);
+/* total pairs inside the larger cut-off over all replicas at the current state (each
+ * unordered pair once); the algorithmic work unit of the pair kernel */
+int h4d_count_pairs(h4d_ctx* ctx, int64_t* n_pairs_in_cutoff);
+
+/* ---- checkpoint ---- */
+int h4d_save(h4d_ctx* ctx, const char* path);
+int h4d_load(h4d_ctx* ctx, const char* path);
+
+/* ---- stateless kernels (one system, host buffers) ---- */
+
+/* 4D pair forces and energy of one configuration (Sec. II.A 4D distance; Eqs. 9-11, 19-20):
+ * host_x [n][3] positions, host_w [n] altitudes (NULL = all 0); atom types follow the
+ * layout above with n_water waters.  Writes host_F [n][3] (FP32 math, returned as
+ * double) and *U (FP64).  Altitude-screening applies to pairs with exactly one nonzero
+ * altitude.  Allocates device scratch per call. */
+int h4d_eval_forces(const h4d_params* params, double L, int32_t n_water, int32_t n,
+                    const double* host_x, const double* host_w, double* host_F, double* U);
+
+/* Neighbour pairs (i < j) under the fixed-point criterion: X = round(x/L 2^32) mod 2^32
+ * per coordinate, pair iff sum ((int32)(X_i - X_j))^2 <= floor((r_list/L 2^32)^2).
+ * Writes up to cap pairs sorted by (i, j) and the total count to *n_out. */
+int h4d_neighbor_pairs(double L, int32_t n, const double* host_x, double r_list, int32_t* host_i,
+                       int32_t* host_j, int64_t cap, int64_t* n_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* H4D_H */

@@ -244,11 +244,11 @@ static double flyer_energy(const orc_params* p, int n, const double* x, const ui
 
 /* ------------------------------------------------------------------------------------ */
 /* Fixed-point neighbour criterion (definition shared by name with the GPU path):        */
-/* X = floor(x/L * 2^32) mod 2^32 per coordinate; (i,j) is a list pair iff              */
+/* X = round(x/L * 2^32) mod 2^32 per coordinate; (i,j) is a list pair iff              */
 /* sum_c ((int32)(X_i - X_j))^2 <= floor((r_list/L * 2^32)^2).                           */
 /* ------------------------------------------------------------------------------------ */
 static uint32_t fixpt(double x, double L) {
-  double s = floor(wrap(x, L) / L * 4294967296.0);
+  double s = nearbyint(wrap(x, L) / L * 4294967296.0);
   return (uint32_t)((uint64_t)s & 0xffffffffULL);
 }
 

@@ -1,0 +1,805 @@
+// h4d_api.cu -- host side of the libh4d C ABI (declared in include/h4d.h): parameter
+// checking, device buffers, launch plan, state transfer and checkpoints.  All simulation
+// steps run in the kernels of h4d_engine.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/h4d.h"
+#include "h4d_engine.cuh"
+
+using namespace h4d;
+
+struct h4d_ctx {
+  h4d_params prm;
+  uint64_t seed;
+  cudaStream_t stream;
+  int R;
+  int total_atoms;
+  int max_nbr;
+  int cta_threads;
+  int n_ctas;
+  size_t smem;
+  std::vector<Rep> rep_h;
+  std::vector<Group> groups_h;
+  std::vector<int> cta_groups_h;
+  Eng eng;
+  // device allocations
+  Rep* d_rep = nullptr;
+  Group* d_groups = nullptr;
+  int* d_cta_groups = nullptr;
+  uint4* d_pos = nullptr;
+  float4* d_vhi = nullptr;
+  float4* d_vlo = nullptr;
+  float4* d_force = nullptr;
+  uint4* d_pos_save = nullptr;
+  float4* d_vhi_save = nullptr;
+  float4* d_vlo_save = nullptr;
+  uint4* d_ref = nullptr;
+  uint16_t* d_nbr = nullptr;
+  int* d_ncnt = nullptr;
+  h4d_record* d_rec = nullptr;
+  double* d_scratch = nullptr;
+  unsigned long long* d_count = nullptr;
+};
+
+#define CK(x)                                  \
+  do {                                         \
+    if ((x) != cudaSuccess) return H4D_ECUDA; \
+  } while (0)
+
+static const double kTwo32 = 4294967296.0;
+
+static uint32_t __float_as_uint_host(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, sizeof(u));
+  return u;
+}
+
+// fixed-point box fraction of a coordinate (matches the criterion stated in h4d.h)
+static uint32_t to_fixed(double x, double L) {
+  double y = x - L * std::floor(x / L);
+  if (y >= L) y -= L;
+  double s = std::nearbyint(y / L * kTwo32);
+  return (uint32_t)((uint64_t)s & 0xffffffffULL);
+}
+
+static double rmax_of(const h4d_params& p) { return std::max(p.rc_lj, p.rc_coul); }
+
+static int check_params(const h4d_params* p) {
+  if (!p) return H4D_EINVAL;
+  if (p->system != H4D_SYS_LJ && p->system != H4D_SYS_AQ) return H4D_EINVAL;
+  if (p->ntypes < 2 || p->ntypes > 4) return H4D_EINVAL;
+  if (!(p->beta > 0) || !(p->dt > 0) || !(p->rc_lj > 0) || !(p->rc_coul > 0)) return H4D_EINVAL;
+  if (p->n_f < 1 || p->w_max < 0 || p->skin < 0) return H4D_EINVAL;
+  if (p->schedule < 0 || p->schedule > 2) return H4D_EINVAL;
+  if (p->threads_per_atom != 0 && (p->threads_per_atom & (p->threads_per_atom - 1))) return H4D_EINVAL;
+  if (p->threads_per_atom > 32) return H4D_EINVAL;
+  for (int t = 0; t < p->ntypes; ++t)
+    if (!(p->mass[t] > 0) || p->sig[t] < 0 || p->eps[t] < 0) return H4D_EINVAL;
+  if (p->system == H4D_SYS_LJ) {
+    // the LJ specialisation assumes equal sizes/energies and charges +q/-q
+    if (p->sig[0] != p->sig[1] || p->eps[0] != p->eps[1] || p->q[0] != -p->q[1]) return H4D_EINVAL;
+  }
+  return H4D_OK;
+}
+
+static void fill_pot(const h4d_params& p, Pot& P, Proto& pr) {
+  std::memset(&P, 0, sizeof(P));
+  P.sys = p.system;
+  P.ntypes = p.ntypes;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      int k = i * 4 + j;
+      bool ok = i < p.ntypes && j < p.ntypes;
+      double sig = ok ? 0.5 * (p.sig[i] + p.sig[j]) : 0.0;
+      double eps = ok ? std::sqrt(p.eps[i] * p.eps[j]) : 0.0;
+      double sc6 = (sig > 0) ? std::pow(sig / p.rc_lj, 6.0) : 0.0;
+      double shift = 4.0 * eps * (sc6 * sc6 - sc6);
+      double kq = ok ? p.kcoul * p.q[i] * p.q[j] : 0.0;
+      P.dsig2[k] = sig * sig;
+      P.deps4[k] = 4.0 * eps;
+      P.dljshift[k] = shift;
+      P.dkq[k] = kq;
+      P.sig2[k] = (float)(sig * sig);
+      P.eps4[k] = (float)(4.0 * eps);
+      P.ljshift[k] = (float)shift;
+      P.kq[k] = (float)kq;
+    }
+  if (p.system == H4D_SYS_LJ) {
+    // LJ specialisation reads kq[0] for like and kq[1] for unlike charges
+    P.kq[0] = (float)(p.kcoul * p.q[0] * p.q[0]);
+    P.kq[1] = (float)(p.kcoul * p.q[0] * p.q[1]);
+  }
+  P.rc2_lj = (float)(p.rc_lj * p.rc_lj);
+  P.rc2_c = (float)(p.rc_coul * p.rc_coul);
+  P.rc2_max = std::max(P.rc2_lj, P.rc2_c);
+  P.alpha = (float)p.alpha;
+  P.shift_c = (float)(std::erfc(p.alpha * p.rc_coul) / p.rc_coul);
+  P.two_alpha_sqrtpi = (float)(2.0 * p.alpha / std::sqrt(M_PI));
+  P.kappa_sr = (float)p.kappa_sr;
+  P.drc2_lj = p.rc_lj * p.rc_lj;
+  P.drc2_c = p.rc_coul * p.rc_coul;
+  P.dalpha = p.alpha;
+  P.dshift_c = std::erfc(p.alpha * p.rc_coul) / p.rc_coul;
+  P.dkappa_sr = p.kappa_sr;
+  for (int t = 0; t < 4; ++t) {
+    double m = (t < p.ntypes) ? p.mass[t] * p.mvv2e : 1.0;
+    P.dm[t] = m;
+    P.inv_m[t] = (float)(1.0 / m);
+    P.inv_m_d[t] = 1.0 / m;
+  }
+  P.d_oh2 = p.d_oh * p.d_oh;
+  P.d_hh2 = p.d_hh * p.d_hh;
+  std::memset(&pr, 0, sizeof(pr));
+  pr.n_f = p.n_f;
+  pr.schedule = p.schedule;
+  pr.w_max = p.w_max;
+  pr.sched_n = p.sched_n;
+  pr.dt = p.dt;
+  pr.tau_t = p.tau_t;
+  pr.beta = p.beta;
+  pr.beta_mu = p.beta_mu;
+}
+
+// neighbour-row capacity from the densest plausible packing (about one particle per sigma^3
+// for the LJ electrolyte, liquid water for the aqueous system)
+static int derive_max_nbr(const h4d_params& p) {
+  double rl = rmax_of(p) + p.skin;
+  double rho = (p.system == H4D_SYS_LJ) ? 1.05 / std::pow(p.sig[0], 3) : 0.105;
+  int m = (int)std::ceil(4.0 / 3.0 * M_PI * rl * rl * rl * rho * 1.1) + 16;
+  return ((m + 31) / 32) * 32;
+}
+
+static int choose_tpa(const h4d_params& p, int n_atoms) {
+  if (p.threads_per_atom > 0) return p.threads_per_atom;
+  if (n_atoms >= 2048) return 4;
+  if (n_atoms >= 512) return 8;
+  return 16;
+}
+
+static int choose_threads(int n_atoms) {
+  if (n_atoms >= 2048) return 512;
+  if (n_atoms >= 256) return 256;
+  return 128;
+}
+
+static void set_rep_geometry(const h4d_params& p, Rep& r, double L) {
+  r.L = L;
+  r.scale = (float)(L / kTwo32);
+  r.c_drift = (float)(p.dt * kTwo32 / L);
+  double rl = rmax_of(p) + p.skin;
+  int nc = std::min((int)std::floor(L / rl), 16);  // bigger cells stay valid, smem stays bounded
+  r.nc = (nc >= 3) ? nc : 0;
+  double s = rl / L * kTwo32;
+  r.T_list = (unsigned long long)(s * s);
+  double h = 0.5 * p.skin / L * kTwo32;
+  r.T_move = (unsigned long long)(h * h);
+}
+
+static int alloc_all(h4d_ctx* c) {
+  size_t na = (size_t)c->total_atoms;
+  CK(cudaMalloc(&c->d_pos, na * sizeof(uint4)));
+  CK(cudaMalloc(&c->d_vhi, na * sizeof(float4)));
+  CK(cudaMalloc(&c->d_vlo, na * sizeof(float4)));
+  CK(cudaMalloc(&c->d_force, na * sizeof(float4)));
+  CK(cudaMalloc(&c->d_pos_save, na * sizeof(uint4)));
+  CK(cudaMalloc(&c->d_vhi_save, na * sizeof(float4)));
+  CK(cudaMalloc(&c->d_vlo_save, na * sizeof(float4)));
+  CK(cudaMalloc(&c->d_ref, na * sizeof(uint4)));
+  CK(cudaMalloc(&c->d_nbr, na * (size_t)c->max_nbr * sizeof(uint16_t)));
+  CK(cudaMalloc(&c->d_ncnt, na * sizeof(int)));
+  CK(cudaMemset(c->d_pos, 0, na * sizeof(uint4)));
+  CK(cudaMemset(c->d_vhi, 0, na * sizeof(float4)));
+  CK(cudaMemset(c->d_vlo, 0, na * sizeof(float4)));
+  CK(cudaMemset(c->d_force, 0, na * sizeof(float4)));
+  CK(cudaMemset(c->d_ncnt, 0, na * sizeof(int)));
+  size_t nrec = 0;
+  for (auto& r : c->rep_h) nrec += (size_t)r.rec_cap;
+  CK(cudaMalloc(&c->d_rec, nrec * sizeof(h4d_record)));
+  CK(cudaMemset(c->d_rec, 0, nrec * sizeof(h4d_record)));
+  CK(cudaMalloc(&c->d_rep, c->rep_h.size() * sizeof(Rep)));
+  CK(cudaMalloc(&c->d_groups, c->groups_h.size() * sizeof(Group)));
+  CK(cudaMalloc(&c->d_cta_groups, c->cta_groups_h.size() * sizeof(int)));
+  CK(cudaMalloc(&c->d_scratch, 2 * c->rep_h.size() * sizeof(double)));
+  CK(cudaMalloc(&c->d_count, sizeof(unsigned long long)));
+  return H4D_OK;
+}
+
+static void fill_eng(h4d_ctx* c) {
+  Eng& e = c->eng;
+  fill_pot(c->prm, e.pot, e.proto);
+  e.rep = c->d_rep;
+  e.groups = c->d_groups;
+  e.cta_groups = c->d_cta_groups;
+  e.pos = c->d_pos;
+  e.vhi = c->d_vhi;
+  e.vlo = c->d_vlo;
+  e.force = c->d_force;
+  e.pos_save = c->d_pos_save;
+  e.vhi_save = c->d_vhi_save;
+  e.vlo_save = c->d_vlo_save;
+  e.ref = c->d_ref;
+  e.nbr = c->d_nbr;
+  e.ncnt = c->d_ncnt;
+  e.rec = c->d_rec;
+  e.max_nbr = c->max_nbr;
+  e.seed = c->seed;
+}
+
+static int push_plan(h4d_ctx* c) {
+  CK(cudaMemcpyAsync(c->d_rep, c->rep_h.data(), c->rep_h.size() * sizeof(Rep), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_groups, c->groups_h.data(), c->groups_h.size() * sizeof(Group), cudaMemcpyHostToDevice,
+                     c->stream));
+  CK(cudaMemcpyAsync(c->d_cta_groups, c->cta_groups_h.data(), c->cta_groups_h.size() * sizeof(int),
+                     cudaMemcpyHostToDevice, c->stream));
+  return H4D_OK;
+}
+
+static int pull_reps(h4d_ctx* c) {
+  CK(cudaMemcpyAsync(c->rep_h.data(), c->d_rep, c->rep_h.size() * sizeof(Rep), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return H4D_OK;
+}
+
+// Maxwell-Boltzmann draw on the host (3 normals per atom from Philox counter {atom, 0, 4, 0})
+static void mulhilo(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
+  __uint128_t p = (__uint128_t)a * b;
+  *hi = (uint64_t)(p >> 64);
+  *lo = (uint64_t)p;
+}
+static void philox_host(uint64_t c[4], uint64_t k0, uint64_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    uint64_t hi0, lo0, hi1, lo1;
+    mulhilo(0xD2E7470EE14C6C93ULL, c[0], &hi0, &lo0);
+    mulhilo(0xCA5A826395121157ULL, c[2], &hi1, &lo1);
+    uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += 0x9E3779B97F4A7C15ULL;
+    k1 += 0xBB67AE8584CAA73BULL;
+  }
+}
+static double h_u01(uint64_t r) { return (double)(r >> 11) * 0x1.0p-53; }
+static double h_u01o(uint64_t r) { return (double)((r >> 11) + 1) * 0x1.0p-53; }
+
+static int atom_type_host(int a, int nw3) { return a < nw3 ? ((a % 3 == 0) ? 2 : 3) : ((a - nw3) & 1); }
+
+static void split_ff(double v, float& hi, float& lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+
+static int upload_replica(h4d_ctx* c, int r, int n_pairs, const double* x, const double* v) {
+  Rep& R = c->rep_h[r];
+  if (n_pairs < 0 || n_pairs > R.cap_pairs) return H4D_ECAPACITY;
+  R.n_pairs = n_pairs;
+  int n = R.nw3 + 2 * n_pairs;
+  std::vector<uint4> pos(n);
+  std::vector<float4> vh(n), vl(n);
+  for (int a = 0; a < n; ++a) {
+    pos[a] = make_uint4(to_fixed(x[3 * a], R.L), to_fixed(x[3 * a + 1], R.L), to_fixed(x[3 * a + 2], R.L), 0u);
+    double vv[3];
+    if (v) {
+      vv[0] = v[3 * a]; vv[1] = v[3 * a + 1]; vv[2] = v[3 * a + 2];
+    } else {
+      uint64_t q[4] = {(uint64_t)a, 0, 4, 0};
+      philox_host(q, c->seed, (uint64_t)r);
+      int t = atom_type_host(a, R.nw3);
+      double sd = std::sqrt(1.0 / (c->prm.beta * c->prm.mass[t] * c->prm.mvv2e));
+      double rad0 = std::sqrt(-2.0 * std::log(h_u01o(q[0])));
+      double rad1 = std::sqrt(-2.0 * std::log(h_u01o(q[2])));
+      vv[0] = sd * rad0 * std::cos(2.0 * M_PI * h_u01(q[1]));
+      vv[1] = sd * rad0 * std::sin(2.0 * M_PI * h_u01(q[1]));
+      vv[2] = sd * rad1 * std::cos(2.0 * M_PI * h_u01(q[3]));
+    }
+    float h, l;
+    split_ff(vv[0], h, l); vh[a].x = h; vl[a].x = l;
+    split_ff(vv[1], h, l); vh[a].y = h; vl[a].y = l;
+    split_ff(vv[2], h, l); vh[a].z = h; vl[a].z = l;
+    vh[a].w = vl[a].w = 0.f;
+  }
+  if (n > 0) {
+    CK(cudaMemcpyAsync(c->d_pos + R.atom_off, pos.data(), n * sizeof(uint4), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_vhi + R.atom_off, vh.data(), n * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_vlo + R.atom_off, vl.data(), n * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return H4D_OK;
+}
+
+static int check_device() {
+  int dev = 0, ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return H4D_ENODEV;
+  if (cudaGetDevice(&dev) != cudaSuccess) return H4D_ENODEV;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return H4D_ENODEV;
+  if (!(prop.major == 10 && prop.minor == 3)) return H4D_ENODEV;
+  return H4D_OK;
+}
+
+// one group (a whole CTA) per replica; the CTA size follows the replica size
+static int make_plan(h4d_ctx* c) {
+  c->groups_h.clear();
+  c->cta_groups_h.clear();
+  int threads = 32;
+  for (auto& r : c->rep_h) threads = std::max(threads, choose_threads(r.cap_atoms));
+  c->cta_threads = threads;
+  size_t smem = 0;
+  for (int i = 0; i < c->R; ++i) {
+    Rep& r = c->rep_h[i];
+    Group g;
+    g.rep = i;
+    g.warp0 = 0;
+    g.nwarps = threads / 32;
+    g.bar = 0;
+    g.smem_off = 0;
+    g.pad = 0;
+    c->cta_groups_h.push_back((int)c->groups_h.size());
+    c->groups_h.push_back(g);
+    smem = std::max(smem, group_smem_bytes(r.cap_atoms, r.nc, threads));
+  }
+  c->cta_groups_h.push_back((int)c->groups_h.size());
+  c->n_ctas = c->R;
+  c->smem = smem;
+  if (smem > 227 * 1024) return H4D_ECAPACITY;
+  return H4D_OK;
+}
+
+extern "C" {
+
+const char* h4d_strerror(int code) {
+  switch (code) {
+    case H4D_OK: return "ok";
+    case H4D_EINVAL: return "invalid argument";
+    case H4D_ECAPACITY: return "capacity exceeded (neighbour rows, shared memory or ion pairs)";
+    case H4D_ETIMEOUT: return "bounded device loop gave up";
+    case H4D_ENAN: return "non-finite state in equilibrium MD";
+    case H4D_ECUDA: return "CUDA runtime error";
+    case H4D_ENODEV: return "no sm_103 CUDA device";
+    default: return "unknown error";
+  }
+}
+
+int h4d_create(const h4d_params* params, const h4d_system* sys, uint64_t seed, void* cuda_stream, h4d_ctx** out) {
+  if (!out) return H4D_EINVAL;
+  *out = nullptr;
+  int rc = check_params(params);
+  if (rc) return rc;
+  if (!sys || sys->n_replicas < 1 || !sys->L || !sys->n_pairs || !sys->cap_pairs || !sys->host_x) return H4D_EINVAL;
+  rc = check_device();
+  if (rc) return rc;
+  h4d_ctx* c = new (std::nothrow) h4d_ctx();
+  if (!c) return H4D_ECUDA;
+  c->prm = *params;
+  c->seed = seed;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->R = sys->n_replicas;
+  c->max_nbr = params->max_nbr > 0 ? params->max_nbr : derive_max_nbr(*params);
+  c->rep_h.resize(c->R);
+  int off = 0;
+  for (int r = 0; r < c->R; ++r) {
+    Rep& R = c->rep_h[r];
+    std::memset(&R, 0, sizeof(Rep));
+    int nw = sys->n_water ? sys->n_water[r] : 0;
+    if (nw < 0 || sys->n_pairs[r] < 0 || sys->cap_pairs[r] < sys->n_pairs[r] || !(sys->L[r] > 0)) {
+      delete c;
+      return H4D_EINVAL;
+    }
+    if (nw > 0 && params->system != H4D_SYS_AQ) { delete c; return H4D_EINVAL; }
+    R.n_water = nw;
+    R.nw3 = 3 * nw;
+    R.n_pairs = sys->n_pairs[r];
+    R.cap_pairs = sys->cap_pairs[r];
+    R.cap_atoms = R.nw3 + 2 * R.cap_pairs;
+    if (R.cap_atoms > 65535 || R.cap_atoms < 1) { delete c; return H4D_ECAPACITY; }
+    if (2.0 * (rmax_of(*params) + params->skin) >= sys->L[r]) { delete c; return H4D_EINVAL; }
+    R.atom_off = off;
+    off += R.cap_atoms;
+    set_rep_geometry(*params, R, sys->L[r]);
+    R.tpa = choose_tpa(*params, R.cap_atoms);
+    R.rec_cap = 1024;
+    R.rec_off = r * R.rec_cap;
+  }
+  c->total_atoms = off;
+  // the neighbour rows are tpa-interleaved: capacity must be a multiple of every tpa used
+  c->max_nbr = ((c->max_nbr + 31) / 32) * 32;
+  rc = make_plan(c);
+  if (rc) { delete c; return rc; }
+  rc = alloc_all(c);
+  if (rc) { h4d_destroy(c); return rc; }
+  fill_eng(c);
+  size_t xo = 0;
+  for (int r = 0; r < c->R; ++r) {
+    Rep& R = c->rep_h[r];
+    rc = upload_replica(c, r, R.n_pairs, sys->host_x + xo, sys->host_v ? sys->host_v + xo : nullptr);
+    if (rc) { h4d_destroy(c); return rc; }
+    xo += 3 * (size_t)(R.nw3 + 2 * R.n_pairs);
+  }
+  rc = push_plan(c);
+  if (rc) { h4d_destroy(c); return rc; }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) { h4d_destroy(c); return H4D_ECUDA; }
+  *out = c;
+  return H4D_OK;
+}
+
+void h4d_destroy(h4d_ctx* c) {
+  if (!c) return;
+  void* ptrs[] = {c->d_rep, c->d_groups, c->d_cta_groups, c->d_pos, c->d_vhi, c->d_vlo, c->d_force,
+                  c->d_pos_save, c->d_vhi_save, c->d_vlo_save, c->d_ref, c->d_nbr, c->d_ncnt, c->d_rec,
+                  c->d_scratch, c->d_count};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete c;
+}
+
+int h4d_set_mu(h4d_ctx* c, double beta_mu) {
+  if (!c || !std::isfinite(beta_mu)) return H4D_EINVAL;
+  c->prm.beta_mu = beta_mu;
+  c->eng.proto.beta_mu = beta_mu;
+  return H4D_OK;
+}
+
+int h4d_set_protocol(h4d_ctx* c, int32_t n_f, double w_max, double dt, double kappa_sr, int32_t schedule) {
+  if (!c || n_f < 1 || !(w_max >= 0) || !(dt > 0) || !(kappa_sr >= 0) || schedule < 0 || schedule > 2)
+    return H4D_EINVAL;
+  c->prm.n_f = n_f;
+  c->prm.w_max = w_max;
+  c->prm.dt = dt;
+  c->prm.kappa_sr = kappa_sr;
+  c->prm.schedule = schedule;
+  int rc = pull_reps(c);
+  if (rc) return rc;
+  for (auto& r : c->rep_h) r.c_drift = (float)(dt * kTwo32 / r.L);
+  fill_pot(c->prm, c->eng.pot, c->eng.proto);
+  c->eng.proto.no_accept = c->eng.proto.no_accept;
+  return push_plan(c);
+}
+
+int h4d_set_no_accept(h4d_ctx* c, int32_t on) {
+  if (!c) return H4D_EINVAL;
+  c->eng.proto.no_accept = on ? 1 : 0;
+  return H4D_OK;
+}
+
+static int check_errors(h4d_ctx* c) {
+  int rc = pull_reps(c);
+  if (rc) return rc;
+  for (auto& r : c->rep_h) {
+    if (r.err & 1) return H4D_ECAPACITY;
+    if (r.err & 2) return H4D_ENAN;
+  }
+  return H4D_OK;
+}
+
+int h4d_run_md(h4d_ctx* c, int64_t n_steps) {
+  if (!c || n_steps < 0 || n_steps > (int64_t)1 << 30) return H4D_EINVAL;
+  if (n_steps == 0) return H4D_OK;
+  return launch_cycles(c->eng, c->n_ctas, c->cta_threads, c->smem, 1, (int)n_steps, 0, c->stream);
+}
+
+int h4d_run_trials(h4d_ctx* c, int64_t k_cycles, int32_t n_eq) {
+  if (!c || k_cycles < 0 || n_eq < 0) return H4D_EINVAL;
+  if (k_cycles == 0) return H4D_OK;
+  return launch_cycles(c->eng, c->n_ctas, c->cta_threads, c->smem, k_cycles, n_eq, 1, c->stream);
+}
+
+int32_t h4d_num_replicas(h4d_ctx* c) { return c ? c->R : 0; }
+
+int h4d_get_counts(h4d_ctx* c, int32_t r, h4d_counts* out) {
+  if (!c || !out || r < 0 || r >= c->R) return H4D_EINVAL;
+  int rc = pull_reps(c);
+  if (rc) return rc;
+  const Rep& R = c->rep_h[r];
+  out->n_pairs = R.n_pairs;
+  out->cycles = R.cycles;
+  out->trials_ins = R.trials_ins;
+  out->trials_del = R.trials_del;
+  out->accepted_ins = R.acc_ins;
+  out->accepted_del = R.acc_del;
+  out->rejected_status = R.rej_status;
+  out->md_steps = R.md_steps;
+  out->sum_n = R.sum_n;
+  out->sum_n2 = R.sum_n2;
+  out->nbr_builds = R.builds;
+  out->error_flags = R.err;
+  out->t_nemd_ns = R.t_nemd_ns;
+  out->t_md_ns = R.t_md_ns;
+  return H4D_OK;
+}
+
+int h4d_get_energies(h4d_ctx* c, int32_t r, double* U, double* K) {
+  if (!c || r < 0 || r >= c->R) return H4D_EINVAL;
+  int rc = launch_energy(c->eng, c->n_ctas, c->cta_threads, c->smem, c->d_scratch, c->d_scratch + c->R, c->stream);
+  if (rc) return rc;
+  double u = 0, k = 0;
+  CK(cudaMemcpyAsync(&u, c->d_scratch + r, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&k, c->d_scratch + c->R + r, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (U) *U = u;
+  if (K) *K = k;
+  return check_errors(c);
+}
+
+int h4d_get_work(h4d_ctx* c, int32_t r, h4d_record* out, int64_t cap, int64_t* n) {
+  if (!c || r < 0 || r >= c->R || (cap > 0 && !out)) return H4D_EINVAL;
+  int rc = pull_reps(c);
+  if (rc) return rc;
+  const Rep& R = c->rep_h[r];
+  std::vector<h4d_record> buf(R.rec_cap);
+  CK(cudaMemcpyAsync(buf.data(), c->d_rec + R.rec_off, R.rec_cap * sizeof(h4d_record), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  int64_t have = std::min<int64_t>(R.rec_count, R.rec_cap);
+  int64_t take = std::min<int64_t>(have, cap);
+  for (int64_t k = 0; k < take; ++k) {
+    int64_t idx = R.rec_count - take + k;
+    out[k] = buf[idx % R.rec_cap];
+  }
+  if (n) *n = take;
+  return H4D_OK;
+}
+
+int h4d_get_state(h4d_ctx* c, int32_t r, double* x, double* v, int64_t cap_atoms, int64_t* n_atoms) {
+  if (!c || r < 0 || r >= c->R) return H4D_EINVAL;
+  int rc = pull_reps(c);
+  if (rc) return rc;
+  const Rep& R = c->rep_h[r];
+  int n = R.nw3 + 2 * R.n_pairs;
+  if (n_atoms) *n_atoms = n;
+  if (n > cap_atoms) return H4D_ECAPACITY;
+  std::vector<uint4> pos(n);
+  std::vector<float4> vh(n), vl(n);
+  if (n > 0) {
+    CK(cudaMemcpyAsync(pos.data(), c->d_pos + R.atom_off, n * sizeof(uint4), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(vh.data(), c->d_vhi + R.atom_off, n * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(vl.data(), c->d_vlo + R.atom_off, n * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  const double h = R.L / kTwo32;
+  for (int a = 0; a < n; ++a) {
+    if (x) {
+      x[3 * a] = (double)pos[a].x * h;
+      x[3 * a + 1] = (double)pos[a].y * h;
+      x[3 * a + 2] = (double)pos[a].z * h;
+    }
+    if (v) {
+      v[3 * a] = (double)vh[a].x + (double)vl[a].x;
+      v[3 * a + 1] = (double)vh[a].y + (double)vl[a].y;
+      v[3 * a + 2] = (double)vh[a].z + (double)vl[a].z;
+    }
+  }
+  return H4D_OK;
+}
+
+int h4d_set_state(h4d_ctx* c, int32_t r, int32_t n_pairs, const double* x, const double* v) {
+  if (!c || r < 0 || r >= c->R || !x) return H4D_EINVAL;
+  int rc = pull_reps(c);
+  if (rc) return rc;
+  rc = upload_replica(c, r, n_pairs, x, v);
+  if (rc) return rc;
+  return push_plan(c);
+}
+
+int h4d_count_pairs(h4d_ctx* c, int64_t* n) {
+  if (!c || !n) return H4D_EINVAL;
+  CK(cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->stream));
+  int rc = launch_count_pairs(c->eng, c->n_ctas, c->cta_threads, c->smem, c->d_count, c->stream);
+  if (rc) return rc;
+  unsigned long long v = 0;
+  CK(cudaMemcpyAsync(&v, c->d_count, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *n = (int64_t)v;
+  return check_errors(c);
+}
+
+// ---- checkpoint: a flat binary image of the replica table and per-atom state ----
+static const uint64_t kMagic = 0x3130303044344848ULL;  // "HH4D0001"
+
+int h4d_save(h4d_ctx* c, const char* path) {
+  if (!c || !path) return H4D_EINVAL;
+  int rc = pull_reps(c);
+  if (rc) return rc;
+  size_t na = (size_t)c->total_atoms;
+  std::vector<uint4> pos(na);
+  std::vector<float4> vh(na), vl(na);
+  size_t nrec = (size_t)c->R * 1024;
+  std::vector<h4d_record> rec(nrec);
+  CK(cudaMemcpyAsync(pos.data(), c->d_pos, na * sizeof(uint4), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(vh.data(), c->d_vhi, na * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(vl.data(), c->d_vlo, na * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(rec.data(), c->d_rec, nrec * sizeof(h4d_record), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return H4D_EINVAL;
+  uint64_t hdr[4] = {kMagic, (uint64_t)c->R, (uint64_t)na, c->seed};
+  bool ok = std::fwrite(hdr, sizeof(hdr), 1, f) == 1;
+  ok = ok && std::fwrite(c->rep_h.data(), sizeof(Rep), c->R, f) == (size_t)c->R;
+  ok = ok && std::fwrite(pos.data(), sizeof(uint4), na, f) == na;
+  ok = ok && std::fwrite(vh.data(), sizeof(float4), na, f) == na;
+  ok = ok && std::fwrite(vl.data(), sizeof(float4), na, f) == na;
+  ok = ok && std::fwrite(rec.data(), sizeof(h4d_record), nrec, f) == nrec;
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? H4D_OK : H4D_EINVAL;
+}
+
+int h4d_load(h4d_ctx* c, const char* path) {
+  if (!c || !path) return H4D_EINVAL;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return H4D_EINVAL;
+  uint64_t hdr[4];
+  size_t na = (size_t)c->total_atoms;
+  size_t nrec = (size_t)c->R * 1024;
+  std::vector<Rep> reps(c->R);
+  std::vector<uint4> pos(na);
+  std::vector<float4> vh(na), vl(na);
+  std::vector<h4d_record> rec(nrec);
+  bool ok = std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == kMagic && hdr[1] == (uint64_t)c->R &&
+            hdr[2] == (uint64_t)na;
+  ok = ok && std::fread(reps.data(), sizeof(Rep), c->R, f) == (size_t)c->R;
+  ok = ok && std::fread(pos.data(), sizeof(uint4), na, f) == na;
+  ok = ok && std::fread(vh.data(), sizeof(float4), na, f) == na;
+  ok = ok && std::fread(vl.data(), sizeof(float4), na, f) == na;
+  ok = ok && std::fread(rec.data(), sizeof(h4d_record), nrec, f) == nrec;
+  std::fclose(f);
+  if (!ok) return H4D_EINVAL;
+  for (int r = 0; r < c->R; ++r)
+    if (reps[r].atom_off != c->rep_h[r].atom_off || reps[r].cap_atoms != c->rep_h[r].cap_atoms) return H4D_EINVAL;
+  c->seed = hdr[3];
+  c->eng.seed = hdr[3];
+  c->rep_h = reps;
+  CK(cudaMemcpyAsync(c->d_pos, pos.data(), na * sizeof(uint4), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_vhi, vh.data(), na * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_vlo, vl.data(), na * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_rec, rec.data(), nrec * sizeof(h4d_record), cudaMemcpyHostToDevice, c->stream));
+  int rc = push_plan(c);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return H4D_OK;
+}
+
+// ---- stateless entry points ----
+int h4d_eval_forces(const h4d_params* params, double L, int32_t n_water, int32_t n, const double* x,
+                    const double* w, double* F, double* U) {
+  int rc = check_params(params);
+  if (rc) return rc;
+  if (!x || !F || n < 0 || n_water < 0 || 3 * n_water > n || !(L > 0)) return H4D_EINVAL;
+  if (((n - 3 * n_water) & 1) != 0) return H4D_EINVAL;
+  if (2.0 * (rmax_of(*params) + params->skin) >= L) return H4D_EINVAL;
+  if (n > 65535) return H4D_ECAPACITY;
+  rc = check_device();
+  if (rc) return rc;
+  h4d_ctx* c = new (std::nothrow) h4d_ctx();
+  if (!c) return H4D_ECUDA;
+  c->prm = *params;
+  c->seed = 0;
+  c->stream = 0;
+  c->R = 1;
+  c->max_nbr = params->max_nbr > 0 ? params->max_nbr : derive_max_nbr(*params);
+  c->max_nbr = ((c->max_nbr + 31) / 32) * 32;
+  c->rep_h.resize(1);
+  Rep& R = c->rep_h[0];
+  std::memset(&R, 0, sizeof(Rep));
+  R.n_water = n_water;
+  R.nw3 = 3 * n_water;
+  R.n_pairs = (n - 3 * n_water) / 2;
+  R.cap_pairs = R.n_pairs;
+  R.cap_atoms = std::max(n, 1);
+  R.atom_off = 0;
+  set_rep_geometry(*params, R, L);
+  R.tpa = choose_tpa(*params, n);
+  R.rec_cap = 1;
+  c->total_atoms = R.cap_atoms;
+  rc = make_plan(c);
+  if (rc) { delete c; return rc; }
+  rc = alloc_all(c);
+  if (rc) { h4d_destroy(c); return rc; }
+  fill_eng(c);
+  std::vector<uint4> pos(n);
+  double wsum = 0.0;
+  int wcnt = 0;
+  for (int a = 0; a < n; ++a) {
+    float wa = w ? (float)w[a] : 0.0f;
+    if (wa != 0.0f) { wsum += w[a]; ++wcnt; }
+    pos[a] = make_uint4(to_fixed(x[3 * a], L), to_fixed(x[3 * a + 1], L), to_fixed(x[3 * a + 2], L),
+                        __float_as_uint_host(wa));
+  }
+  rc = H4D_OK;
+  if (n > 0 && cudaMemcpy(c->d_pos, pos.data(), n * sizeof(uint4), cudaMemcpyHostToDevice) != cudaSuccess) rc = H4D_ECUDA;
+  if (!rc) rc = push_plan(c);
+  if (!rc) rc = launch_eval(c->eng, c->cta_threads, c->smem, (float)(wcnt ? wsum / wcnt : 0.0), c->d_scratch, 0);
+  std::vector<float4> f(n);
+  double u = 0.0;
+  if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = H4D_ECUDA;
+  if (!rc && n > 0 && cudaMemcpy(f.data(), c->d_force, n * sizeof(float4), cudaMemcpyDeviceToHost) != cudaSuccess) rc = H4D_ECUDA;
+  if (!rc && cudaMemcpy(&u, c->d_scratch, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) rc = H4D_ECUDA;
+  if (!rc) rc = check_errors(c);
+  if (!rc) {
+    for (int a = 0; a < n; ++a) {
+      F[3 * a] = f[a].x;
+      F[3 * a + 1] = f[a].y;
+      F[3 * a + 2] = f[a].z;
+    }
+    if (U) *U = u;
+  }
+  h4d_destroy(c);
+  return rc;
+}
+
+int h4d_neighbor_pairs(double L, int32_t n, const double* x, double r_list, int32_t* oi, int32_t* oj, int64_t cap,
+                       int64_t* n_out) {
+  if (!x || n < 0 || !(L > 0) || !(r_list > 0) || 2.0 * r_list >= L || (cap > 0 && (!oi || !oj))) return H4D_EINVAL;
+  if (n > 65535) return H4D_ECAPACITY;
+  int rc = check_device();
+  if (rc) return rc;
+  h4d_ctx* c = new (std::nothrow) h4d_ctx();
+  if (!c) return H4D_ECUDA;
+  std::memset(&c->prm, 0, sizeof(c->prm));
+  c->prm.system = H4D_SYS_LJ;
+  c->prm.ntypes = 2;
+  c->prm.rc_lj = c->prm.rc_coul = r_list;
+  c->prm.dt = 1.0;
+  c->prm.beta = 1.0;
+  c->prm.mvv2e = 1.0;
+  c->prm.mass[0] = c->prm.mass[1] = 1.0;
+  c->seed = 0;
+  c->stream = 0;
+  c->R = 1;
+  c->max_nbr = ((std::min(std::max(n, 1), 4096) + 31) / 32) * 32;
+  c->rep_h.resize(1);
+  Rep& R = c->rep_h[0];
+  std::memset(&R, 0, sizeof(Rep));
+  int np = (n + 1) / 2;
+  R.n_pairs = np;
+  R.cap_pairs = np;
+  R.cap_atoms = std::max(2 * np, 1);
+  set_rep_geometry(c->prm, R, L);
+  R.tpa = 1;
+  R.rec_cap = 1;
+  c->total_atoms = R.cap_atoms;
+  rc = make_plan(c);
+  if (rc) { delete c; return rc; }
+  rc = alloc_all(c);
+  if (rc) { h4d_destroy(c); return rc; }
+  fill_eng(c);
+  // atoms beyond n (odd n) are parked far away from every pair: they are dropped below
+  std::vector<uint4> pos(R.cap_atoms);
+  for (int a = 0; a < n; ++a)
+    pos[a] = make_uint4(to_fixed(x[3 * a], L), to_fixed(x[3 * a + 1], L), to_fixed(x[3 * a + 2], L), 0u);
+  for (int a = n; a < R.cap_atoms; ++a) pos[a] = pos[0];
+  rc = H4D_OK;
+  if (cudaMemcpy(c->d_pos, pos.data(), R.cap_atoms * sizeof(uint4), cudaMemcpyHostToDevice) != cudaSuccess) rc = H4D_ECUDA;
+  if (!rc) rc = push_plan(c);
+  if (!rc) rc = launch_list(c->eng, 1, c->cta_threads, c->smem, 0);
+  if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = H4D_ECUDA;
+  std::vector<int> cnt(R.cap_atoms);
+  std::vector<uint16_t> nb((size_t)R.cap_atoms * c->max_nbr);
+  if (!rc && cudaMemcpy(cnt.data(), c->d_ncnt, R.cap_atoms * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = H4D_ECUDA;
+  if (!rc && cudaMemcpy(nb.data(), c->d_nbr, nb.size() * sizeof(uint16_t), cudaMemcpyDeviceToHost) != cudaSuccess) rc = H4D_ECUDA;
+  if (!rc) rc = check_errors(c);
+  if (!rc) {
+    int64_t m = 0;
+    for (int i = 0; i < n; ++i) {
+      std::vector<int> row;
+      for (int s = 0; s < cnt[i]; ++s) {
+        int j = nb[(size_t)s * R.cap_atoms + i];  // tpa = 1 layout
+        if (j > i && j < n) row.push_back(j);
+      }
+      std::sort(row.begin(), row.end());
+      for (int j : row) {
+        if (m < cap) { oi[m] = i; oj[m] = j; }
+        ++m;
+      }
+    }
+    if (n_out) *n_out = m;
+  }
+  h4d_destroy(c);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,1115 @@
+// h4d_engine.cu -- sm_103a kernels of libh4d: neighbour build, 4D pair force/energy,
+// velocity Verlet with the altitude protocol, FP64 work/energy sums, Metropolis and
+// commit, CSVR equilibrium MD.  One group of warps owns one replica for a whole launch
+// and keeps its positions in shared memory; all steps of all cycles run inside the
+// launch (persistent), synchronised by the group's named barrier.
+//
+// Paper references: Sec. II.A (Eq. 2 protocol, NVE evolution, two-end momentum reversal,
+// Eqs. 3-8 Metropolis), Sec. II.B.1 (flyers fixed in 3D), Sec. II.B.2 (Eqs. 9-11
+// screened 4D Coulomb), Sec. II.D (Eqs. 19-20 potentials), SI Sec. S5 (Eqs. S6-S7).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "h4d_engine.cuh"
+
+namespace h4d {
+
+typedef unsigned long long u64;
+
+// ------------------------------------------------------------------------------------
+// Philox4x64-10 (Salmon et al., SC'11).  Counter {c0, c1, purpose, 0}, key {seed, replica}.
+// ------------------------------------------------------------------------------------
+enum : u64 { kPurTrial = 1, kPurGamma = 2, kPurThermo = 3, kPurVinit = 4 };
+
+__device__ __forceinline__ void philox4x64(u64 c[4], u64 k0, u64 k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const u64 m0 = 0xD2E7470EE14C6C93ULL, m1 = 0xCA5A826395121157ULL;
+    u64 lo0 = m0 * c[0], hi0 = __umul64hi(m0, c[0]);
+    u64 lo1 = m1 * c[2], hi1 = __umul64hi(m1, c[2]);
+    u64 n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += 0x9E3779B97F4A7C15ULL;
+    k1 += 0xBB67AE8584CAA73BULL;
+  }
+}
+
+__device__ __forceinline__ void draw4(u64 seed, u64 rep, u64 c0, u64 c1, u64 pur, u64 out[4]) {
+  out[0] = c0; out[1] = c1; out[2] = pur; out[3] = 0;
+  philox4x64(out, seed, rep);
+}
+__device__ __forceinline__ double u01(u64 r) { return (double)(r >> 11) * 0x1.0p-53; }
+__device__ __forceinline__ double u01_open(u64 r) { return (double)((r >> 11) + 1) * 0x1.0p-53; }
+__device__ __forceinline__ int pick_index(u64 r, int n) { return (int)(((r >> 32) * (u64)n) >> 32); }
+__device__ __forceinline__ double gauss_c(u64 a, u64 b) {
+  return sqrt(-2.0 * log(u01_open(a))) * cos(2.0 * 3.141592653589793 * u01(b));
+}
+__device__ __forceinline__ double gauss_s(u64 a, u64 b) {
+  return sqrt(-2.0 * log(u01_open(a))) * sin(2.0 * 3.141592653589793 * u01(b));
+}
+
+// ------------------------------------------------------------------------------------
+// small helpers
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void gsync(int bar, int nthreads) {
+  if (bar == 0) __syncthreads();
+  else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ int type_of(int a, int nw3) {
+  return a < nw3 ? ((a % 3 == 0) ? 2 : 3) : ((a - nw3) & 1);
+}
+
+// float-float accumulate: (hi, lo) += d
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float d) {
+  float s = hi + d;
+  float bp = s - hi;
+  float err = (hi - (s - bp)) + (d - bp);
+  lo += err;
+  float t = s + lo;
+  lo = lo - (t - s);
+  hi = t;
+}
+// (hi, lo) *= a
+__device__ __forceinline__ void ff_scale(float& hi, float& lo, float a) {
+  float p = hi * a;
+  float e = fmaf(hi, a, -p);
+  float l = fmaf(lo, a, e);
+  float t = p + l;
+  lo = l - (t - p);
+  hi = t;
+}
+
+__device__ __forceinline__ float wbits(const uint4& p) { return __uint_as_float(p.w); }
+
+// Abramowitz & Stegun 7.1.26: erfc(x) = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^{-x^2},
+// t = 1/(1 + p x), |error| <= 1.5e-7 for x >= 0.  Returns the polynomial factor; the
+// caller multiplies by e^{-x^2}, which it also needs for the force.
+__device__ __forceinline__ float as_erfc_poly(float x) {
+  float t;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(fmaf(0.3275911f, x, 1.0f)));
+  float p = fmaf(t, 1.061405429f, -1.453152027f);
+  p = fmaf(t, p, 1.421413741f);
+  p = fmaf(t, p, -0.284496736f);
+  p = fmaf(t, p, 0.254829592f);
+  return p * t;
+}
+__device__ __forceinline__ float exp_neg_sq(float x) {
+  // e^{-x^2} = 2^{-x^2 log2 e}
+  float y = -x * x * 1.4426950408889634f;
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+  return r;
+}
+
+// pair-table entry of (ti, tj)
+template <int SYS>
+struct PairCoef {
+  float sig2, eps4, ljshift, kq;
+};
+
+template <int SYS>
+__device__ __forceinline__ PairCoef<SYS> coef(const Pot& P, int ti, int tj) {
+  PairCoef<SYS> c;
+  if (SYS == H4D_SYS_LJ) {
+    // equal sizes and energies; charges +1/-1 by type parity
+    c.sig2 = P.sig2[0];
+    c.eps4 = P.eps4[0];
+    c.ljshift = P.ljshift[0];
+    c.kq = (ti == tj) ? P.kq[0] : P.kq[1];
+  } else {
+    int k = ti * 4 + tj;
+    c.sig2 = P.sig2[k];
+    c.eps4 = P.eps4[k];
+    c.ljshift = P.ljshift[k];
+    c.kq = P.kq[k];
+  }
+  return c;
+}
+
+// -du/dr / r of the 4D pair term (FP32): LJ (Eq. 19) + screened erfc Coulomb (Eqs. 9-11, 20)
+template <int SYS>
+__device__ __forceinline__ float pair_fr(const Pot& P, const PairCoef<SYS>& c, float r2, float g) {
+  float rinv = rsqrtf(r2);
+  float rinv2 = rinv * rinv;
+  float s2 = c.sig2 * rinv2;
+  float s6 = s2 * s2 * s2;
+  float fr_lj = c.eps4 * s6 * fmaf(12.0f, s6, -6.0f) * rinv2;
+  fr_lj = (r2 < P.rc2_lj) ? fr_lj : 0.0f;
+  float r = r2 * rinv;
+  float x = P.alpha * r;
+  float ex = exp_neg_sq(x);
+  float erfcx = as_erfc_poly(x) * ex;
+  float fr_c = c.kq * g * fmaf(erfcx, rinv, P.two_alpha_sqrtpi * ex) * rinv2;
+  fr_c = (r2 < P.rc2_c) ? fr_c : 0.0f;
+  return fr_lj + fr_c;
+}
+
+// FP32 pair energy (protocol-work diagnostic only)
+template <int SYS>
+__device__ __forceinline__ float pair_u32(const Pot& P, const PairCoef<SYS>& c, float r2, float g) {
+  float u = 0.0f;
+  float rinv = rsqrtf(r2);
+  if (r2 < P.rc2_lj) {
+    float s2 = c.sig2 * rinv * rinv;
+    float s6 = s2 * s2 * s2;
+    u += c.eps4 * (s6 * s6 - s6) - c.ljshift;
+  }
+  if (r2 < P.rc2_c) {
+    float x = P.alpha * r2 * rinv;
+    float erfcx = as_erfc_poly(x) * exp_neg_sq(x);
+    u += c.kq * g * (erfcx * rinv - P.shift_c);
+  }
+  return u;
+}
+
+// FP64 pair energy for the end-point Hamiltonians of each trial
+__device__ __forceinline__ double pair_u64(const Pot& P, int ti, int tj, double r2, double g) {
+  int k = ti * 4 + tj;
+  double u = 0.0;
+  if (r2 < P.drc2_lj && P.deps4[k] != 0.0) {
+    double s2 = P.dsig2[k] / r2;
+    double s6 = s2 * s2 * s2;
+    u += P.deps4[k] * (s6 * s6 - s6) - P.dljshift[k];
+  }
+  if (r2 < P.drc2_c && P.dkq[k] != 0.0) {
+    double r = sqrt(r2);
+    u += P.dkq[k] * g * (erfc(P.dalpha * r) / r - P.dshift_c);
+  }
+  return u;
+}
+
+// ------------------------------------------------------------------------------------
+// Per-group shared memory
+// ------------------------------------------------------------------------------------
+struct GScal {
+  int flag_rebuild, flag_overflow, flag_nan, n_tot;
+  int fly0, fly1, ins, status;
+  int flip_s, flip_e, cat, ani;
+  int n_before, accept, pad0, pad1;
+  float w_cur, g_scr, pad2, pad3;
+  double alpha_th, dW[2], wprot, wprot_c, red_out;
+  double ln_u, ustart, kstart, uend, kend;
+  double vfly[6];
+  unsigned int xfly[6];
+  double kw[32];
+};
+
+struct GView {
+  uint4* pos;
+  int* cstart;
+  int* cfill;
+  uint16_t* sorted;
+  uint16_t* cellof;
+  double* red;
+  GScal* s;
+};
+
+__device__ __forceinline__ GView carve(char* base, int cap_atoms, int nc, int nthreads) {
+  GView v;
+  size_t ncell = nc >= 3 ? (size_t)nc * nc * nc : 0;
+  char* p = base;
+  v.pos = (uint4*)p; p += 16 * (size_t)cap_atoms;
+  v.cstart = (int*)p; p += 4 * (ncell + 1);
+  v.cfill = (int*)p; p += 4 * ncell;
+  v.sorted = (uint16_t*)p; p += 2 * (size_t)cap_atoms;
+  v.cellof = (uint16_t*)p; p += 2 * (size_t)cap_atoms;
+  size_t off = (size_t)(p - base);
+  off = (off + 15) & ~(size_t)15;
+  p = base + off;
+  v.red = (double*)p; p += 8 * (size_t)nthreads;
+  v.s = (GScal*)p;
+  return v;
+}
+
+struct Ctx {
+  GView v;
+  Rep* R;
+  const Eng* e;
+  int tid, T, bar, tpa;
+  __device__ void sync() const { gsync(bar, T); }
+};
+
+__device__ __forceinline__ size_t nbr_index(const Eng& e, const Rep& R, int i, int s, int tpa) {
+  return (size_t)R.atom_off * e.max_nbr + ((size_t)(s / tpa) * R.cap_atoms + i) * tpa + (s % tpa);
+}
+
+// deterministic group-wide FP64 sum: warp butterflies, then thread 0 adds warp slots in order
+__device__ double group_sum(const Ctx& c, double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  int warp = c.tid >> 5, lane = c.tid & 31;
+  c.sync();
+  if (lane == 0) c.v.s->kw[warp] = x;
+  c.sync();
+  if (c.tid == 0) {
+    double s = 0.0, comp = 0.0;  // Kahan
+    for (int w = 0; w < (c.T >> 5); ++w) {
+      double y = c.v.s->kw[w] - comp;
+      double t = s + y;
+      comp = (t - s) - y;
+      s = t;
+    }
+    c.v.s->red_out = s;
+  }
+  c.sync();
+  return c.v.s->red_out;
+}
+
+// ------------------------------------------------------------------------------------
+// Neighbour list: fixed-point cells, deterministic stable counting sort, full rows
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ int cell_of_pos(const uint4& p, int nc) {
+  int cx = (int)__umulhi(p.x, (unsigned)nc);
+  int cy = (int)__umulhi(p.y, (unsigned)nc);
+  int cz = (int)__umulhi(p.z, (unsigned)nc);
+  return (cx * nc + cy) * nc + cz;
+}
+
+__device__ __forceinline__ u64 fixed_d2(const uint4& a, const uint4& b) {
+  long long dx = (int)(a.x - b.x), dy = (int)(a.y - b.y), dz = (int)(a.z - b.z);
+  return (u64)(dx * dx) + (u64)(dy * dy) + (u64)(dz * dz);
+}
+
+__device__ __forceinline__ bool excluded_pair(int i, int j, int nw3) {
+  return i < nw3 && j < nw3 && (i / 3) == (j / 3);
+}
+
+__device__ void build_list(const Ctx& c) {
+  const Eng& e = *c.e;
+  Rep& R = *c.R;
+  GView& v = const_cast<GView&>(c.v);
+  const int n = v.s->n_tot;
+  const int nc = R.nc;
+  const int tpa = c.tpa;
+  const int maxn = e.max_nbr;
+  if (nc >= 3) {
+    const int ncell = nc * nc * nc;
+    for (int k = c.tid; k < ncell; k += c.T) v.cfill[k] = 0;
+    c.sync();
+    for (int a = c.tid; a < n; a += c.T) {
+      int cc = cell_of_pos(v.pos[a], nc);
+      v.cellof[a] = (uint16_t)cc;
+      atomicAdd(&v.cfill[cc], 1);
+    }
+    c.sync();
+    if (c.tid < 32) {  // exclusive scan over cells by warp 0
+      int lane = c.tid;
+      int carry = 0;
+      for (int b = 0; b < ncell; b += 32) {
+        int k = b + lane;
+        int x = (k < ncell) ? v.cfill[k] : 0;
+        int incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        if (k < ncell) { v.cstart[k] = carry + incl - x; v.cfill[k] = carry + incl - x; }
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      if (lane == 0) v.cstart[ncell] = carry;
+      __syncwarp();
+      // stable scatter: atoms of a cell end up in ascending index order
+      unsigned lt = (1u << lane) - 1u;
+      for (int b = 0; b < n; b += 32) {
+        int a = b + lane;
+        int cc = (a < n) ? (int)v.cellof[a] : -1 - lane;
+        unsigned peers = __match_any_sync(0xffffffffu, cc);
+        int rank = __popc(peers & lt);
+        int base = (a < n) ? v.cfill[cc] : 0;
+        __syncwarp();
+        if (a < n) {
+          v.sorted[base + rank] = (uint16_t)a;
+          if (rank == 0) v.cfill[cc] = base + __popc(peers);
+        }
+        __syncwarp();
+      }
+    }
+    c.sync();
+  }
+  // rows: one thread per atom, fixed cell order, ascending index within a cell
+  int overflow = 0;
+  for (int i = c.tid; i < n; i += c.T) {
+    uint4 pi = v.pos[i];
+    int cnt = 0;
+    if (nc >= 3) {
+      int cx = (int)__umulhi(pi.x, (unsigned)nc), cy = (int)__umulhi(pi.y, (unsigned)nc),
+          cz = (int)__umulhi(pi.z, (unsigned)nc);
+      for (int dx = -1; dx <= 1; ++dx) {
+        int ex = cx + dx; ex += (ex < 0) ? nc : 0; ex -= (ex >= nc) ? nc : 0;
+        for (int dy = -1; dy <= 1; ++dy) {
+          int ey = cy + dy; ey += (ey < 0) ? nc : 0; ey -= (ey >= nc) ? nc : 0;
+          for (int dz = -1; dz <= 1; ++dz) {
+            int ez = cz + dz; ez += (ez < 0) ? nc : 0; ez -= (ez >= nc) ? nc : 0;
+            int cc = (ex * nc + ey) * nc + ez;
+            int s0 = v.cstart[cc], s1 = v.cstart[cc + 1];
+            for (int q = s0; q < s1; ++q) {
+              int j = v.sorted[q];
+              if (j == i || excluded_pair(i, j, R.nw3)) continue;
+              if (fixed_d2(pi, v.pos[j]) <= R.T_list) {
+                if (cnt < maxn) e.nbr[nbr_index(e, R, i, cnt, tpa)] = (uint16_t)j;
+                ++cnt;
+              }
+            }
+          }
+        }
+      }
+    } else {
+      for (int j = 0; j < n; ++j) {
+        if (j == i || excluded_pair(i, j, R.nw3)) continue;
+        if (fixed_d2(pi, v.pos[j]) <= R.T_list) {
+          if (cnt < maxn) e.nbr[nbr_index(e, R, i, cnt, tpa)] = (uint16_t)j;
+          ++cnt;
+        }
+      }
+    }
+    if (cnt > maxn) { overflow = 1; cnt = maxn; }
+    e.ncnt[R.atom_off + i] = cnt;
+    e.ref[R.atom_off + i] = pi;
+  }
+  if (overflow) atomicOr(&v.s->flag_overflow, 1);
+  c.sync();
+  if (c.tid == 0) {
+    R.builds++;
+    v.s->flag_rebuild = 0;
+    if (v.s->flag_overflow) R.err |= 1;
+  }
+  c.sync();
+}
+
+// ------------------------------------------------------------------------------------
+// Force pass (FP32): tpa lanes per atom over its full row, butterfly reduction.
+// mode bits: 1 = apply the second half kick, 2 = accumulate kinetic partials,
+//            4 = flyer rows compute protocol work with previous altitude w_prev
+// ------------------------------------------------------------------------------------
+template <int SYS>
+__device__ void force_pass(const Ctx& c, int mode, float w_prev, double* kin_out) {
+  const Eng& e = *c.e;
+  const Rep& R = *c.R;
+  const Pot& P = e.pot;
+  const GView& v = c.v;
+  const int n = v.s->n_tot;
+  const int tpa = c.tpa;
+  const int nsub = c.T / tpa;
+  const int sub = c.tid / tpa, lin = c.tid % tpa;
+  const int fly0 = v.s->fly0, fly1 = v.s->fly1;
+  const float gscr = v.s->g_scr;
+  const float scale = R.scale;
+  const float half_dt = 0.5f * (float)e.proto.dt;
+  float kin = 0.0f;
+  for (int a0 = 0; a0 < n; a0 += nsub) {
+    const int i = a0 + sub;
+    const bool active = i < n;
+    float fx = 0.f, fy = 0.f, fz = 0.f, dwk = 0.f;
+    const bool iflyer = active && (i == fly0 || i == fly1);
+    if (active) {
+      const uint4 pi = v.pos[i];
+      const int ti = type_of(i, R.nw3);
+      const float wi = wbits(pi);
+      const bool wnz_i = wi != 0.0f;
+      const int cnt = e.ncnt[R.atom_off + i];
+      const bool do_work = (mode & 4) && iflyer;
+      for (int s = lin; s < cnt; s += tpa) {
+        const int j = e.nbr[nbr_index(e, R, i, s, tpa)];
+        const uint4 pj = v.pos[j];
+        const float dx = (float)(int)(pj.x - pi.x) * scale;
+        const float dy = (float)(int)(pj.y - pi.y) * scale;
+        const float dz = (float)(int)(pj.z - pi.z) * scale;
+        const float wj = wbits(pj);
+        const float dw = wi - wj;
+        const float r3 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float r2 = fmaf(dw, dw, r3);
+        if (r2 < P.rc2_max) {
+          const int tj = type_of(j, R.nw3);
+          const float g = (wnz_i != (wj != 0.0f)) ? gscr : 1.0f;
+          const PairCoef<SYS> cf = coef<SYS>(P, ti, tj);
+          const float fr = pair_fr<SYS>(P, cf, r2, g);
+          fx = fmaf(-fr, dx, fx);
+          fy = fmaf(-fr, dy, fy);
+          fz = fmaf(-fr, dz, fz);
+        }
+        if (do_work && j != fly0 && j != fly1) {
+          const int tj = type_of(j, R.nw3);
+          const PairCoef<SYS> cf = coef<SYS>(P, ti, tj);
+          const float r2o = fmaf(w_prev, w_prev, r3);
+          const float go = __expf(-P.kappa_sr * w_prev);
+          const float un = (r2 < P.rc2_max) ? pair_u32<SYS>(P, cf, r2, gscr) : 0.0f;
+          const float uo = (r2o < P.rc2_max) ? pair_u32<SYS>(P, cf, r2o, go) : 0.0f;
+          dwk += un - uo;
+        }
+      }
+    }
+    for (int o = tpa >> 1; o > 0; o >>= 1) {
+      fx += __shfl_xor_sync(0xffffffffu, fx, o, tpa);
+      fy += __shfl_xor_sync(0xffffffffu, fy, o, tpa);
+      fz += __shfl_xor_sync(0xffffffffu, fz, o, tpa);
+      dwk += __shfl_xor_sync(0xffffffffu, dwk, o, tpa);
+    }
+    if (active && lin == 0) {
+      const int ga = R.atom_off + i;
+      e.force[ga] = make_float4(fx, fy, fz, 0.f);
+      if ((mode & 4) && iflyer) v.s->dW[i == fly0 ? 0 : 1] = (double)dwk;
+      if (!iflyer && (mode & 3)) {
+        float4 h = e.vhi[ga], l = e.vlo[ga];
+        const int ti = type_of(i, R.nw3);
+        if (mode & 1) {
+          const float cm = half_dt * P.inv_m[ti];
+          ff_add(h.x, l.x, fx * cm);
+          ff_add(h.y, l.y, fy * cm);
+          ff_add(h.z, l.z, fz * cm);
+          e.vhi[ga] = h;
+          e.vlo[ga] = l;
+        }
+        if (mode & 2) {
+          const float vx = h.x + l.x, vy = h.y + l.y, vz = h.z + l.z;
+          kin += (float)P.dm[ti] * fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+        }
+      }
+    }
+  }
+  if (mode & 2) *kin_out = group_sum(c, (double)kin) * 0.5;
+}
+
+// ------------------------------------------------------------------------------------
+// Kick + drift pass: optional thermostat scale, half kick, fixed-point drift, move check
+// ------------------------------------------------------------------------------------
+__device__ void kick_drift(const Ctx& c, float alpha) {
+  const Eng& e = *c.e;
+  const Rep& R = *c.R;
+  const Pot& P = e.pot;
+  const GView& v = c.v;
+  const int n = v.s->n_tot;
+  const int fly0 = v.s->fly0, fly1 = v.s->fly1;
+  const float half_dt = 0.5f * (float)e.proto.dt;
+  int moved = 0, bad = 0;
+  for (int a = c.tid; a < n; a += c.T) {
+    if (a == fly0 || a == fly1) continue;  // flyers keep their 3D state (Sec. II.B.1)
+    const int ga = R.atom_off + a;
+    float4 h = e.vhi[ga], l = e.vlo[ga];
+    if (alpha != 1.0f) {
+      ff_scale(h.x, l.x, alpha);
+      ff_scale(h.y, l.y, alpha);
+      ff_scale(h.z, l.z, alpha);
+    }
+    const float4 f = e.force[ga];
+    const float cm = half_dt * P.inv_m[type_of(a, R.nw3)];
+    ff_add(h.x, l.x, f.x * cm);
+    ff_add(h.y, l.y, f.y * cm);
+    ff_add(h.z, l.z, f.z * cm);
+    e.vhi[ga] = h;
+    e.vlo[ga] = l;
+    const float sx = fmaf(h.x, R.c_drift, l.x * R.c_drift);
+    const float sy = fmaf(h.y, R.c_drift, l.y * R.c_drift);
+    const float sz = fmaf(h.z, R.c_drift, l.z * R.c_drift);
+    const float lim = 1.0e9f;
+    if (!(fabsf(sx) < lim && fabsf(sy) < lim && fabsf(sz) < lim)) { bad = 1; continue; }
+    uint4 p = v.pos[a];
+    p.x += (unsigned)__float2int_rn(sx);
+    p.y += (unsigned)__float2int_rn(sy);
+    p.z += (unsigned)__float2int_rn(sz);
+    v.pos[a] = p;
+    if (fixed_d2(p, e.ref[ga]) > R.T_move) moved = 1;
+  }
+  if (moved) v.s->flag_rebuild = 1;
+  if (bad) v.s->flag_nan = 1;
+}
+
+__device__ void scale_velocities(const Ctx& c, float alpha) {
+  const Eng& e = *c.e;
+  const Rep& R = *c.R;
+  const int n = c.v.s->n_tot;
+  for (int a = c.tid; a < n; a += c.T) {
+    const int ga = R.atom_off + a;
+    float4 h = e.vhi[ga], l = e.vlo[ga];
+    ff_scale(h.x, l.x, alpha);
+    ff_scale(h.y, l.y, alpha);
+    ff_scale(h.z, l.z, alpha);
+    e.vhi[ga] = h;
+    e.vlo[ga] = l;
+  }
+}
+
+__device__ void negate_velocities(const Ctx& c, int n) {
+  const Eng& e = *c.e;
+  const Rep& R = *c.R;
+  for (int a = c.tid; a < n; a += c.T) {
+    const int ga = R.atom_off + a;
+    float4 h = e.vhi[ga], l = e.vlo[ga];
+    h.x = -h.x; h.y = -h.y; h.z = -h.z;
+    l.x = -l.x; l.y = -l.y; l.z = -l.z;
+    e.vhi[ga] = h;
+    e.vlo[ga] = l;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// FP64 end-point energies
+// ------------------------------------------------------------------------------------
+// U over atoms [0, n_tot) leaving out ex0/ex1 (-1 = none); each unordered pair once
+__device__ double energy64(const Ctx& c, int ex0, int ex1) {
+  const Eng& e = *c.e;
+  const Rep& R = *c.R;
+  const Pot& P = e.pot;
+  const GView& v = c.v;
+  const int n = v.s->n_tot;
+  const double scale = R.L * 0x1.0p-32;
+  const double gscr = exp(-P.dkappa_sr * (double)v.s->w_cur);
+  const double rc2max = P.drc2_lj > P.drc2_c ? P.drc2_lj : P.drc2_c;
+  double acc = 0.0, comp = 0.0;
+  for (int i = c.tid; i < n; i += c.T) {
+    if (i == ex0 || i == ex1) continue;
+    const uint4 pi = v.pos[i];
+    const int ti = type_of(i, R.nw3);
+    const double wi = (double)wbits(pi);
+    const int cnt = e.ncnt[R.atom_off + i];
+    for (int s = 0; s < cnt; ++s) {
+      const int j = e.nbr[nbr_index(e, R, i, s, c.tpa)];
+      if (j <= i || j == ex0 || j == ex1) continue;
+      const uint4 pj = v.pos[j];
+      const double dx = (double)(int)(pj.x - pi.x) * scale;
+      const double dy = (double)(int)(pj.y - pi.y) * scale;
+      const double dz = (double)(int)(pj.z - pi.z) * scale;
+      const double wj = (double)wbits(pj);
+      const double dw = wi - wj;
+      const double r2 = dx * dx + dy * dy + dz * dz + dw * dw;
+      if (r2 >= rc2max) continue;
+      const double g = ((wi != 0.0) != (wj != 0.0)) ? gscr : 1.0;
+      const double y = pair_u64(P, ti, type_of(j, R.nw3), r2, g) - comp;
+      const double t = acc + y;
+      comp = (t - acc) - y;
+      acc = t;
+    }
+  }
+  return group_sum(c, acc);
+}
+
+__device__ double kinetic64(const Ctx& c) {
+  const Eng& e = *c.e;
+  const Rep& R = *c.R;
+  const int n = c.v.s->n_tot;
+  const int fly0 = c.v.s->fly0, fly1 = c.v.s->fly1;
+  double acc = 0.0;
+  for (int a = c.tid; a < n; a += c.T) {
+    if (a == fly0 || a == fly1) continue;
+    const int ga = R.atom_off + a;
+    const float4 h = e.vhi[ga], l = e.vlo[ga];
+    const double vx = (double)h.x + (double)l.x, vy = (double)h.y + (double)l.y,
+                 vz = (double)h.z + (double)l.z;
+    acc += 0.5 * e.pot.dm[type_of(a, R.nw3)] * (vx * vx + vy * vy + vz * vz);
+  }
+  return group_sum(c, acc);
+}
+
+// ------------------------------------------------------------------------------------
+// Thermostat (equilibrium MD only): CSVR (Bussi, Donadio, Parrinello 2007, Eq. A7) with
+// the chi-square variate from the Marsaglia-Tsang gamma sampler (ACM TOMS 2000).
+// ------------------------------------------------------------------------------------
+__device__ double chi2_variate(const Eng& e, const Rep& R, u64 rep_id, u64 step, double dof) {
+  double k = 0.5 * dof;
+  if (k <= 0.0) return 0.0;
+  const double k0 = k;
+  if (k < 1.0) k += 1.0;
+  const double d = k - 1.0 / 3.0, cc = 1.0 / sqrt(9.0 * d);
+  double g = d, boost = 1.0;
+  for (u64 attempt = 0; attempt < 4096; ++attempt) {
+    u64 r[4];
+    draw4(e.seed, rep_id, step, attempt, kPurGamma, r);
+    const double z = gauss_c(r[0], r[1]);
+    double t = 1.0 + cc * z;
+    if (t <= 0.0) continue;
+    t = t * t * t;
+    const double u = u01_open(r[2]);
+    if (log(u) < 0.5 * z * z + d - d * t + d * log(t)) {
+      g = d * t;
+      if (k0 < 1.0) boost = pow(u01_open(r[3]), 1.0 / k0);
+      break;
+    }
+  }
+  return 2.0 * g * boost;
+}
+
+__device__ double csvr_alpha(const Eng& e, const Rep& R, u64 rep_id, u64 step, double K, int n) {
+  const double dof = 3.0 * n - 3.0 * R.n_water;
+  if (dof < 1.0 || e.proto.tau_t <= 0.0 || K <= 0.0) return 1.0;
+  const double Kbar = 0.5 * dof / e.proto.beta;
+  const double cdec = exp(-e.proto.dt / e.proto.tau_t);
+  u64 r[4];
+  draw4(e.seed, rep_id, step, 0, kPurThermo, r);
+  const double R1 = gauss_c(r[0], r[1]);
+  const double S = chi2_variate(e, R, rep_id, step, dof - 1.0);
+  const double Knew = K + (1.0 - cdec) * (Kbar * (S + R1 * R1) / dof - K) +
+                      2.0 * R1 * sqrt(Kbar * K * (1.0 - cdec) * cdec / dof);
+  double a = sqrt(Knew / K);
+  if (R1 + sqrt(dof * K * cdec / (Kbar * (1.0 - cdec))) < 0.0) a = -a;
+  return a;
+}
+
+// ------------------------------------------------------------------------------------
+// Protocol: altitude at NEMD step k (Eq. 2; Eqs. S6-S7 insertion forms; deletion is the
+// time reverse of insertion)
+// ------------------------------------------------------------------------------------
+__device__ double altitude(const Proto& pr, int insertion, int k) {
+  const int kk = insertion ? k : pr.n_f - k;
+  const double xi = (double)kk / (double)pr.n_f;
+  double s;
+  if (pr.schedule == H4D_SCHED_WV) s = 1.0 - pow(xi, pr.sched_n);
+  else if (pr.schedule == H4D_SCHED_WX) s = pow(1.0 - xi, pr.sched_n);
+  else s = 1.0 - xi;
+  return pr.w_max * s;
+}
+
+// ------------------------------------------------------------------------------------
+// Phases
+// ------------------------------------------------------------------------------------
+template <int SYS>
+__device__ void initial_forces(const Ctx& c) {
+  build_list(c);
+  force_pass<SYS>(c, 0, 0.f, nullptr);
+  c.sync();
+}
+
+// equilibrium MD: n_steps velocity-Verlet steps at w = 0 with the CSVR thermostat
+template <int SYS>
+__device__ void md_phase(const Ctx& c, int n_steps) {
+  const Eng& e = *c.e;
+  Rep& R = *c.R;
+  GScal* S = c.v.s;
+  initial_forces<SYS>(c);
+  float alpha = 1.0f;
+  for (int st = 0; st < n_steps; ++st) {
+    kick_drift(c, alpha);
+    c.sync();
+    if (S->flag_rebuild) build_list(c);
+    double K = 0.0;
+    force_pass<SYS>(c, 1 | 2, 0.f, &K);  // ends with group syncs
+    if (c.tid == 0) {
+      const int n = S->n_tot;
+      double a = csvr_alpha(e, R, (u64)(c.R - e.rep), R.step_ctr, K, n);
+      if (!isfinite(a) || !isfinite(K)) { a = 1.0; S->flag_nan = 1; }
+      S->alpha_th = a;
+      R.step_ctr++;
+      R.md_steps++;
+    }
+    c.sync();
+    alpha = (float)S->alpha_th;
+  }
+  if (alpha != 1.0f) scale_velocities(c, alpha);
+  c.sync();
+  if (c.tid == 0 && S->flag_nan) R.err |= 2;
+}
+
+// one pair-exchange trial (Sec. II.A); readings as in the oracle:
+//  - insertion / deletion with probability 1/2, cation and anion chosen independently;
+//  - all velocities reversed with probability 1/2 before NEMD and after the decision;
+//    a rejection restores the state saved after the first reversal;
+//  - Delta H = H_{N+1}(end, all in 3D) - H_N(start, flyers absent) for insertion and the
+//    reverse for deletion, flyers' kinetic energy left out (it cancels against Eqs. 3-4).
+template <int SYS>
+__device__ void trial_phase(const Ctx& c) {
+  const Eng& e = *c.e;
+  Rep& R = *c.R;
+  GScal* S = c.v.s;
+  const u64 rep_id = (u64)(c.R - e.rep);
+  if (c.tid == 0) {
+    const u64 t = R.trial_ctr++;
+    u64 b0[4], b1[4], b2[4], b3[4], b4[4];
+    draw4(e.seed, rep_id, t, 0, kPurTrial, b0);
+    draw4(e.seed, rep_id, t, 1, kPurTrial, b1);
+    draw4(e.seed, rep_id, t, 2, kPurTrial, b2);
+    draw4(e.seed, rep_id, t, 3, kPurTrial, b3);
+    draw4(e.seed, rep_id, t, 4, kPurTrial, b4);
+    S->ins = (int)(b0[0] >> 63);
+    S->flip_s = (int)(b0[1] >> 63);
+    S->flip_e = (int)(b0[2] >> 63);
+    S->ln_u = log(u01_open(b0[3]));
+    const int N = R.n_pairs;
+    S->n_before = N;
+    S->status = 0;
+    if (!S->ins && N == 0) S->status = 1;
+    if (S->ins && N >= R.cap_pairs) S->status = 2;
+    S->cat = -1;
+    S->ani = -1;
+    if (S->ins) {
+      S->xfly[0] = (unsigned)(b1[0] >> 32); S->xfly[1] = (unsigned)(b1[1] >> 32);
+      S->xfly[2] = (unsigned)(b1[2] >> 32); S->xfly[3] = (unsigned)(b1[3] >> 32);
+      S->xfly[4] = (unsigned)(b2[0] >> 32); S->xfly[5] = (unsigned)(b2[1] >> 32);
+      const double sdc = sqrt(1.0 / (e.proto.beta * e.pot.dm[0]));
+      const double sda = sqrt(1.0 / (e.proto.beta * e.pot.dm[1]));
+      S->vfly[0] = sdc * gauss_c(b3[0], b3[1]);
+      S->vfly[1] = sdc * gauss_s(b3[0], b3[1]);
+      S->vfly[2] = sdc * gauss_c(b3[2], b3[3]);
+      S->vfly[3] = sda * gauss_s(b3[2], b3[3]);
+      S->vfly[4] = sda * gauss_c(b4[0], b4[1]);
+      S->vfly[5] = sda * gauss_s(b4[0], b4[1]);
+    } else if (N > 0) {
+      S->cat = pick_index(b1[0], N);
+      S->ani = pick_index(b1[1], N);
+    }
+  }
+  c.sync();
+  const int N = S->n_before;
+  const int n = R.nw3 + 2 * N;
+  const int ins = S->ins;
+  if (S->flip_s) negate_velocities(c, n);
+  if (S->status != 0) {
+    c.sync();
+    if (S->flip_e) negate_velocities(c, n);
+    if (c.tid == 0) {
+      h4d_record rr;
+      rr.move = ins; rr.accepted = 0; rr.n_before = N; rr.n_after = N; rr.status = S->status;
+      rr.cation = -1; rr.anion = -1; rr.pad = 0;
+      rr.dH = 0.0; rr.beta_dM = 0.0; rr.w_prot = 0.0; rr.ln_u = S->ln_u; rr.x_acc = 0.0;
+      e.rec[R.rec_off + (int)(R.rec_count % R.rec_cap)] = rr;
+      R.rec_count++;
+      R.cycles++;
+      if (ins) R.trials_ins++; else R.trials_del++;
+      R.rej_status++;
+      R.sum_n += (double)N;
+      R.sum_n2 += (double)N * (double)N;
+    }
+    c.sync();
+    return;
+  }
+  // save the state for a rejection (positions from shared memory, velocities)
+  for (int a = c.tid; a < n; a += c.T) {
+    const int ga = R.atom_off + a;
+    e.pos_save[ga] = c.v.pos[a];
+    e.vhi_save[ga] = e.vhi[ga];
+    e.vlo_save[ga] = e.vlo[ga];
+  }
+  c.sync();
+  const float w0 = (float)altitude(e.proto, ins, 0);
+  if (c.tid == 0) {
+    if (ins) {
+      const int ci = n, ai = n + 1;
+      c.v.pos[ci] = make_uint4(S->xfly[0], S->xfly[1], S->xfly[2], __float_as_uint(w0));
+      c.v.pos[ai] = make_uint4(S->xfly[3], S->xfly[4], S->xfly[5], __float_as_uint(w0));
+      e.vhi[R.atom_off + ci] = make_float4((float)S->vfly[0], (float)S->vfly[1], (float)S->vfly[2], 0.f);
+      e.vlo[R.atom_off + ci] = make_float4((float)(S->vfly[0] - (double)(float)S->vfly[0]),
+                                           (float)(S->vfly[1] - (double)(float)S->vfly[1]),
+                                           (float)(S->vfly[2] - (double)(float)S->vfly[2]), 0.f);
+      e.vhi[R.atom_off + ai] = make_float4((float)S->vfly[3], (float)S->vfly[4], (float)S->vfly[5], 0.f);
+      e.vlo[R.atom_off + ai] = make_float4((float)(S->vfly[3] - (double)(float)S->vfly[3]),
+                                           (float)(S->vfly[4] - (double)(float)S->vfly[4]),
+                                           (float)(S->vfly[5] - (double)(float)S->vfly[5]), 0.f);
+      S->fly0 = ci;
+      S->fly1 = ai;
+      S->n_tot = n + 2;
+    } else {
+      S->fly0 = R.nw3 + 2 * S->cat;
+      S->fly1 = R.nw3 + 2 * S->ani + 1;
+      S->n_tot = n;
+    }
+    S->w_cur = w0;
+    S->g_scr = expf(-e.pot.kappa_sr * w0);
+    S->wprot = 0.0;
+    S->wprot_c = 0.0;
+    S->dW[0] = S->dW[1] = 0.0;
+  }
+  c.sync();
+  build_list(c);
+  const int f0 = S->fly0, f1 = S->fly1;
+  // H_start: insertion leaves the flyers out, deletion has everyone in 3D
+  const double Us = ins ? energy64(c, f0, f1) : energy64(c, -1, -1);
+  const double Ks = kinetic64(c);
+  force_pass<SYS>(c, 0, 0.f, nullptr);
+  c.sync();
+  for (int k = 0; k < e.proto.n_f; ++k) {
+    kick_drift(c, 1.0f);
+    c.sync();
+    if (S->flag_rebuild) build_list(c);
+    const float w_prev = S->w_cur;
+    const float w_next = (float)altitude(e.proto, ins, k + 1);
+    if (c.tid == 0) {
+      uint4 p0 = c.v.pos[f0], p1 = c.v.pos[f1];
+      p0.w = __float_as_uint(w_next);
+      p1.w = __float_as_uint(w_next);
+      c.v.pos[f0] = p0;
+      c.v.pos[f1] = p1;
+      S->w_cur = w_next;
+      S->g_scr = expf(-e.pot.kappa_sr * w_next);
+    }
+    c.sync();
+    force_pass<SYS>(c, 1 | 4, w_prev, nullptr);
+    c.sync();
+    if (c.tid == 0) {
+      const double y = (S->dW[0] + S->dW[1]) - S->wprot_c;
+      const double t = S->wprot + y;
+      S->wprot_c = (t - S->wprot) - y;
+      S->wprot = t;
+    }
+  }
+  c.sync();
+  // H_end: insertion has everyone in 3D, deletion leaves the flyers out
+  const double Ue = ins ? energy64(c, -1, -1) : energy64(c, f0, f1);
+  const double Ke = kinetic64(c);
+  if (c.tid == 0) {
+    const double dH = (Ue + Ke) - (Us + Ks);
+    const double V = R.L * R.L * R.L;
+    double bdm, xacc;
+    if (ins) {
+      bdm = e.proto.beta * dH - 2.0 * log(V / (double)(N + 1));  // Eq. 6
+      xacc = -bdm + e.proto.beta_mu;
+    } else {
+      bdm = -e.proto.beta * dH - 2.0 * log(V / (double)N);       // Eq. 8
+      xacc = bdm - e.proto.beta_mu;
+    }
+    int status = isfinite(dH) ? 0 : 3;
+    int acc = (status == 0) && (S->ln_u < xacc) && !e.proto.no_accept;
+    S->accept = acc;
+    h4d_record rr;
+    rr.move = ins; rr.accepted = acc; rr.n_before = N;
+    rr.n_after = N + (acc ? (ins ? 1 : -1) : 0);
+    rr.status = status;
+    rr.cation = ins ? -1 : S->cat; rr.anion = ins ? -1 : S->ani; rr.pad = 0;
+    rr.dH = dH; rr.beta_dM = bdm; rr.w_prot = S->wprot; rr.ln_u = S->ln_u; rr.x_acc = xacc;
+    e.rec[R.rec_off + (int)(R.rec_count % R.rec_cap)] = rr;
+    R.rec_count++;
+    R.cycles++;
+    if (ins) { R.trials_ins++; R.acc_ins += acc; } else { R.trials_del++; R.acc_del += acc; }
+    if (status) R.rej_status++;
+    S->ustart = Us; S->uend = Ue; S->kstart = Ks; S->kend = Ke;
+  }
+  c.sync();
+  const int acc = S->accept;
+  if (acc) {
+    if (c.tid == 0) {
+      if (ins) {
+        uint4 p0 = c.v.pos[f0], p1 = c.v.pos[f1];
+        p0.w = 0u; p1.w = 0u;  // altitude(n_f) of an insertion is 0
+        c.v.pos[f0] = p0;
+        c.v.pos[f1] = p1;
+        R.n_pairs = N + 1;
+      } else {
+        // swap-with-last keeps the interleaved cation/anion layout
+        const int lc = R.nw3 + 2 * (N - 1), la = lc + 1;
+        uint4 pc = c.v.pos[lc], pa = c.v.pos[la];
+        c.v.pos[f0] = pc;
+        c.v.pos[f1] = pa;
+        e.vhi[R.atom_off + f0] = e.vhi[R.atom_off + lc];
+        e.vlo[R.atom_off + f0] = e.vlo[R.atom_off + lc];
+        e.vhi[R.atom_off + f1] = e.vhi[R.atom_off + la];
+        e.vlo[R.atom_off + f1] = e.vlo[R.atom_off + la];
+        R.n_pairs = N - 1;
+      }
+    }
+  } else {
+    for (int a = c.tid; a < n; a += c.T) {
+      const int ga = R.atom_off + a;
+      c.v.pos[a] = e.pos_save[ga];
+      e.vhi[ga] = e.vhi_save[ga];
+      e.vlo[ga] = e.vlo_save[ga];
+    }
+  }
+  c.sync();
+  if (c.tid == 0) {
+    S->n_tot = R.nw3 + 2 * R.n_pairs;
+    S->fly0 = S->fly1 = -1;
+    S->w_cur = 0.f;
+    S->g_scr = 1.f;
+    const double Nn = (double)R.n_pairs;
+    R.sum_n += Nn;
+    R.sum_n2 += Nn * Nn;
+  }
+  c.sync();
+  if (S->flip_e) negate_velocities(c, S->n_tot);
+  c.sync();
+}
+
+// ------------------------------------------------------------------------------------
+// Kernels
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ u64 gtimer() {
+  u64 t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// bind this thread to its group's replica; false for warps outside every group
+__device__ bool setup_ctx(const Eng& e, char* smem, Ctx& c) {
+  const int warp = threadIdx.x >> 5;
+  const int g0 = e.cta_groups[blockIdx.x], g1 = e.cta_groups[blockIdx.x + 1];
+  int gi = -1;
+  for (int g = g0; g < g1; ++g)
+    if (warp >= e.groups[g].warp0 && warp < e.groups[g].warp0 + e.groups[g].nwarps) gi = g;
+  if (gi < 0) return false;
+  const Group G = e.groups[gi];
+  Rep* R = &e.rep[G.rep];
+  c.R = R;
+  c.e = &e;
+  c.tid = threadIdx.x - 32 * G.warp0;
+  c.T = 32 * G.nwarps;
+  c.bar = G.bar;
+  c.tpa = R->tpa;
+  c.v = carve(smem + G.smem_off, R->cap_atoms, R->nc, c.T);
+  GScal* S = c.v.s;
+  if (c.tid == 0) {
+    S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0;
+    S->n_tot = R->nw3 + 2 * R->n_pairs;
+    S->fly0 = S->fly1 = -1;
+    S->w_cur = 0.f; S->g_scr = 1.f;
+  }
+  c.sync();
+  for (int a = c.tid; a < S->n_tot; a += c.T) c.v.pos[a] = e.pos[R->atom_off + a];
+  c.sync();
+  return true;
+}
+
+template <int SYS>
+__global__ void __launch_bounds__(1024) cycles_kernel(Eng e, long long k_cycles, int n_eq, int do_trial) {
+  extern __shared__ __align__(16) char smem[];
+  Ctx c;
+  if (!setup_ctx(e, smem, c)) return;
+  Rep* R = c.R;
+  GScal* S = c.v.s;
+  for (long long cyc = 0; cyc < k_cycles; ++cyc) {
+    u64 t0 = gtimer();
+    if (n_eq > 0) md_phase<SYS>(c, n_eq);
+    u64 t1 = gtimer();
+    if (do_trial) trial_phase<SYS>(c);
+    u64 t2 = gtimer();
+    if (c.tid == 0) {
+      R->t_md_ns += (double)(t1 - t0);
+      R->t_nemd_ns += (double)(t2 - t1);
+    }
+  }
+  c.sync();
+  for (int a = c.tid; a < S->n_tot; a += c.T) e.pos[R->atom_off + a] = c.v.pos[a];
+  if (c.tid == 0) {
+    if (S->flag_overflow) R->err |= 1;
+    if (S->flag_nan) R->err |= 2;
+  }
+}
+
+// current U (FP64) and K of each replica
+__global__ void __launch_bounds__(1024) energy_kernel(Eng e, double* U, double* K) {
+  extern __shared__ __align__(16) char smem[];
+  Ctx c;
+  if (!setup_ctx(e, smem, c)) return;
+  build_list(c);
+  const double u = energy64(c, -1, -1);
+  const double k = kinetic64(c);
+  const int r = (int)(c.R - e.rep);
+  if (c.tid == 0) { U[r] = u; K[r] = k; }
+}
+
+// pairs within the larger cut-off (each unordered pair once), summed over replicas
+__global__ void __launch_bounds__(1024) count_kernel(Eng e, unsigned long long* out) {
+  extern __shared__ __align__(16) char smem[];
+  Ctx c;
+  if (!setup_ctx(e, smem, c)) return;
+  Rep* R = c.R;
+  GScal* S = c.v.s;
+  build_list(c);
+  unsigned long long cnt = 0;
+  const float scale = R->scale;
+  for (int i = c.tid; i < S->n_tot; i += c.T) {
+    const uint4 pi = c.v.pos[i];
+    const int m = e.ncnt[R->atom_off + i];
+    for (int s = 0; s < m; ++s) {
+      const int j = e.nbr[nbr_index(e, *R, i, s, c.tpa)];
+      if (j <= i) continue;
+      const uint4 pj = c.v.pos[j];
+      const float dx = (float)(int)(pj.x - pi.x) * scale;
+      const float dy = (float)(int)(pj.y - pi.y) * scale;
+      const float dz = (float)(int)(pj.z - pi.z) * scale;
+      if (dx * dx + dy * dy + dz * dz < e.pot.rc2_max) ++cnt;
+    }
+  }
+  atomicAdd(out, cnt);
+}
+
+// one configuration as given: list, FP32 forces (written to e.force), FP64 energy;
+// wbar is the mean altitude of the flying particles (Sec. II.B.2)
+template <int SYS>
+__global__ void __launch_bounds__(1024) eval_kernel(Eng e, float wbar, double* U) {
+  extern __shared__ __align__(16) char smem[];
+  const Group G = e.groups[0];
+  Rep* R = &e.rep[0];
+  Ctx c;
+  c.R = R; c.e = &e;
+  c.tid = threadIdx.x;
+  c.T = blockDim.x;
+  c.bar = 0;
+  c.tpa = R->tpa;
+  c.v = carve(smem + G.smem_off, R->cap_atoms, R->nc, c.T);
+  GScal* S = c.v.s;
+  if (c.tid == 0) {
+    S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0;
+    S->n_tot = R->nw3 + 2 * R->n_pairs;
+    S->fly0 = S->fly1 = -1;
+    S->w_cur = wbar;
+    S->g_scr = expf(-e.pot.kappa_sr * wbar);
+  }
+  c.sync();
+  for (int a = c.tid; a < S->n_tot; a += c.T) c.v.pos[a] = e.pos[R->atom_off + a];
+  c.sync();
+  build_list(c);
+  force_pass<SYS>(c, 0, 0.f, nullptr);
+  c.sync();
+  const double u = energy64(c, -1, -1);
+  if (c.tid == 0) {
+    *U = u;
+    if (S->flag_overflow) R->err |= 1;
+  }
+}
+
+int launch_eval(const Eng& e, int threads, size_t smem, float wbar, double* U, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (e.pot.sys == H4D_SYS_LJ) {
+    cudaFuncSetAttribute(eval_kernel<H4D_SYS_LJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    eval_kernel<H4D_SYS_LJ><<<1, threads, smem, st>>>(e, wbar, U);
+  } else {
+    cudaFuncSetAttribute(eval_kernel<H4D_SYS_AQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    eval_kernel<H4D_SYS_AQ><<<1, threads, smem, st>>>(e, wbar, U);
+  }
+  return cudaGetLastError() == cudaSuccess ? H4D_OK : H4D_ECUDA;
+}
+
+// neighbour rows only (for the bit-exact neighbour-set check)
+__global__ void __launch_bounds__(1024) list_kernel(Eng e) {
+  extern __shared__ __align__(16) char smem[];
+  Ctx c;
+  if (!setup_ctx(e, smem, c)) return;
+  build_list(c);
+}
+
+int launch_list(const Eng& e, int n_ctas, int cta_threads, size_t smem, void* stream) {
+  cudaFuncSetAttribute(list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  list_kernel<<<n_ctas, cta_threads, smem, (cudaStream_t)stream>>>(e);
+  return cudaGetLastError() == cudaSuccess ? H4D_OK : H4D_ECUDA;
+}
+
+static int check(cudaError_t err) { return err == cudaSuccess ? H4D_OK : H4D_ECUDA; }
+
+int launch_cycles(const Eng& e, int n_ctas, int cta_threads, size_t smem, long long k_cycles, int n_eq,
+                  int do_trial, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (e.pot.sys == H4D_SYS_LJ) {
+    cudaFuncSetAttribute(cycles_kernel<H4D_SYS_LJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cycles_kernel<H4D_SYS_LJ><<<n_ctas, cta_threads, smem, st>>>(e, k_cycles, n_eq, do_trial);
+  } else {
+    cudaFuncSetAttribute(cycles_kernel<H4D_SYS_AQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cycles_kernel<H4D_SYS_AQ><<<n_ctas, cta_threads, smem, st>>>(e, k_cycles, n_eq, do_trial);
+  }
+  return check(cudaGetLastError());
+}
+
+int launch_energy(const Eng& e, int n_ctas, int cta_threads, size_t smem, double* U, double* K, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaFuncSetAttribute(energy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  energy_kernel<<<n_ctas, cta_threads, smem, st>>>(e, U, K);
+  return check(cudaGetLastError());
+}
+
+int launch_count_pairs(const Eng& e, int n_ctas, int cta_threads, size_t smem, unsigned long long* out,
+                       void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaFuncSetAttribute(count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  count_kernel<<<n_ctas, cta_threads, smem, st>>>(e, out);
+  return check(cudaGetLastError());
+}
+
+}  // namespace h4d

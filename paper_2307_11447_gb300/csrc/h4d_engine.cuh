@@ -1,0 +1,111 @@
+// h4d_engine.cuh -- device-side data layout of libh4d (shared by h4d_engine.cu and
+// h4d_api.cu only).
+//
+// Layout in HBM (all replicas packed back to back, replica r at atom offset atom_off[r]):
+//   pos   uint4  [atoms]  x,y,z as 32-bit fixed-point fractions of the box edge (exact
+//                         periodic wrap and exact minimum-image differences), .w = altitude
+//                         as float bits (nonzero only for flying ions)
+//   vhi/vlo float4 [atoms] velocity as an unevaluated float-float sum (about 48 bits)
+//   force float4  [atoms] FP32 force of the last evaluation
+//   nbr   uint16  [atoms * max_nbr] full neighbour rows, tpa-interleaved (see nbr_index)
+// Each replica is simulated by one group of warps (a whole CTA or a slice of one) that
+// keeps the replica's positions in shared memory for the whole launch.
+#pragma once
+#include <cstdint>
+
+#include "../../include/h4d.h"
+
+namespace h4d {
+
+constexpr int kMaxT = 4;
+constexpr int kMaxGroupsPerCta = 15;  // named barriers 1..15
+
+struct Pot {
+  int sys, ntypes;
+  float sig2[16], eps4[16], ljshift[16], kq[16];  // per (ti*4 + tj)
+  float rc2_lj, rc2_c, rc2_max, alpha, shift_c, two_alpha_sqrtpi, kappa_sr;
+  float inv_m[kMaxT];  // 1 / (m mvv2e)
+  double dsig2[16], deps4[16], dljshift[16], dkq[16];
+  double drc2_lj, drc2_c, dalpha, dshift_c, dkappa_sr;
+  double dm[kMaxT];    // m mvv2e
+  double d_oh2, d_hh2;  // squared water bond lengths
+  double inv_m_d[kMaxT];
+};
+
+struct Proto {
+  int n_f, schedule;
+  double w_max, sched_n, dt, tau_t;
+  double beta, beta_mu;
+  int no_accept, pad;
+};
+
+struct Rep {
+  double L;
+  float scale;    // L / 2^32 (fixed-point unit in length)
+  float c_drift;  // dt * 2^32 / L
+  int n_water, nw3;
+  int n_pairs, cap_pairs;
+  int atom_off, cap_atoms;
+  int nc;         // cells per dimension (0 = all pairs)
+  int tpa;
+  unsigned long long T_list;   // neighbour criterion threshold (fixed-point units^2)
+  unsigned long long T_move;   // (skin/2)^2 in fixed-point units^2
+  int rec_off, rec_cap;
+  long long rec_count;
+  unsigned long long trial_ctr, step_ctr;
+  // statistics
+  long long cycles, trials_ins, trials_del, acc_ins, acc_del, rej_status, md_steps, builds, err;
+  double sum_n, sum_n2;
+  double t_nemd_ns, t_md_ns;
+  int dirty;      // state changed on the host: rebuild list and forces
+  int pad;
+};
+
+struct Group {
+  int rep, warp0, nwarps, bar, smem_off, pad;
+};
+
+struct Eng {
+  Pot pot;
+  Proto proto;
+  Rep* rep;
+  const Group* groups;
+  const int* cta_groups;  // groups of CTA c are [cta_groups[c], cta_groups[c+1])
+  uint4* pos;
+  float4* vhi;
+  float4* vlo;
+  float4* force;
+  uint4* pos_save;
+  float4* vhi_save;
+  float4* vlo_save;
+  uint4* ref;
+  uint16_t* nbr;
+  int* ncnt;
+  h4d_record* rec;
+  int max_nbr;
+  unsigned long long seed;
+};
+
+// shared-memory bytes a group needs for a replica
+inline size_t group_smem_bytes(int cap_atoms, int nc, int nthreads) {
+  size_t ncell = nc >= 3 ? (size_t)nc * nc * nc : 0;
+  size_t b = 16 * (size_t)cap_atoms;            // positions
+  b += 4 * (ncell + 1) + 4 * ncell;             // cell start + fill
+  b += 2 * (size_t)cap_atoms * 2;               // sorted atoms + cell of atom
+  b = (b + 15) & ~(size_t)15;
+  b += 8 * (size_t)nthreads;                    // reduction scratch
+  b += 640;                                     // per-group scalars
+  return (b + 127) & ~(size_t)127;
+}
+
+// Launches (h4d_engine.cu)
+int launch_cycles(const Eng& e, int n_ctas, int cta_threads, size_t smem, long long k_cycles,
+                  int n_eq, int do_trial, void* stream);
+int launch_energy(const Eng& e, int n_ctas, int cta_threads, size_t smem, double* U, double* K,
+                  void* stream);
+int launch_eval(const Eng& e, int threads, size_t smem, float wbar, double* U, void* stream);
+int launch_list(const Eng& e, int n_ctas, int cta_threads, size_t smem, void* stream);
+int launch_count_pairs(const Eng& e, int n_ctas, int cta_threads, size_t smem,
+                       unsigned long long* out, void* stream);
+
+}  // namespace h4d

@@ -1,0 +1,329 @@
+"""Thin ctypes binding of libh4d (include/h4d.h).  Argument marshalling only: every step
+of the method runs in the library's CUDA kernels.  The functions keep the C names.
+
+The library is built in-tree (``paper_2307_11447_gb300/build.py``); loading fails loudly
+when it is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+H4D_OK = 0
+H4D_EINVAL = -1
+H4D_ECAPACITY = -2
+H4D_ETIMEOUT = -3
+H4D_ENAN = -4
+H4D_ECUDA = -5
+H4D_ENODEV = -6
+H4D_SYS_LJ = 0
+H4D_SYS_AQ = 1
+SCHED = {"linear": 0, "wv": 1, "wx": 2}
+
+
+class H4DError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class h4d_params(ctypes.Structure):
+    _fields_ = [
+        ("system", ctypes.c_int32),
+        ("ntypes", ctypes.c_int32),
+        ("beta", ctypes.c_double),
+        ("beta_mu", ctypes.c_double),
+        ("rc_lj", ctypes.c_double),
+        ("rc_coul", ctypes.c_double),
+        ("alpha", ctypes.c_double),
+        ("kcoul", ctypes.c_double),
+        ("kappa_sr", ctypes.c_double),
+        ("q", ctypes.c_double * 4),
+        ("sig", ctypes.c_double * 4),
+        ("eps", ctypes.c_double * 4),
+        ("mass", ctypes.c_double * 4),
+        ("mvv2e", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("w_max", ctypes.c_double),
+        ("tau_t", ctypes.c_double),
+        ("sched_n", ctypes.c_double),
+        ("n_f", ctypes.c_int32),
+        ("schedule", ctypes.c_int32),
+        ("d_oh", ctypes.c_double),
+        ("d_hh", ctypes.c_double),
+        ("skin", ctypes.c_double),
+        ("max_nbr", ctypes.c_int32),
+        ("threads_per_atom", ctypes.c_int32),
+    ]
+
+
+class h4d_system(ctypes.Structure):
+    _fields_ = [
+        ("n_replicas", ctypes.c_int32),
+        ("L", ctypes.POINTER(ctypes.c_double)),
+        ("n_water", ctypes.POINTER(ctypes.c_int32)),
+        ("n_pairs", ctypes.POINTER(ctypes.c_int32)),
+        ("cap_pairs", ctypes.POINTER(ctypes.c_int32)),
+        ("host_x", ctypes.POINTER(ctypes.c_double)),
+        ("host_v", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class h4d_counts(ctypes.Structure):
+    _fields_ = [
+        ("n_pairs", ctypes.c_int64),
+        ("cycles", ctypes.c_int64),
+        ("trials_ins", ctypes.c_int64),
+        ("trials_del", ctypes.c_int64),
+        ("accepted_ins", ctypes.c_int64),
+        ("accepted_del", ctypes.c_int64),
+        ("rejected_status", ctypes.c_int64),
+        ("md_steps", ctypes.c_int64),
+        ("sum_n", ctypes.c_double),
+        ("sum_n2", ctypes.c_double),
+        ("nbr_builds", ctypes.c_int64),
+        ("error_flags", ctypes.c_int64),
+        ("t_nemd_ns", ctypes.c_double),
+        ("t_md_ns", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+RECORD_DTYPE = np.dtype(
+    [
+        ("move", np.int32),
+        ("accepted", np.int32),
+        ("n_before", np.int32),
+        ("n_after", np.int32),
+        ("status", np.int32),
+        ("cation", np.int32),
+        ("anion", np.int32),
+        ("pad", np.int32),
+        ("dH", np.float64),
+        ("beta_dM", np.float64),
+        ("w_prot", np.float64),
+        ("ln_u", np.float64),
+        ("x_acc", np.float64),
+    ]
+)
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.OUT
+
+
+def lib():
+    """Load libh4d (building it first when the sources are newer)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libh4d.so is missing; the CUDA library is required")
+        L = ctypes.CDLL(path)
+        vp = ctypes.c_void_p
+        pd = ctypes.POINTER(ctypes.c_double)
+        pi32 = ctypes.POINTER(ctypes.c_int32)
+        i32, i64, d = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "h4d_create": ([ctypes.POINTER(h4d_params), ctypes.POINTER(h4d_system), ctypes.c_uint64, vp, ctypes.POINTER(vp)], i32),
+            "h4d_destroy": ([vp], None),
+            "h4d_strerror": ([ctypes.c_int], ctypes.c_char_p),
+            "h4d_set_mu": ([vp, d], i32),
+            "h4d_set_protocol": ([vp, i32, d, d, d, i32], i32),
+            "h4d_set_no_accept": ([vp, i32], i32),
+            "h4d_run_md": ([vp, i64], i32),
+            "h4d_run_trials": ([vp, i64, i32], i32),
+            "h4d_get_counts": ([vp, i32, ctypes.POINTER(h4d_counts)], i32),
+            "h4d_get_energies": ([vp, i32, pd, pd], i32),
+            "h4d_get_work": ([vp, i32, vp, i64, ctypes.POINTER(i64)], i32),
+            "h4d_get_state": ([vp, i32, pd, pd, i64, ctypes.POINTER(i64)], i32),
+            "h4d_set_state": ([vp, i32, i32, pd, pd], i32),
+            "h4d_num_replicas": ([vp], i32),
+            "h4d_count_pairs": ([vp, ctypes.POINTER(i64)], i32),
+            "h4d_save": ([vp, ctypes.c_char_p], i32),
+            "h4d_load": ([vp, ctypes.c_char_p], i32),
+            "h4d_eval_forces": ([ctypes.POINTER(h4d_params), d, i32, i32, pd, pd, pd, pd], i32),
+            "h4d_neighbor_pairs": ([d, i32, pd, d, pi32, pi32, i64, ctypes.POINTER(i64)], i32),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().h4d_strerror(code).decode()
+
+
+def _ck(code: int, where: str):
+    if code != H4D_OK:
+        raise H4DError(code, where)
+
+
+def _pd(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_params(cfg: dict, **override) -> h4d_params:
+    c = dict(cfg)
+    c.update(override)
+    p = h4d_params()
+    p.system = H4D_SYS_LJ if c.get("system", "lj") == "lj" else H4D_SYS_AQ
+    p.ntypes = len(c["q"])
+    p.beta = c["beta"]
+    p.beta_mu = c.get("beta_mu", 0.0)
+    p.rc_lj = c["rc_lj"]
+    p.rc_coul = c["rc_coul"]
+    p.alpha = c["alpha"]
+    p.kcoul = c["kcoul"]
+    p.kappa_sr = c.get("kappa_sr", 0.0)
+    for k in range(p.ntypes):
+        p.q[k] = c["q"][k]
+        p.sig[k] = c["sig"][k]
+        p.eps[k] = c["eps"][k]
+        p.mass[k] = c["mass"][k]
+    p.mvv2e = c.get("mvv2e", 1.0)
+    p.dt = c["dt"]
+    p.w_max = c["w_max"]
+    p.tau_t = c.get("tau_t", 0.0)
+    p.sched_n = c.get("sched_n", 1.0)
+    p.n_f = c["n_f"]
+    s = c.get("schedule", "linear")
+    p.schedule = SCHED[s] if isinstance(s, str) else int(s)
+    p.d_oh = c.get("d_oh", 0.0)
+    p.d_hh = c.get("d_hh", 0.0)
+    p.skin = c.get("skin", 0.3)
+    p.max_nbr = c.get("max_nbr", 0)
+    p.threads_per_atom = c.get("threads_per_atom", 0)
+    return p
+
+
+class Context:
+    """Owns an h4d_ctx.  Replicas: list of dicts with keys L, n_pairs, cap_pairs, x, v
+    (optional), n_water (optional)."""
+
+    def __init__(self, params: h4d_params, replicas: list, seed: int, stream: int | None = None):
+        R = len(replicas)
+        self.params = params
+        L = np.array([r["L"] for r in replicas], np.float64)
+        nw = np.array([r.get("n_water", 0) for r in replicas], np.int32)
+        npair = np.array([r["n_pairs"] for r in replicas], np.int32)
+        cap = np.array([r["cap_pairs"] for r in replicas], np.int32)
+        xs = np.ascontiguousarray(np.concatenate([np.asarray(r["x"], np.float64).reshape(-1, 3) for r in replicas]))
+        have_v = all(r.get("v") is not None for r in replicas)
+        vs = np.ascontiguousarray(np.concatenate([np.asarray(r["v"], np.float64).reshape(-1, 3) for r in replicas])) if have_v else None
+        s = h4d_system()
+        s.n_replicas = R
+        s.L = _pd(L)
+        s.n_water = nw.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        s.n_pairs = npair.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        s.cap_pairs = cap.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        s.host_x = _pd(xs)
+        s.host_v = _pd(vs)
+        h = ctypes.c_void_p()
+        _ck(lib().h4d_create(ctypes.byref(params), ctypes.byref(s), seed, ctypes.c_void_p(stream or 0), ctypes.byref(h)), "h4d_create")
+        self.h = h
+        self.R = R
+        self.cap_atoms = [3 * int(nw[i]) + 2 * int(cap[i]) for i in range(R)]
+
+    def close(self):
+        if self.h:
+            lib().h4d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def h4d_set_mu(self, beta_mu):
+        _ck(lib().h4d_set_mu(self.h, beta_mu), "h4d_set_mu")
+
+    def h4d_set_protocol(self, n_f, w_max, dt, kappa_sr, schedule=0):
+        _ck(lib().h4d_set_protocol(self.h, n_f, w_max, dt, kappa_sr, schedule), "h4d_set_protocol")
+
+    def h4d_set_no_accept(self, on):
+        _ck(lib().h4d_set_no_accept(self.h, int(on)), "h4d_set_no_accept")
+
+    def h4d_run_md(self, n_steps):
+        _ck(lib().h4d_run_md(self.h, n_steps), "h4d_run_md")
+
+    def h4d_run_trials(self, k_cycles, n_eq):
+        _ck(lib().h4d_run_trials(self.h, k_cycles, n_eq), "h4d_run_trials")
+
+    def h4d_get_counts(self, r=0) -> dict:
+        c = h4d_counts()
+        _ck(lib().h4d_get_counts(self.h, r, ctypes.byref(c)), "h4d_get_counts")
+        return c.as_dict()
+
+    def h4d_get_energies(self, r=0):
+        U = ctypes.c_double()
+        K = ctypes.c_double()
+        _ck(lib().h4d_get_energies(self.h, r, ctypes.byref(U), ctypes.byref(K)), "h4d_get_energies")
+        return U.value, K.value
+
+    def h4d_get_work(self, r=0, cap=1024) -> np.ndarray:
+        out = np.zeros(cap, RECORD_DTYPE)
+        n = ctypes.c_int64()
+        _ck(lib().h4d_get_work(self.h, r, out.ctypes.data, cap, ctypes.byref(n)), "h4d_get_work")
+        return out[: n.value]
+
+    def h4d_get_state(self, r=0):
+        cap = self.cap_atoms[r]
+        x = np.zeros((cap, 3))
+        v = np.zeros((cap, 3))
+        n = ctypes.c_int64()
+        _ck(lib().h4d_get_state(self.h, r, _pd(x), _pd(v), cap, ctypes.byref(n)), "h4d_get_state")
+        return x[: n.value].copy(), v[: n.value].copy()
+
+    def h4d_set_state(self, r, n_pairs, x, v):
+        x = np.ascontiguousarray(x, np.float64)
+        v = None if v is None else np.ascontiguousarray(v, np.float64)
+        _ck(lib().h4d_set_state(self.h, r, n_pairs, _pd(x), _pd(v)), "h4d_set_state")
+
+    def h4d_count_pairs(self) -> int:
+        n = ctypes.c_int64()
+        _ck(lib().h4d_count_pairs(self.h, ctypes.byref(n)), "h4d_count_pairs")
+        return n.value
+
+    def h4d_save(self, path):
+        _ck(lib().h4d_save(self.h, path.encode()), "h4d_save")
+
+    def h4d_load(self, path):
+        _ck(lib().h4d_load(self.h, path.encode()), "h4d_load")
+
+
+def h4d_eval_forces(params: h4d_params, L: float, x, w=None, n_water: int = 0):
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    n = x.shape[0]
+    wa = None if w is None else np.ascontiguousarray(w, np.float64)
+    F = np.zeros((n, 3))
+    U = ctypes.c_double()
+    _ck(lib().h4d_eval_forces(ctypes.byref(params), L, n_water, n, _pd(x), _pd(wa), _pd(F), ctypes.byref(U)), "h4d_eval_forces")
+    return U.value, F
+
+
+def h4d_neighbor_pairs(L: float, x, r_list: float):
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    n = x.shape[0]
+    m = ctypes.c_int64()
+    _ck(lib().h4d_neighbor_pairs(L, n, _pd(x), r_list, None, None, 0, ctypes.byref(m)), "h4d_neighbor_pairs")
+    oi = np.zeros(max(m.value, 1), np.int32)
+    oj = np.zeros(max(m.value, 1), np.int32)
+    _ck(
+        lib().h4d_neighbor_pairs(L, n, _pd(x), r_list, oi.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                 oj.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), m.value, ctypes.byref(m)),
+        "h4d_neighbor_pairs",
+    )
+    return oi[: m.value], oj[: m.value]

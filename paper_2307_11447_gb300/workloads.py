@@ -142,9 +142,24 @@ def _pick_far(rng, L, placed, n_new, min_dist, max_tries=200000):
 
 
 def lj_positions(n_pairs: int, L: float, seed: int, min_dist: float = 0.8) -> np.ndarray:
-    """Uniform random ion positions (interleaved cation/anion) with overlap rejection."""
+    """Uniform random ion positions (interleaved cation/anion) with overlap rejection:
+    every atom closer than min_dist (minimum image) to another is redrawn until none is."""
+    from scipy.spatial import cKDTree
+
     rng = np.random.default_rng(seed)
-    return _pick_far(rng, L, [], 2 * n_pairs, min_dist)
+    n = 2 * n_pairs
+    x = rng.random((n, 3)) * L
+    for _ in range(10000):
+        if n < 2:
+            break
+        pairs = cKDTree(np.mod(x, L), boxsize=L).query_pairs(min_dist, output_type="ndarray")
+        if len(pairs) == 0:
+            break
+        bad = np.unique(pairs[:, 1])
+        x[bad] = rng.random((bad.size, 3)) * L
+    else:
+        raise RuntimeError("could not place atoms without overlap")
+    return np.mod(x, L)
 
 
 def batched_replicas(n_rep: int = 256, seed: int = 7, n_min: int = 100, n_max: int = 1000,

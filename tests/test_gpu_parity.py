@@ -1,0 +1,154 @@
+"""GPU (libh4d, sm_103a) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (written here, derived in the design doc):
+  * forces: |F_gpu - F_orc|_i <= 1e-5 (|F_orc|_i + F_rms) per atom (FP32 pair math);
+  * potential energy: FP64 on both sides on identical fixed-point positions, rel 1e-10;
+  * neighbour sets: bit-exact (integer criterion);
+  * per-trial work: |beta dM_gpu - beta dM_orc| <= 1e-4 + 1e-6 |beta dM| (kT units), and
+    strictly <= 1e-4 for trials within 20 kT of the acceptance boundary (|x| < 20); the
+    relative part is the FP32-force floor of trajectories that exchange hundreds of kT;
+  * accept/reject identical wherever |ln u - x| exceeds 1e-3.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2307_11447_gb300 import lib as h4d
+from paper_2307_11447_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TWO32 = 4294967296.0
+
+
+def quantize(x, L):
+    """Positions exactly as the library stores them: 32-bit box fractions."""
+    y = np.mod(x, L)
+    return np.mod(np.rint(y / L * TWO32), TWO32) * (L / TWO32)
+
+
+def force_close(Fg, Fo, rel=1e-5):
+    frms = math.sqrt((Fo**2).sum(1).mean())
+    err = np.linalg.norm(Fg - Fo, axis=1)
+    bound = rel * (np.linalg.norm(Fo, axis=1) + frms)
+    return err, bound
+
+
+def lj_cfg(n_ions, rho, **kw):
+    cfg = wl.lj_config(n_ions, rho, kw.pop("n_f", 100))
+    cfg.update(kw)
+    return cfg
+
+
+@pytest.mark.parametrize("n_ions,rho,seed", [(250, 0.2, 1), (1000, 0.3, 2), (4000, 0.3, 3), (162, 0.2, 4)])
+def test_forces_3d_match_oracle(n_ions, rho, seed):
+    cfg = lj_cfg(n_ions, rho)
+    L = cfg["L"]
+    x = quantize(wl.lj_positions(n_ions // 2, L, seed), L)
+    po = orc.make_params(cfg, use_cells=1)
+    Uo, Fo = orc.energy_forces(po, x)
+    Ug, Fg = h4d.h4d_eval_forces(h4d.make_params(cfg), L, x)
+    err, bound = force_close(Fg, Fo)
+    assert np.all(err <= bound), (err / bound).max()
+    assert Ug == pytest.approx(Uo, rel=1e-10, abs=1e-9)
+
+
+@pytest.mark.parametrize("w_fly,kappa", [(0.6, 0.0), (1.7, 0.8), (3.2, 1.0), (4.0, 0.3)])
+def test_forces_4d_with_flyers_match_oracle(w_fly, kappa):
+    cfg = lj_cfg(250, 0.2, kappa_sr=kappa)
+    L = cfg["L"]
+    x = quantize(wl.lj_positions(125, L, 7), L)
+    w = np.zeros(250)
+    fly = np.zeros(250, np.uint8)
+    fly[[10, 33]] = 1
+    w[[10, 33]] = float(np.float32(w_fly))  # altitudes are stored in FP32 by the library
+    po = orc.make_params(cfg)
+    Uo, Fo = orc.energy_forces(po, x, w, fly)
+    Ug, Fg = h4d.h4d_eval_forces(h4d.make_params(cfg), L, x, w)
+    err, bound = force_close(Fg, Fo)
+    keep = fly == 0  # flyer rows are frozen in NEMD; their 3D force is never used
+    assert np.all(err[keep] <= bound[keep]), (err[keep] / bound[keep]).max()
+    assert Ug == pytest.approx(Uo, rel=1e-10, abs=1e-9)
+
+
+def test_three_d_recovered_on_gpu():
+    cfg = lj_cfg(250, 0.2)
+    L = cfg["L"]
+    x = quantize(wl.lj_positions(125, L, 9), L)
+    p = h4d.make_params(cfg)
+    U3, F3 = h4d.h4d_eval_forces(p, L, x)
+    U4, F4 = h4d.h4d_eval_forces(p, L, x, np.zeros(250))
+    assert U3 == U4 and np.array_equal(F3, F4)
+
+
+@pytest.mark.parametrize("n,L,r_list,seed", [(300, 9.0, 4.3, 1), (2000, 23.7, 4.3, 2), (4001, 23.7, 4.3, 3),
+                                             (777, 14.0, 4.6, 4), (2, 9.0, 4.3, 5), (0, 9.0, 4.3, 6)])
+def test_neighbor_sets_bit_exact(n, L, r_list, seed):
+    x = np.random.default_rng(seed).random((n, 3)) * L
+    oi, oj = orc.neighbor_pairs(x, L, r_list)
+    gi, gj = h4d.h4d_neighbor_pairs(L, x, r_list)
+    assert np.array_equal(oi, gi) and np.array_equal(oj, gj)
+
+
+def _equilibrated_c0(seed=1, steps=300):
+    cfg = dict(wl.CONFIGS["lj250"])
+    cfg.update(seed=seed, replica=0)
+    po = orc.make_params(cfg, use_cells=0)
+    x = wl.lj_positions(cfg["n_pairs"], cfg["L"], seed)
+    st = orc.State(po, quantize(x, cfg["L"]), None, cfg["n_pairs"], cfg["cap_pairs"])
+    orc.init_velocities(po, st)
+    orc.md(po, st, steps)
+    return cfg, st.positions(), st.velocities()
+
+
+def test_single_trials_match_oracle():
+    cfg, x0, v0 = _equilibrated_c0()
+    L = cfg["L"]
+    x0 = quantize(x0, L)
+    n_pairs = cfg["n_pairs"]
+    cfg["beta_mu"] = -8.0
+    po = orc.make_params(cfg)
+    ctx = h4d.Context(h4d.make_params(cfg), [dict(L=L, n_pairs=n_pairs, cap_pairs=cfg["cap_pairs"], x=x0, v=v0)],
+                      seed=cfg["seed"])
+    moves = set()
+    for k in range(12):
+        ctx.h4d_set_state(0, n_pairs, x0, v0)
+        ctx.h4d_run_trials(1, 0)
+        rg = ctx.h4d_get_work(0, 1)[0]
+        st = orc.State(po, x0, v0, n_pairs, cfg["cap_pairs"])
+        st.s.trial_ctr = k
+        ro = orc.trial(po, st)
+        moves.add(int(ro["move"]))
+        assert rg["move"] == ro["move"] and rg["cation"] == ro["cation"] and rg["anion"] == ro["anion"]
+        assert rg["status"] == ro["status"] == 0
+        assert rg["ln_u"] == pytest.approx(ro["ln_u"], abs=1e-14)
+        err = abs(rg["beta_dM"] - ro["beta_dM"])
+        assert err <= 1e-4 + 1e-6 * abs(ro["beta_dM"]), (k, rg["beta_dM"], ro["beta_dM"])
+        if abs(ro["x_acc"]) < 20:
+            assert err <= 1e-4, (k, rg["beta_dM"], ro["beta_dM"])
+        if abs(ro["ln_u"] - ro["x_acc"]) > 1e-3:
+            assert rg["accepted"] == ro["accepted"]
+        xg, vg = ctx.h4d_get_state(0)
+        xo, vo = st.positions(), st.velocities()
+        assert xg.shape == xo.shape
+        d = xg - xo
+        d -= L * np.round(d / L)
+        assert np.abs(d).max() < 1e-5
+        assert np.abs(vg - vo).max() < 1e-4
+    assert moves == {0, 1}
+
+
+def test_energy_getter_matches_oracle():
+    cfg, x0, v0 = _equilibrated_c0(seed=2, steps=50)
+    L = cfg["L"]
+    x0 = quantize(x0, L)
+    ctx = h4d.Context(h4d.make_params(cfg), [dict(L=L, n_pairs=cfg["n_pairs"], cap_pairs=cfg["cap_pairs"], x=x0, v=v0)],
+                      seed=3)
+    U, K = ctx.h4d_get_energies(0)
+    po = orc.make_params(cfg)
+    Uo, _ = orc.energy_forces(po, x0)
+    Ko = orc.kinetic(po, v0)
+    assert U == pytest.approx(Uo, rel=1e-10)
+    assert K == pytest.approx(Ko, rel=1e-7)
