@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--workload", default="lj4000")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--equil", type=int, default=1000)
+    ap.add_argument("--n-eq", type=int, default=None, help="override equilibrium steps per cycle (profiling)")
+    ap.add_argument("--n-f", type=int, default=None, help="override NEMD steps per trial (profiling)")
+    ap.add_argument("--tune-iters", type=int, default=20, help="force passes per autotuner candidate")
     return ap.parse_args()
 
 
@@ -58,6 +61,10 @@ def workload(name, chains, rank):
     from paper_2307_11447_gb300 import workloads as wl
 
     cfg = dict(wl.CONFIGS[name])
+    if ARGS.n_eq is not None:
+        cfg["n_eq"] = ARGS.n_eq
+    if ARGS.n_f is not None:
+        cfg["n_f"] = ARGS.n_f
     reps = []
     for c in range(chains):
         seed = 1000 * (rank + 1) + c
@@ -143,8 +150,13 @@ def run_gpu(args):
     with torch.cuda.stream(stream):
         ctx = h4d.Context(params, reps, seed=12345 + rank, stream=stream.cuda_stream)
     n_eq, n_f = cfg["n_eq"], cfg["n_f"]
-    # equilibrate the random starts (untimed), then warm up
+    # equilibrate the random starts (untimed), autotune the force pass, then warm up
     ctx.h4d_run_md(args.equil)
+    tune = ctx.h4d_autotune(args.tune_iters)
+    tpa_hist = {}
+    for r in range(ctx.R):
+        t = ctx.h4d_get_counts(r)["threads_per_atom"]
+        tpa_hist[t] = tpa_hist.get(t, 0) + 1
     for _ in range(args.warmup):
         ctx.h4d_run_trials(1, n_eq)
     torch.cuda.synchronize()
@@ -180,9 +192,13 @@ def run_gpu(args):
         atom_steps += n_atoms * (n_eq + n_f) * args.steps
         nemd_atom_steps += n_atoms * n_f * args.steps
         accepted += (b["accepted_ins"] + b["accepted_del"]) - (a["accepted_ins"] + a["accepted_del"])
+    builds = sum(b["nbr_builds"] - a["nbr_builds"] for a, b in zip(c0, c1))
     t_nemd = sum(b["t_nemd_ns"] - a["t_nemd_ns"] for a, b in zip(c0, c1)) / 1e9
     t_md = sum(b["t_md_ns"] - a["t_md_ns"] for a, b in zip(c0, c1)) / 1e9
     nemd_frac = t_nemd / max(t_nemd + t_md, 1e-30)
+    t_all = max(t_nemd + t_md, 1e-30)
+    phase = {k: sum(b[f"t_{k}_ns"] - a[f"t_{k}_ns"] for a, b in zip(c0, c1)) / 1e9 / t_all
+             for k in ("build", "force", "energy")}
     tmax = t_ms
     tot = np.array([atom_steps, nemd_atom_steps, accepted], np.float64)
     if world > 1:
@@ -228,6 +244,11 @@ def run_gpu(args):
             "nemd_4d_atom_steps_per_s": tot[1] / (secs * nemd_frac) if nemd_frac > 0 else None,
             "accepted_exchanges_per_s": tot[2] / secs,
             "accepted": int(tot[2]),
+            "md_steps_per_nbr_build": (n_eq + n_f) * args.steps * len(c0) / max(builds, 1),
+            "nemd_time_fraction": nemd_frac,
+            "phase_time_fraction": phase,
+            "autotuned_threads_per_atom": {str(k): v for k, v in sorted(tpa_hist.items())},
+            "autotune_us_per_force_pass_and_build": {str(k): [round(a / 1e3, 1), round(b / 1e3, 1)] for k, (a, b) in tune.items()},
             "trials": int(args.chains * world * args.steps),
             "gpu_launches": args.steps,
             "clocks": clk,
@@ -239,7 +260,7 @@ def run_gpu(args):
             "e2e": e2e,
         }
         if rank == 0 and os.environ.get("H4D_BENCH_CPU", "1") == "1":
-            out["cpu_baseline"] = cpu_baseline(args.workload, sample_steps=8)
+            out["cpu_baseline"] = cpu_baseline(args.workload, sample_steps=60)
         print(json.dumps(out), flush=True)
     ctx.close()
     if world > 1:
@@ -360,8 +381,13 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+ARGS = None
+
+
 def main():
+    global ARGS
     args = parse()
+    ARGS = args
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -83,7 +83,8 @@ typedef struct h4d_params {
   int32_t n_f;            /* NEMD steps per trial */
   int32_t schedule;       /* H4D_SCHED_* */
   double d_oh, d_hh;      /* rigid water bond lengths (O-H, H-H) */
-  double skin;            /* neighbour-list skin; the list is rebuilt when an atom moved skin/2 */
+  double skin;            /* Verlet-list skin: rebuilt when the two largest displacements sum to it */
+  double skin_outer;      /* skin of the outer list the Verlet list is filtered from (0 = 4 skin) */
   int32_t max_nbr;        /* neighbour-row capacity per atom; 0 = derived from density */
   int32_t threads_per_atom; /* 1,2,4,8,16 or 32; 0 = autotune per replica size */
 } h4d_params;
@@ -113,6 +114,10 @@ typedef struct h4d_counts {
   int64_t nbr_builds;       /* neighbour-list builds */
   int64_t error_flags;      /* bit 0 row overflow, bit 1 non-finite MD state, bit 2 timeout */
   double t_nemd_ns, t_md_ns; /* device time spent in NEMD trials and equilibrium MD */
+  double t_build_ns;        /* of which: neighbour-list builds */
+  double t_force_ns;        /* of which: FP32 force passes */
+  double t_energy_ns;       /* of which: FP64 end-point energies */
+  int64_t threads_per_atom; /* lanes that share one neighbour row in the force pass */
 } h4d_counts;
 
 /* One trial record; Delta M follows the insertion direction (Eqs. 6, 8). */
@@ -156,6 +161,13 @@ int h4d_run_md(h4d_ctx* ctx, int64_t n_steps);
  * then one insertion or deletion trial (NEMD + Metropolis + commit).  One persistent
  * launch runs all cycles of all replicas. */
 int h4d_run_trials(h4d_ctx* ctx, int64_t k_cycles, int32_t n_eq);
+
+/* Autotuner: for every replica, time n_iter equilibrium force passes (device timers) for
+ * each threads-per-atom value in {1, 2, 4, 8, 16} and keep the fastest.  State and
+ * counters are left as they were; synchronises the stream.  When not NULL, host_pass_ns
+ * and host_build_ns (5 entries each, one per candidate) receive the mean device time of
+ * one force pass and of one neighbour build per replica. */
+int h4d_autotune(h4d_ctx* ctx, int32_t n_iter, double* host_pass_ns, double* host_build_ns);
 
 /* ---- getters (synchronise the context stream) ---- */
 int h4d_get_counts(h4d_ctx* ctx, int32_t replica, h4d_counts* out);

@@ -13,6 +13,8 @@ BUILD = os.path.join(HERE, "_build")
 SOURCES = ["h4d_engine.cu", "h4d_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+# extra preprocessor defines (e.g. engine launch bounds), space separated
+DEFINES = os.environ.get("H4D_NVCC_DEFINES", "").split()
 
 
 def _nvcc() -> str:
@@ -38,7 +40,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *DEFINES, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

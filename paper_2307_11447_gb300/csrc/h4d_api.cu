@@ -23,6 +23,7 @@ struct h4d_ctx {
   int R;
   int total_atoms;
   int max_nbr;
+  int max_out;
   int cta_threads;
   int n_ctas;
   size_t smem;
@@ -44,6 +45,9 @@ struct h4d_ctx {
   uint4* d_ref = nullptr;
   uint16_t* d_nbr = nullptr;
   int* d_ncnt = nullptr;
+  uint16_t* d_nbr_out = nullptr;
+  int* d_ncnt_out = nullptr;
+  uint4* d_ref_out = nullptr;
   h4d_record* d_rec = nullptr;
   double* d_scratch = nullptr;
   unsigned long long* d_count = nullptr;
@@ -77,7 +81,7 @@ static int check_params(const h4d_params* p) {
   if (p->system != H4D_SYS_LJ && p->system != H4D_SYS_AQ) return H4D_EINVAL;
   if (p->ntypes < 2 || p->ntypes > 4) return H4D_EINVAL;
   if (!(p->beta > 0) || !(p->dt > 0) || !(p->rc_lj > 0) || !(p->rc_coul > 0)) return H4D_EINVAL;
-  if (p->n_f < 1 || p->w_max < 0 || p->skin < 0) return H4D_EINVAL;
+  if (p->n_f < 1 || p->w_max < 0 || p->skin < 0 || p->skin_outer < 0) return H4D_EINVAL;
   if (p->schedule < 0 || p->schedule > 2) return H4D_EINVAL;
   if (p->threads_per_atom != 0 && (p->threads_per_atom & (p->threads_per_atom - 1))) return H4D_EINVAL;
   if (p->threads_per_atom > 32) return H4D_EINVAL;
@@ -133,6 +137,7 @@ static void fill_pot(const h4d_params& p, Pot& P, Proto& pr) {
     double m = (t < p.ntypes) ? p.mass[t] * p.mvv2e : 1.0;
     P.dm[t] = m;
     P.inv_m[t] = (float)(1.0 / m);
+    P.m_f[t] = (float)m;
     P.inv_m_d[t] = 1.0 / m;
   }
   P.d_oh2 = p.d_oh * p.d_oh;
@@ -150,6 +155,16 @@ static void fill_pot(const h4d_params& p, Pot& P, Proto& pr) {
 
 // neighbour-row capacity from the densest plausible packing (about one particle per sigma^3
 // for the LJ electrolyte, liquid water for the aqueous system)
+static double outer_skin(const h4d_params& p) {
+  return std::max(p.skin_outer > 0 ? p.skin_outer : 4.0 * p.skin, p.skin);
+}
+
+static int derive_max_rows(const h4d_params& p, double rl) {
+  double rho = (p.system == H4D_SYS_LJ) ? 1.05 / std::pow(p.sig[0], 3) : 0.105;
+  int m = (int)std::ceil(4.0 / 3.0 * M_PI * rl * rl * rl * rho * 1.1) + 16;
+  return ((m + 127) / 128) * 128;
+}
+
 static int derive_max_nbr(const h4d_params& p) {
   double rl = rmax_of(p) + p.skin;
   double rho = (p.system == H4D_SYS_LJ) ? 1.05 / std::pow(p.sig[0], 3) : 0.105;
@@ -175,12 +190,26 @@ static void set_rep_geometry(const h4d_params& p, Rep& r, double L) {
   r.scale = (float)(L / kTwo32);
   r.c_drift = (float)(p.dt * kTwo32 / L);
   double rl = rmax_of(p) + p.skin;
-  int nc = std::min((int)std::floor(L / rl), 16);  // bigger cells stay valid, smem stays bounded
-  r.nc = (nc >= 3) ? nc : 0;
+  double ro = rmax_of(p) + outer_skin(p);
+  // cells (for the outer list) of at least r_outer with a 3^3 stencil, else all pairs;
+  // capped so the cell table stays small in shared memory (bigger cells remain valid)
+  int nc1 = std::min((int)std::floor(L / ro), 8);
+  if (nc1 >= 3) { r.nc = nc1; r.reach = 1; }
+  else { r.nc = 0; r.reach = 0; }
   double s = rl / L * kTwo32;
   r.T_list = (unsigned long long)(s * s);
   double h = 0.5 * p.skin / L * kTwo32;
   r.T_move = (unsigned long long)(h * h);
+  r.skin_fx = (float)(p.skin / L * kTwo32);
+  double so = ro / L * kTwo32;
+  r.T_out = (unsigned long long)(so * so);
+  // 16-bit coordinates floor each difference, so |d16| <= |d|/q + 1 per axis and the
+  // 16-bit length is at most |d|/q + sqrt(3); a radius of ceil(r/q) + 2 covers it
+  double r16 = std::ceil(ro / L * 65536.0) + 2.0;
+  r.T16_out = (unsigned)std::min(r16 * r16, 4.0e9);
+  double r8 = std::ceil(ro / L * 256.0) + 2.0;  // same bound on 8-bit coordinates
+  r.T8_out = (unsigned)std::min(r8 * r8, 4.0e9);
+  r.skin_out_fx = (float)(outer_skin(p) / L * kTwo32);
 }
 
 static int alloc_all(h4d_ctx* c) {
@@ -195,6 +224,10 @@ static int alloc_all(h4d_ctx* c) {
   CK(cudaMalloc(&c->d_ref, na * sizeof(uint4)));
   CK(cudaMalloc(&c->d_nbr, na * (size_t)c->max_nbr * sizeof(uint16_t)));
   CK(cudaMalloc(&c->d_ncnt, na * sizeof(int)));
+  CK(cudaMalloc(&c->d_nbr_out, na * (size_t)c->max_out * sizeof(uint16_t)));
+  CK(cudaMalloc(&c->d_ncnt_out, na * sizeof(int)));
+  CK(cudaMalloc(&c->d_ref_out, na * sizeof(uint4)));
+  CK(cudaMemset(c->d_ncnt_out, 0, na * sizeof(int)));
   CK(cudaMemset(c->d_pos, 0, na * sizeof(uint4)));
   CK(cudaMemset(c->d_vhi, 0, na * sizeof(float4)));
   CK(cudaMemset(c->d_vlo, 0, na * sizeof(float4)));
@@ -228,8 +261,12 @@ static void fill_eng(h4d_ctx* c) {
   e.ref = c->d_ref;
   e.nbr = c->d_nbr;
   e.ncnt = c->d_ncnt;
+  e.nbr_out = c->d_nbr_out;
+  e.ncnt_out = c->d_ncnt_out;
+  e.ref_out = c->d_ref_out;
   e.rec = c->d_rec;
   e.max_nbr = c->max_nbr;
+  e.max_out = c->max_out;
   e.seed = c->seed;
 }
 
@@ -407,8 +444,9 @@ int h4d_create(const h4d_params* params, const h4d_system* sys, uint64_t seed, v
     R.rec_off = r * R.rec_cap;
   }
   c->total_atoms = off;
-  // the neighbour rows are tpa-interleaved: capacity must be a multiple of every tpa used
-  c->max_nbr = ((c->max_nbr + 31) / 32) * 32;
+  // rows are packed 4 per lane and tpa-interleaved: capacity is a multiple of 4 * 32
+  c->max_nbr = ((c->max_nbr + 127) / 128) * 128;
+  c->max_out = std::max(c->max_nbr, derive_max_rows(*params, rmax_of(*params) + outer_skin(*params)));
   rc = make_plan(c);
   if (rc) { delete c; return rc; }
   rc = alloc_all(c);
@@ -432,7 +470,7 @@ void h4d_destroy(h4d_ctx* c) {
   if (!c) return;
   void* ptrs[] = {c->d_rep, c->d_groups, c->d_cta_groups, c->d_pos, c->d_vhi, c->d_vlo, c->d_force,
                   c->d_pos_save, c->d_vhi_save, c->d_vlo_save, c->d_ref, c->d_nbr, c->d_ncnt, c->d_rec,
-                  c->d_scratch, c->d_count};
+                  c->d_scratch, c->d_count, c->d_nbr_out, c->d_ncnt_out, c->d_ref_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -491,6 +529,46 @@ int h4d_run_trials(h4d_ctx* c, int64_t k_cycles, int32_t n_eq) {
 
 int32_t h4d_num_replicas(h4d_ctx* c) { return c ? c->R : 0; }
 
+int h4d_autotune(h4d_ctx* c, int32_t n_iter, double* pass_ns, double* build_ns) {
+  if (!c || n_iter < 1 || n_iter > 100000) return H4D_EINVAL;
+  int rc = pull_reps(c);
+  if (rc) return rc;
+  const std::vector<Rep> saved = c->rep_h;
+  const int cand[5] = {1, 2, 4, 8, 16};
+  std::vector<double> best_t(c->R, 1e300);
+  std::vector<int> best(c->R, saved.empty() ? 4 : saved[0].tpa);
+  for (int k = 0; k < 5; ++k) {
+    for (int r = 0; r < c->R; ++r) {
+      c->rep_h[r] = saved[r];
+      c->rep_h[r].tpa = cand[k];
+      c->rep_h[r].t_force_ns = 0.0;
+      c->rep_h[r].t_build_ns = 0.0;
+    }
+    rc = push_plan(c);
+    if (rc) return rc;
+    rc = launch_forces(c->eng, c->n_ctas, c->cta_threads, c->smem, n_iter, c->stream);
+    if (rc) return rc;
+    rc = pull_reps(c);
+    if (rc) return rc;
+    double fsum = 0.0, bsum = 0.0;
+    for (int r = 0; r < c->R; ++r) {
+      if (c->rep_h[r].t_force_ns < best_t[r]) { best_t[r] = c->rep_h[r].t_force_ns; best[r] = cand[k]; }
+      fsum += c->rep_h[r].t_force_ns;
+      bsum += c->rep_h[r].t_build_ns;
+    }
+    if (pass_ns) pass_ns[k] = fsum / c->R / n_iter;
+    if (build_ns) build_ns[k] = bsum / c->R;
+  }
+  for (int r = 0; r < c->R; ++r) {
+    c->rep_h[r] = saved[r];
+    c->rep_h[r].tpa = best[r];
+  }
+  rc = push_plan(c);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return H4D_OK;
+}
+
 int h4d_get_counts(h4d_ctx* c, int32_t r, h4d_counts* out) {
   if (!c || !out || r < 0 || r >= c->R) return H4D_EINVAL;
   int rc = pull_reps(c);
@@ -510,6 +588,10 @@ int h4d_get_counts(h4d_ctx* c, int32_t r, h4d_counts* out) {
   out->error_flags = R.err;
   out->t_nemd_ns = R.t_nemd_ns;
   out->t_md_ns = R.t_md_ns;
+  out->t_build_ns = R.t_build_ns;
+  out->t_force_ns = R.t_force_ns;
+  out->t_energy_ns = R.t_energy_ns;
+  out->threads_per_atom = R.tpa;
   return H4D_OK;
 }
 
@@ -681,7 +763,8 @@ int h4d_eval_forces(const h4d_params* params, double L, int32_t n_water, int32_t
   c->stream = 0;
   c->R = 1;
   c->max_nbr = params->max_nbr > 0 ? params->max_nbr : derive_max_nbr(*params);
-  c->max_nbr = ((c->max_nbr + 31) / 32) * 32;
+  c->max_nbr = ((c->max_nbr + 127) / 128) * 128;
+  c->max_out = std::max(c->max_nbr, derive_max_rows(*params, rmax_of(*params) + outer_skin(*params)));
   c->rep_h.resize(1);
   Rep& R = c->rep_h[0];
   std::memset(&R, 0, sizeof(Rep));
@@ -750,7 +833,8 @@ int h4d_neighbor_pairs(double L, int32_t n, const double* x, double r_list, int3
   c->seed = 0;
   c->stream = 0;
   c->R = 1;
-  c->max_nbr = ((std::min(std::max(n, 1), 4096) + 31) / 32) * 32;
+  c->max_nbr = ((std::min(std::max(n, 1), 4096) + 127) / 128) * 128;
+  c->max_out = c->max_nbr;
   c->rep_h.resize(1);
   Rep& R = c->rep_h[0];
   std::memset(&R, 0, sizeof(Rep));
@@ -787,7 +871,7 @@ int h4d_neighbor_pairs(double L, int32_t n, const double* x, double r_list, int3
     for (int i = 0; i < n; ++i) {
       std::vector<int> row;
       for (int s = 0; s < cnt[i]; ++s) {
-        int j = nb[(size_t)s * R.cap_atoms + i];  // tpa = 1 layout
+        int j = nb[((size_t)(s >> 2) * R.cap_atoms + i) * 4 + (s & 3)];  // tpa = 1 packet layout
         if (j > i && j < n) row.push_back(j);
       }
       std::sort(row.begin(), row.end());

@@ -13,6 +13,14 @@
 
 #include "h4d_engine.cuh"
 
+// Engine launch bounds: threads per CTA and CTAs per SM the register allocation targets
+#ifndef H4D_MAXTHREADS
+#define H4D_MAXTHREADS 1024
+#endif
+#ifndef H4D_MINBLOCKS
+#define H4D_MINBLOCKS 1
+#endif
+
 namespace h4d {
 
 typedef unsigned long long u64;
@@ -59,6 +67,11 @@ __device__ __forceinline__ void gsync(int bar, int nthreads) {
 
 __device__ __forceinline__ int type_of(int a, int nw3) {
   return a < nw3 ? ((a % 3 == 0) ? 2 : 3) : ((a - nw3) & 1);
+}
+template <int SYS>
+__device__ __forceinline__ int type_t(int a, int nw3) {
+  if (SYS == H4D_SYS_LJ) return a & 1;  // no waters: ions alternate cation/anion
+  return type_of(a, nw3);
 }
 
 // float-float accumulate: (hi, lo) += d
@@ -194,6 +207,9 @@ struct GScal {
   double vfly[6];
   unsigned int xfly[6];
   double kw[32];
+  float d1w[32], d2w[32];  // per-warp largest and second-largest displacement since the build
+  float o1w[32], o2w[32];  // the same since the outer-list build
+  int next_item, n_items;  // dynamic work items of the outer build
 };
 
 struct GView {
@@ -201,38 +217,86 @@ struct GView {
   int* cstart;
   int* cfill;
   uint16_t* sorted;
-  uint16_t* cellof;
-  double* red;
+  unsigned* sorted8;  // packed 8-bit box coordinates of the sorted list (x | y<<8 | z<<16)
   GScal* s;
 };
 
 __device__ __forceinline__ GView carve(char* base, int cap_atoms, int nc, int nthreads) {
+  (void)nthreads;
   GView v;
-  size_t ncell = nc >= 3 ? (size_t)nc * nc * nc : 0;
+  size_t ncell = nc > 0 ? (size_t)nc * nc * nc : 0;
+  size_t slots = (size_t)cap_atoms + 3 * ncell;
   char* p = base;
-  v.pos = (uint4*)p; p += 16 * (size_t)cap_atoms;
-  v.cstart = (int*)p; p += 4 * (ncell + 1);
-  v.cfill = (int*)p; p += 4 * ncell;
-  v.sorted = (uint16_t*)p; p += 2 * (size_t)cap_atoms;
-  v.cellof = (uint16_t*)p; p += 2 * (size_t)cap_atoms;
-  size_t off = (size_t)(p - base);
-  off = (off + 15) & ~(size_t)15;
-  p = base + off;
-  v.red = (double*)p; p += 8 * (size_t)nthreads;
+  v.pos = (uint4*)p; p += smem_align16(16 * (size_t)cap_atoms);
+  v.cstart = (int*)p; p += smem_align16(4 * (ncell + 1));
+  v.cfill = (int*)p; p += smem_align16(4 * (ncell + 1));
+  v.sorted = (uint16_t*)p; p += smem_align16(2 * slots);
+  v.sorted8 = (unsigned*)p; p += smem_align16(4 * slots);
   v.s = (GScal*)p;
   return v;
 }
 
+__device__ __forceinline__ unsigned pack8(const uint4& p) {
+  return (p.x >> 24) | ((p.y >> 24) << 8) | ((p.z >> 24) << 16);
+}
+
+// read-only geometry of the group's replica, held in registers for the whole launch so
+// inner loops never reload it from global memory
+struct RepC {
+  double L;
+  float scale, c_drift;
+  int n_water, nw3, atom_off, cap_atoms, nc, cap_pairs;
+  unsigned long long T_list, T_move;
+  float skin_fx;      // Verlet-list skin in fixed-point units
+  float skin_out_fx;  // outer-list skin in fixed-point units
+  unsigned long long T_out;
+  unsigned T16_out;   // conservative outer threshold on 16-bit coordinates
+  unsigned T8_out;    // conservative outer threshold on 8-bit coordinates
+};
+
+__device__ __forceinline__ RepC repc_of(const Rep& R) {
+  RepC r;
+  r.L = R.L; r.scale = R.scale; r.c_drift = R.c_drift;
+  r.n_water = R.n_water; r.nw3 = R.nw3; r.atom_off = R.atom_off; r.cap_atoms = R.cap_atoms;
+  r.nc = R.nc; r.cap_pairs = R.cap_pairs; r.T_list = R.T_list; r.T_move = R.T_move;
+  r.skin_fx = R.skin_fx;
+  r.skin_out_fx = R.skin_out_fx;
+  r.T_out = R.T_out;
+  r.T16_out = R.T16_out;
+  r.T8_out = R.T8_out;
+  return r;
+}
+
 struct Ctx {
   GView v;
+  RepC r;
   Rep* R;
   const Eng* e;
-  int tid, T, bar, tpa;
+  int tid, T, bar, tpa, ltpa;
   __device__ void sync() const { gsync(bar, T); }
 };
 
-__device__ __forceinline__ size_t nbr_index(const Eng& e, const Rep& R, int i, int s, int tpa) {
-  return (size_t)R.atom_off * e.max_nbr + ((size_t)(s / tpa) * R.cap_atoms + i) * tpa + (s % tpa);
+// Row slot s of atom i lives in packet P = s/4 (element s%4).  Packets are dealt to the
+// atom's tpa lanes round-robin (lane P % tpa, its (P / tpa)-th packet), and the packets of
+// consecutive atoms are adjacent, so one 8-byte load per lane gives four neighbours and a
+// warp reads 256 contiguous bytes.  Builders fill a row packet by packet and store whole
+// packets; the last packet of a row is padded with kNoAtom.
+constexpr uint16_t kNoAtom = 0xFFFF;
+__device__ __forceinline__ size_t packet_index(const Eng& e, const RepC& R, int i, int P, int ltpa) {
+  return (size_t)R.atom_off * e.max_nbr / 4 + ((((size_t)(P >> ltpa) * R.cap_atoms + i) << ltpa) + (P & ((1 << ltpa) - 1)));
+}
+__device__ __forceinline__ size_t nbr_index(const Eng& e, const RepC& R, int i, int s, int ltpa) {
+  return packet_index(e, R, i, s >> 2, ltpa) * 4 + (s & 3);
+}
+// outer rows: one lane per atom (packets of four indices, consecutive atoms adjacent)
+__device__ __forceinline__ size_t out_packet_index(const Eng& e, const RepC& R, int i, int P) {
+  return (size_t)R.atom_off * e.max_out / 4 + (size_t)P * R.cap_atoms + i;
+}
+__device__ __forceinline__ const uint2* out_packets(const Eng& e, const RepC& R) {
+  return reinterpret_cast<const uint2*>(e.nbr_out + (size_t)R.atom_off * e.max_out);
+}
+__device__ __forceinline__ const uint2* nbr_packets(const Eng& e, const RepC& R) {
+  return reinterpret_cast<const uint2*>(e.nbr + (size_t)R.atom_off * e.max_nbr);
 }
 
 // deterministic group-wide FP64 sum: warp butterflies, then thread 0 adds warp slots in order
@@ -257,6 +321,29 @@ __device__ double group_sum(const Ctx& c, double x) {
   return c.v.s->red_out;
 }
 
+__device__ __forceinline__ u64 gtimer() {
+  u64 t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// four row entries collected in a 64-bit shift register and stored as one 8-byte packet
+// (first entry in the low 16 bits); a partial packet is completed with kNoAtom
+struct RowBuf {
+  unsigned long long b;
+  int n;
+  __device__ __forceinline__ void init() { b = ~0ull; n = 0; }
+  __device__ __forceinline__ void put(int j) {
+    b = (b >> 16) | ((unsigned long long)(unsigned)j << 48);
+    ++n;
+  }
+  __device__ __forceinline__ uint2 packet() const {
+    const unsigned long long x = b >> (16 * (4 - n));  // shift in kNoAtom for missing entries
+    const unsigned long long y = x | (n == 4 ? 0ull : (~0ull << (16 * n)));
+    return make_uint2((unsigned)y, (unsigned)(y >> 32));
+  }
+};
+
 // ------------------------------------------------------------------------------------
 // Neighbour list: fixed-point cells, deterministic stable counting sort, full rows
 // ------------------------------------------------------------------------------------
@@ -272,34 +359,52 @@ __device__ __forceinline__ u64 fixed_d2(const uint4& a, const uint4& b) {
   return (u64)(dx * dx) + (u64)(dy * dy) + (u64)(dz * dz);
 }
 
+// Conservative squared distance on the top 16 bits of the fixed-point coordinates (32-bit
+// arithmetic, about 3 ALU ops per axis).  With T16 = ceil(r/q + 1)^2 (q = L/2^16), every
+// pair closer than r passes; a few pairs slightly farther may pass too, which is harmless
+// for the outer list because the Verlet rows apply the exact criterion.
+__device__ __forceinline__ unsigned d2_16(const uint4& a, const uint4& b) {
+  const int dx = (int)(a.x - b.x) >> 16, dy = (int)(a.y - b.y) >> 16, dz = (int)(a.z - b.z) >> 16;
+  return (unsigned)(dx * dx) + (unsigned)(dy * dy) + (unsigned)(dz * dz);
+}
+
 __device__ __forceinline__ bool excluded_pair(int i, int j, int nw3) {
   return i < nw3 && j < nw3 && (i / 3) == (j / 3);
 }
 
+__device__ void build_list_impl(const Ctx& c);
+__device__ void filter_list_impl(const Ctx& c);
+// full build: outer rows from the cell grid, then the Verlet rows filtered from them
 __device__ void build_list(const Ctx& c) {
+  const u64 t0 = (c.tid == 0) ? gtimer() : 0;
+  build_list_impl(c);
+  filter_list_impl(c);
+  if (c.tid == 0) c.R->t_build_ns += (double)(gtimer() - t0);
+}
+// Verlet rows only, filtered from the outer rows (valid while the outer list is)
+__device__ void refresh_list(const Ctx& c) {
+  const u64 t0 = (c.tid == 0) ? gtimer() : 0;
+  filter_list_impl(c);
+  if (c.tid == 0) c.R->t_build_ns += (double)(gtimer() - t0);
+}
+__device__ void build_list_impl(const Ctx& c) {
   const Eng& e = *c.e;
-  Rep& R = *c.R;
+  const RepC& R = c.r;
   GView& v = const_cast<GView&>(c.v);
   const int n = v.s->n_tot;
   const int nc = R.nc;
-  const int tpa = c.tpa;
-  const int maxn = e.max_nbr;
-  if (nc >= 3) {
+  if (nc > 0) {
     const int ncell = nc * nc * nc;
     for (int k = c.tid; k < ncell; k += c.T) v.cfill[k] = 0;
     c.sync();
-    for (int a = c.tid; a < n; a += c.T) {
-      int cc = cell_of_pos(v.pos[a], nc);
-      v.cellof[a] = (uint16_t)cc;
-      atomicAdd(&v.cfill[cc], 1);
-    }
+    for (int a = c.tid; a < n; a += c.T) atomicAdd(&v.cfill[cell_of_pos(v.pos[a], nc)], 1);
     c.sync();
     if (c.tid < 32) {  // exclusive scan over cells by warp 0
       int lane = c.tid;
       int carry = 0;
       for (int b = 0; b < ncell; b += 32) {
         int k = b + lane;
-        int x = (k < ncell) ? v.cfill[k] : 0;
+        int x = (k < ncell) ? ((v.cfill[k] + 3) & ~3) : 0;  // cells padded to 4 entries
         int incl = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -311,71 +416,210 @@ __device__ void build_list(const Ctx& c) {
       }
       if (lane == 0) v.cstart[ncell] = carry;
       __syncwarp();
+      for (int q = lane; q < carry; q += 32) v.sorted[q] = kNoAtom;
+      __syncwarp();
       // stable scatter: atoms of a cell end up in ascending index order
       unsigned lt = (1u << lane) - 1u;
       for (int b = 0; b < n; b += 32) {
         int a = b + lane;
-        int cc = (a < n) ? (int)v.cellof[a] : -1 - lane;
+        int cc = (a < n) ? cell_of_pos(v.pos[a], nc) : -1 - lane;
         unsigned peers = __match_any_sync(0xffffffffu, cc);
         int rank = __popc(peers & lt);
         int base = (a < n) ? v.cfill[cc] : 0;
         __syncwarp();
         if (a < n) {
           v.sorted[base + rank] = (uint16_t)a;
+          v.sorted8[base + rank] = pack8(v.pos[a]);
           if (rank == 0) v.cfill[cc] = base + __popc(peers);
         }
         __syncwarp();
       }
+      // work items = (cell, 32-atom home pass); cfill becomes their exclusive prefix
+      int carry2 = 0;
+      for (int b = 0; b < ncell; b += 32) {
+        int k = b + lane;
+        int x = (k < ncell) ? (v.cstart[k + 1] - v.cstart[k] + 31) >> 5 : 0;
+        int incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        if (k < ncell) v.cfill[k] = carry2 + incl - x;
+        carry2 += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      if (lane == 0) { v.s->n_items = carry2; v.s->next_item = 0; }
     }
     c.sync();
   }
-  // rows: one thread per atom, fixed cell order, ascending index within a cell
+  // Rows: one warp per cell, its lanes holding up to 32 home atoms of the cell at a time.
+  // The candidates of the 27 stencil cells stream through the warp one at a time, so
+  // every lane reads the same shared-memory word (broadcast, no bank conflicts); each lane
+  // appends the accepted candidates to its own row.  Cells are visited in a fixed order
+  // and hold their atoms in ascending index order, so a row does not depend on the thread
+  // mapping.  Without cells (small boxes) every atom is a candidate of every atom.
+  const int nwarps = c.T >> 5, warp = c.tid >> 5, lane = c.tid & 31;
+  // without cells, "cell" k is the k-th chunk of 32 home atoms and every atom is a candidate
+  const int ncell_rows = (nc > 0) ? nc * nc * nc : (n + 31) / 32;
+  const int maxo = e.max_out;
   int overflow = 0;
-  for (int i = c.tid; i < n; i += c.T) {
-    uint4 pi = v.pos[i];
-    int cnt = 0;
-    if (nc >= 3) {
-      int cx = (int)__umulhi(pi.x, (unsigned)nc), cy = (int)__umulhi(pi.y, (unsigned)nc),
-          cz = (int)__umulhi(pi.z, (unsigned)nc);
-      for (int dx = -1; dx <= 1; ++dx) {
-        int ex = cx + dx; ex += (ex < 0) ? nc : 0; ex -= (ex >= nc) ? nc : 0;
-        for (int dy = -1; dy <= 1; ++dy) {
-          int ey = cy + dy; ey += (ey < 0) ? nc : 0; ey -= (ey >= nc) ? nc : 0;
-          for (int dz = -1; dz <= 1; ++dz) {
-            int ez = cz + dz; ez += (ez < 0) ? nc : 0; ez -= (ez >= nc) ? nc : 0;
-            int cc = (ex * nc + ey) * nc + ez;
-            int s0 = v.cstart[cc], s1 = v.cstart[cc + 1];
-            for (int q = s0; q < s1; ++q) {
-              int j = v.sorted[q];
-              if (j == i || excluded_pair(i, j, R.nw3)) continue;
-              if (fixed_d2(pi, v.pos[j]) <= R.T_list) {
-                if (cnt < maxn) e.nbr[nbr_index(e, R, i, cnt, tpa)] = (uint16_t)j;
-                ++cnt;
+  // Work items are (cell, home pass of up to 32 atoms), handed out through a shared
+  // counter so clustered (dense) cells do not leave one warp with all the work.  Without
+  // cells, item k is the k-th chunk of 32 home atoms, assigned round-robin.
+  for (int it = 0;; ++it) {
+    int item;
+    if (nc > 0) {
+      if (lane == 0) item = atomicAdd(&v.s->next_item, 1);
+      item = __shfl_sync(0xffffffffu, item, 0);
+      if (item >= v.s->n_items) break;
+    } else {
+      item = warp + it * nwarps;
+      if (item >= ncell_rows) break;
+    }
+    int cell = 0, pass = item;
+    if (nc > 0) {  // last cell whose first item is <= item (binary search on the prefix)
+      int lo = 0, hi = ncell_rows - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (v.cfill[mid] <= item) lo = mid; else hi = mid - 1;
+      }
+      cell = lo;
+      pass = item - v.cfill[lo];
+    }
+    const int h0 = (nc > 0) ? v.cstart[cell] + 32 * pass : 32 * item;
+    const int h1 = (nc > 0) ? min(h0 + 32, v.cstart[cell + 1]) : min(32 * item + 32, n);
+    if (nc == 0) cell = 0;
+    const int cx = (nc > 0) ? cell / (nc * nc) : 0;
+    const int cy = (nc > 0) ? (cell / nc) % nc : 0;
+    const int cz = (nc > 0) ? cell % nc : 0;
+    for (int hb = h0; hb < h1; hb += 32) {
+      const int hq = hb + lane;
+      const int ih = (hq < h1) ? ((nc > 0) ? (int)v.sorted[hq] : hq) : (int)kNoAtom;
+      const bool act = ih != (int)kNoAtom;
+      const int i = act ? ih : 0;
+      const uint4 pi = v.pos[i];
+      const unsigned pi8 = pack8(pi);
+      int cnt = 0;
+      RowBuf rb;
+      rb.init();
+      const int nst = (nc > 0) ? 27 : 1;
+      for (int d = 0; d < nst; ++d) {
+        int s0 = 0, s1 = n;
+        if (nc > 0) {
+          int ex = cx + d / 9 - 1, ey = cy + (d / 3) % 3 - 1, ez = cz + d % 3 - 1;
+          ex += (ex < 0) ? nc : 0; ex -= (ex >= nc) ? nc : 0;
+          ey += (ey < 0) ? nc : 0; ey -= (ey >= nc) ? nc : 0;
+          ez += (ez < 0) ? nc : 0; ez -= (ez >= nc) ? nc : 0;
+          const int cc = (ex * nc + ey) * nc + ez;
+          s0 = v.cstart[cc];
+          s1 = v.cstart[cc + 1];
+        }
+        // Four candidates per iteration.  With cells: one 8-byte index load and one 16-byte
+        // load of their packed 8-bit coordinates; the per-byte wrapping difference is the
+        // minimum image at 8-bit resolution and __dp4a squares it (a conservative test:
+        // the Verlet filter applies the exact criterion).  Without cells: 16-bit test.
+        for (int q = s0; q < s1; q += 4) {
+          int jj[4];
+          bool near[4];
+          if (nc > 0) {
+            const uint2 w4 = *reinterpret_cast<const uint2*>(v.sorted + q);
+            const uint4 c8 = *reinterpret_cast<const uint4*>(v.sorted8 + q);
+            jj[0] = (int)(w4.x & 0xFFFFu); jj[1] = (int)(w4.x >> 16);
+            jj[2] = (int)(w4.y & 0xFFFFu); jj[3] = (int)(w4.y >> 16);
+            const unsigned cu[4] = {c8.x, c8.y, c8.z, c8.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int d = (int)__vsub4(pi8, cu[u]);
+              near[u] = __dp4a(d, d, 0) <= (int)R.T8_out;
+            }
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              jj[u] = (q + u < s1) ? q + u : (int)kNoAtom;
+              near[u] = d2_16(pi, v.pos[jj[u] == kNoAtom ? i : jj[u]]) <= R.T16_out;
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = jj[u];
+            const bool ok = act && near[u] && (j != (int)kNoAtom) && (j != i) && !excluded_pair(i, j, R.nw3);
+            if (ok) {
+              rb.put(j);
+              ++cnt;
+              if (rb.n == 4) {
+                if (cnt <= maxo)
+                  reinterpret_cast<uint2*>(e.nbr_out)[out_packet_index(e, R, i, (cnt - 1) >> 2)] = rb.packet();
+                rb.init();
               }
             }
           }
         }
       }
-    } else {
-      for (int j = 0; j < n; ++j) {
-        if (j == i || excluded_pair(i, j, R.nw3)) continue;
-        if (fixed_d2(pi, v.pos[j]) <= R.T_list) {
-          if (cnt < maxn) e.nbr[nbr_index(e, R, i, cnt, tpa)] = (uint16_t)j;
-          ++cnt;
-        }
+      if (act) {
+        if (rb.n > 0 && cnt <= maxo)  // last partial packet, padded with kNoAtom
+          reinterpret_cast<uint2*>(e.nbr_out)[out_packet_index(e, R, i, (cnt - 1) >> 2)] = rb.packet();
+        if (cnt > maxo) { overflow = 1; cnt = maxo & ~3; }
+        e.ncnt_out[R.atom_off + i] = cnt;
+        e.ref_out[R.atom_off + i] = pi;
       }
     }
-    if (cnt > maxn) { overflow = 1; cnt = maxn; }
-    e.ncnt[R.atom_off + i] = cnt;
-    e.ref[R.atom_off + i] = pi;
   }
   if (overflow) atomicOr(&v.s->flag_overflow, 1);
   c.sync();
   if (c.tid == 0) {
-    R.builds++;
+    c.R->builds++;
     v.s->flag_rebuild = 0;
-    if (v.s->flag_overflow) R.err |= 1;
   }
+  c.sync();
+}
+
+// Verlet rows filtered from the outer rows: one thread per atom streams its outer row
+// (one 8-byte packet load per four candidates) and keeps the candidates inside r_list, in
+// outer-row order, so the Verlet rows are as deterministic as the outer ones.
+__device__ void filter_list_impl(const Ctx& c) {
+  const Eng& e = *c.e;
+  const RepC& R = c.r;
+  const GView& v = c.v;
+  const int n = v.s->n_tot;
+  const int ltpa = c.ltpa;
+  const int maxn = e.max_nbr;
+  const uint2* pko = out_packets(e, R);
+  const size_t ostride = (size_t)R.cap_atoms;
+  int overflow = 0;
+  for (int i = c.tid; i < n; i += c.T) {
+    const uint4 pi = v.pos[i];
+    const int cnt_out = e.ncnt_out[R.atom_off + i];
+    const int npk = (cnt_out + 3) >> 2;
+    int cnt = 0;
+    RowBuf rb;
+    rb.init();
+    uint2* nbr2 = reinterpret_cast<uint2*>(e.nbr);
+    uint2 q = (npk > 0) ? pko[i] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+    for (int p = 0; p < npk; ++p) {
+      const uint2 qn = (p + 1 < npk) ? pko[(size_t)(p + 1) * ostride + i] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+      const int jj[4] = {(int)(q.x & 0xFFFFu), (int)(q.x >> 16), (int)(q.y & 0xFFFFu), (int)(q.y >> 16)};
+      uint4 pj[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pj[u] = v.pos[jj[u] == kNoAtom ? i : jj[u]];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (jj[u] != kNoAtom && fixed_d2(pi, pj[u]) <= R.T_list) {
+          rb.put(jj[u]);
+          ++cnt;
+          if (rb.n == 4) {
+            if (cnt <= maxn) nbr2[packet_index(e, R, i, (cnt - 1) >> 2, ltpa)] = rb.packet();
+            rb.init();
+          }
+        }
+      }
+      q = qn;
+    }
+    if (rb.n > 0 && cnt <= maxn) nbr2[packet_index(e, R, i, (cnt - 1) >> 2, ltpa)] = rb.packet();
+    if (cnt > maxn) { overflow = 1; cnt = maxn & ~3; }
+    e.ncnt[R.atom_off + i] = cnt;
+    e.ref[R.atom_off + i] = pi;
+  }
+  if (overflow) atomicOr(&v.s->flag_overflow, 1);
   c.sync();
 }
 
@@ -384,58 +628,96 @@ __device__ void build_list(const Ctx& c) {
 // mode bits: 1 = apply the second half kick, 2 = accumulate kinetic partials,
 //            4 = flyer rows compute protocol work with previous altitude w_prev
 // ------------------------------------------------------------------------------------
-template <int SYS>
+template <int SYS, bool NEMD>
+__device__ void force_pass_impl(const Ctx& c, int mode, float w_prev, double* kin_out);
+// mode bits: 1 = apply the second half kick, 2 = return the kinetic energy after it,
+//            4 = flyer rows accumulate the protocol work between w_prev and the current w.
+// NEMD = false assumes every altitude is zero (equilibrium MD).
+template <int SYS, bool NEMD = true>
 __device__ void force_pass(const Ctx& c, int mode, float w_prev, double* kin_out) {
+  const u64 t0 = (c.tid == 0) ? gtimer() : 0;
+  force_pass_impl<SYS, NEMD>(c, mode, w_prev, kin_out);
+  if (c.tid == 0) c.R->t_force_ns += (double)(gtimer() - t0);
+}
+
+template <int SYS, bool NEMD>
+__device__ void force_pass_impl(const Ctx& c, int mode, float w_prev, double* kin_out) {
   const Eng& e = *c.e;
-  const Rep& R = *c.R;
+  const RepC& R = c.r;
   const Pot& P = e.pot;
   const GView& v = c.v;
   const int n = v.s->n_tot;
-  const int tpa = c.tpa;
-  const int nsub = c.T / tpa;
-  const int sub = c.tid / tpa, lin = c.tid % tpa;
-  const int fly0 = v.s->fly0, fly1 = v.s->fly1;
-  const float gscr = v.s->g_scr;
+  const int tpa = c.tpa, ltpa = c.ltpa;
+  const int nsub = c.T >> ltpa;
+  const int sub = c.tid >> ltpa, lin = c.tid & (tpa - 1);
+  const int fly0 = NEMD ? v.s->fly0 : -1, fly1 = NEMD ? v.s->fly1 : -1;
+  const float gscr = NEMD ? v.s->g_scr : 1.0f;
   const float scale = R.scale;
   const float half_dt = 0.5f * (float)e.proto.dt;
+  const uint2* packets = nbr_packets(e, R);
+  const size_t pstride = (size_t)R.cap_atoms << ltpa;
   float kin = 0.0f;
   for (int a0 = 0; a0 < n; a0 += nsub) {
     const int i = a0 + sub;
     const bool active = i < n;
     float fx = 0.f, fy = 0.f, fz = 0.f, dwk = 0.f;
-    const bool iflyer = active && (i == fly0 || i == fly1);
+    const bool iflyer = NEMD && active && (i == fly0 || i == fly1);
     if (active) {
       const uint4 pi = v.pos[i];
-      const int ti = type_of(i, R.nw3);
-      const float wi = wbits(pi);
+      const int ti = type_t<SYS>(i, R.nw3);
+      const float wi = NEMD ? wbits(pi) : 0.0f;
       const bool wnz_i = wi != 0.0f;
       const int cnt = e.ncnt[R.atom_off + i];
-      const bool do_work = (mode & 4) && iflyer;
-      for (int s = lin; s < cnt; s += tpa) {
-        const int j = e.nbr[nbr_index(e, R, i, s, tpa)];
-        const uint4 pj = v.pos[j];
-        const float dx = (float)(int)(pj.x - pi.x) * scale;
-        const float dy = (float)(int)(pj.y - pi.y) * scale;
-        const float dz = (float)(int)(pj.z - pi.z) * scale;
-        const float wj = wbits(pj);
-        const float dw = wi - wj;
-        const float r3 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float r2 = fmaf(dw, dw, r3);
-        if (r2 < P.rc2_max) {
-          const int tj = type_of(j, R.nw3);
-          const float g = (wnz_i != (wj != 0.0f)) ? gscr : 1.0f;
-          const PairCoef<SYS> cf = coef<SYS>(P, ti, tj);
+      const uint2* pk = packets + ((size_t)i << ltpa) + lin;
+      const int nP = (cnt + 3) >> 2;  // packets of the row; this lane owns lin, lin+tpa, ...
+      const int npk = (nP > lin) ? (nP - lin + tpa - 1) >> ltpa : 0;
+      uint2 q = (npk > 0) ? pk[0] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+      for (int p = 0; p < npk; ++p) {
+        const uint2 qn = (p + 1 < npk) ? pk[(size_t)(p + 1) * pstride] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+        const int jj[4] = {(int)(q.x & 0xFFFFu), (int)(q.x >> 16), (int)(q.y & 0xFFFFu), (int)(q.y >> 16)};
+        // branch-free over the four slots: a padding slot reads atom i and gets r^2 = 1e30,
+        // for which every term of the pair function is exactly zero
+        uint4 pj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) pj[u] = v.pos[jj[u] == kNoAtom ? i : jj[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool valid = jj[u] != kNoAtom;
+          const float dx = (float)(int)(pj[u].x - pi.x) * scale;
+          const float dy = (float)(int)(pj[u].y - pi.y) * scale;
+          const float dz = (float)(int)(pj[u].z - pi.z) * scale;
+          float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          float g = 1.0f;
+          if (NEMD) {
+            const float wj = wbits(pj[u]);
+            const float dw = wi - wj;
+            r2 = fmaf(dw, dw, r2);
+            g = (wnz_i != (wj != 0.0f)) ? gscr : 1.0f;
+          }
+          r2 = valid ? r2 : 1.0e30f;
+          const PairCoef<SYS> cf = coef<SYS>(P, ti, type_t<SYS>(jj[u] & 0x7FFF, R.nw3));
           const float fr = pair_fr<SYS>(P, cf, r2, g);
           fx = fmaf(-fr, dx, fx);
           fy = fmaf(-fr, dy, fy);
           fz = fmaf(-fr, dz, fz);
         }
-        if (do_work && j != fly0 && j != fly1) {
-          const int tj = type_of(j, R.nw3);
-          const PairCoef<SYS> cf = coef<SYS>(P, ti, tj);
+        q = qn;
+      }
+      if (NEMD && (mode & 4) && iflyer) {
+        // protocol work of a flying row: U(w_now) - U(w_prev) against every non-flyer
+        const float go = __expf(-P.kappa_sr * w_prev);
+        for (int s2 = lin; s2 < cnt; s2 += tpa) {
+          const int j = e.nbr[nbr_index(e, R, i, s2, ltpa)];
+          if (j == fly0 || j == fly1) continue;
+          const uint4 pj = v.pos[j];
+          const float dx = (float)(int)(pj.x - pi.x) * scale;
+          const float dy = (float)(int)(pj.y - pi.y) * scale;
+          const float dz = (float)(int)(pj.z - pi.z) * scale;
+          const float r3 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const float r2n = fmaf(wi, wi, r3);
           const float r2o = fmaf(w_prev, w_prev, r3);
-          const float go = __expf(-P.kappa_sr * w_prev);
-          const float un = (r2 < P.rc2_max) ? pair_u32<SYS>(P, cf, r2, gscr) : 0.0f;
+          const PairCoef<SYS> cf = coef<SYS>(P, ti, type_t<SYS>(j, R.nw3));
+          const float un = (r2n < P.rc2_max) ? pair_u32<SYS>(P, cf, r2n, gscr) : 0.0f;
           const float uo = (r2o < P.rc2_max) ? pair_u32<SYS>(P, cf, r2o, go) : 0.0f;
           dwk += un - uo;
         }
@@ -445,15 +727,15 @@ __device__ void force_pass(const Ctx& c, int mode, float w_prev, double* kin_out
       fx += __shfl_xor_sync(0xffffffffu, fx, o, tpa);
       fy += __shfl_xor_sync(0xffffffffu, fy, o, tpa);
       fz += __shfl_xor_sync(0xffffffffu, fz, o, tpa);
-      dwk += __shfl_xor_sync(0xffffffffu, dwk, o, tpa);
+      if (NEMD) dwk += __shfl_xor_sync(0xffffffffu, dwk, o, tpa);
     }
     if (active && lin == 0) {
       const int ga = R.atom_off + i;
       e.force[ga] = make_float4(fx, fy, fz, 0.f);
-      if ((mode & 4) && iflyer) v.s->dW[i == fly0 ? 0 : 1] = (double)dwk;
+      if (NEMD && (mode & 4) && iflyer) v.s->dW[i == fly0 ? 0 : 1] = (double)dwk;
       if (!iflyer && (mode & 3)) {
         float4 h = e.vhi[ga], l = e.vlo[ga];
-        const int ti = type_of(i, R.nw3);
+        const int ti = type_t<SYS>(i, R.nw3);
         if (mode & 1) {
           const float cm = half_dt * P.inv_m[ti];
           ff_add(h.x, l.x, fx * cm);
@@ -464,7 +746,7 @@ __device__ void force_pass(const Ctx& c, int mode, float w_prev, double* kin_out
         }
         if (mode & 2) {
           const float vx = h.x + l.x, vy = h.y + l.y, vz = h.z + l.z;
-          kin += (float)P.dm[ti] * fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+          kin += P.m_f[ti] * fmaf(vx, vx, fmaf(vy, vy, vz * vz));
         }
       }
     }
@@ -477,13 +759,15 @@ __device__ void force_pass(const Ctx& c, int mode, float w_prev, double* kin_out
 // ------------------------------------------------------------------------------------
 __device__ void kick_drift(const Ctx& c, float alpha) {
   const Eng& e = *c.e;
-  const Rep& R = *c.R;
+  const RepC& R = c.r;
   const Pot& P = e.pot;
   const GView& v = c.v;
   const int n = v.s->n_tot;
   const int fly0 = v.s->fly0, fly1 = v.s->fly1;
   const float half_dt = 0.5f * (float)e.proto.dt;
-  int moved = 0, bad = 0;
+  int bad = 0;
+  float d1 = 0.f, d2 = 0.f;  // this thread's two largest displacements (Verlet list)
+  float o1 = 0.f, o2 = 0.f;  // the same against the outer-list reference
   for (int a = c.tid; a < n; a += c.T) {
     if (a == fly0 || a == fly1) continue;  // flyers keep their 3D state (Sec. II.B.1)
     const int ga = R.atom_off + a;
@@ -510,15 +794,59 @@ __device__ void kick_drift(const Ctx& c, float alpha) {
     p.y += (unsigned)__float2int_rn(sy);
     p.z += (unsigned)__float2int_rn(sz);
     v.pos[a] = p;
-    if (fixed_d2(p, e.ref[ga]) > R.T_move) moved = 1;
+    const float dd = sqrtf((float)fixed_d2(p, e.ref[ga]));
+    if (dd > d1) { d2 = d1; d1 = dd; } else if (dd > d2) { d2 = dd; }
+    const float de = sqrtf((float)fixed_d2(p, e.ref_out[ga]));
+    if (de > o1) { o2 = o1; o1 = de; } else if (de > o2) { o2 = de; }
   }
-  if (moved) v.s->flag_rebuild = 1;
+  // A list stays valid while the two largest displacements since its build sum to less
+  // than its skin (no pair distance can have shrunk by more).  Warp-level top-2 merges;
+  // every thread folds the warp slots after the next barrier (maybe_rebuild).
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float b1 = __shfl_xor_sync(0xffffffffu, d1, o), b2 = __shfl_xor_sync(0xffffffffu, d2, o);
+    const float hi = fmaxf(d1, b1);
+    d2 = fmaxf(fminf(d1, b1), fmaxf(d2, b2));
+    d1 = hi;
+    const float c1 = __shfl_xor_sync(0xffffffffu, o1, o), c2 = __shfl_xor_sync(0xffffffffu, o2, o);
+    const float hj = fmaxf(o1, c1);
+    o2 = fmaxf(fminf(o1, c1), fmaxf(o2, c2));
+    o1 = hj;
+  }
+  if ((c.tid & 31) == 0) {
+    v.s->d1w[c.tid >> 5] = d1;
+    v.s->d2w[c.tid >> 5] = d2;
+    v.s->o1w[c.tid >> 5] = o1;
+    v.s->o2w[c.tid >> 5] = o2;
+  }
   if (bad) v.s->flag_nan = 1;
+}
+
+// after the barrier that follows kick_drift: fold the warp slots (same answer in every
+// thread) and rebuild what is stale -- everything when the outer list is, else only the
+// Verlet rows
+__device__ __forceinline__ void fold_top2(const float* a1, const float* a2, int nw, float& d1, float& d2) {
+  d1 = 0.f;
+  d2 = 0.f;
+  for (int w = 0; w < nw; ++w) {
+    const float hi = fmaxf(d1, a1[w]);
+    d2 = fmaxf(fminf(d1, a1[w]), fmaxf(d2, a2[w]));
+    d1 = hi;
+  }
+}
+__device__ void build_list(const Ctx& c);
+__device__ void refresh_list(const Ctx& c);
+__device__ void maybe_rebuild(const Ctx& c) {
+  float d1, d2, o1, o2;
+  fold_top2(c.v.s->d1w, c.v.s->d2w, c.T >> 5, d1, d2);
+  fold_top2(c.v.s->o1w, c.v.s->o2w, c.T >> 5, o1, o2);
+  if (o1 + o2 > c.r.skin_out_fx) build_list(c);
+  else if (d1 + d2 > c.r.skin_fx) refresh_list(c);
 }
 
 __device__ void scale_velocities(const Ctx& c, float alpha) {
   const Eng& e = *c.e;
-  const Rep& R = *c.R;
+  const RepC& R = c.r;
   const int n = c.v.s->n_tot;
   for (int a = c.tid; a < n; a += c.T) {
     const int ga = R.atom_off + a;
@@ -533,7 +861,7 @@ __device__ void scale_velocities(const Ctx& c, float alpha) {
 
 __device__ void negate_velocities(const Ctx& c, int n) {
   const Eng& e = *c.e;
-  const Rep& R = *c.R;
+  const RepC& R = c.r;
   for (int a = c.tid; a < n; a += c.T) {
     const int ga = R.atom_off + a;
     float4 h = e.vhi[ga], l = e.vlo[ga];
@@ -548,9 +876,16 @@ __device__ void negate_velocities(const Ctx& c, int n) {
 // FP64 end-point energies
 // ------------------------------------------------------------------------------------
 // U over atoms [0, n_tot) leaving out ex0/ex1 (-1 = none); each unordered pair once
+__device__ double energy64_impl(const Ctx& c, int ex0, int ex1);
 __device__ double energy64(const Ctx& c, int ex0, int ex1) {
+  const u64 t0 = (c.tid == 0) ? gtimer() : 0;
+  const double u = energy64_impl(c, ex0, ex1);
+  if (c.tid == 0) c.R->t_energy_ns += (double)(gtimer() - t0);
+  return u;
+}
+__device__ double energy64_impl(const Ctx& c, int ex0, int ex1) {
   const Eng& e = *c.e;
-  const Rep& R = *c.R;
+  const RepC& R = c.r;
   const Pot& P = e.pot;
   const GView& v = c.v;
   const int n = v.s->n_tot;
@@ -565,7 +900,7 @@ __device__ double energy64(const Ctx& c, int ex0, int ex1) {
     const double wi = (double)wbits(pi);
     const int cnt = e.ncnt[R.atom_off + i];
     for (int s = 0; s < cnt; ++s) {
-      const int j = e.nbr[nbr_index(e, R, i, s, c.tpa)];
+      const int j = e.nbr[nbr_index(e, R, i, s, c.ltpa)];
       if (j <= i || j == ex0 || j == ex1) continue;
       const uint4 pj = v.pos[j];
       const double dx = (double)(int)(pj.x - pi.x) * scale;
@@ -587,7 +922,7 @@ __device__ double energy64(const Ctx& c, int ex0, int ex1) {
 
 __device__ double kinetic64(const Ctx& c) {
   const Eng& e = *c.e;
-  const Rep& R = *c.R;
+  const RepC& R = c.r;
   const int n = c.v.s->n_tot;
   const int fly0 = c.v.s->fly0, fly1 = c.v.s->fly1;
   double acc = 0.0;
@@ -666,7 +1001,7 @@ __device__ double altitude(const Proto& pr, int insertion, int k) {
 template <int SYS>
 __device__ void initial_forces(const Ctx& c) {
   build_list(c);
-  force_pass<SYS>(c, 0, 0.f, nullptr);
+  force_pass<SYS, false>(c, 0, 0.f, nullptr);
   c.sync();
 }
 
@@ -676,14 +1011,15 @@ __device__ void md_phase(const Ctx& c, int n_steps) {
   const Eng& e = *c.e;
   Rep& R = *c.R;
   GScal* S = c.v.s;
+  if (c.tid == 0) S->flag_nan = 0;
   initial_forces<SYS>(c);
   float alpha = 1.0f;
   for (int st = 0; st < n_steps; ++st) {
     kick_drift(c, alpha);
     c.sync();
-    if (S->flag_rebuild) build_list(c);
+    maybe_rebuild(c);
     double K = 0.0;
-    force_pass<SYS>(c, 1 | 2, 0.f, &K);  // ends with group syncs
+    force_pass<SYS, false>(c, 1 | 2, 0.f, &K);  // ends with group syncs
     if (c.tid == 0) {
       const int n = S->n_tot;
       double a = csvr_alpha(e, R, (u64)(c.R - e.rep), R.step_ctr, K, n);
@@ -698,6 +1034,7 @@ __device__ void md_phase(const Ctx& c, int n_steps) {
   if (alpha != 1.0f) scale_velocities(c, alpha);
   c.sync();
   if (c.tid == 0 && S->flag_nan) R.err |= 2;
+  if (c.tid == 0 && S->flag_overflow) R.err |= 1;
 }
 
 // one pair-exchange trial (Sec. II.A); readings as in the oracle:
@@ -807,6 +1144,8 @@ __device__ void trial_phase(const Ctx& c) {
     S->wprot = 0.0;
     S->wprot_c = 0.0;
     S->dW[0] = S->dW[1] = 0.0;
+    S->flag_nan = 0;       // a blow-up inside NEMD only rejects this trial
+    S->flag_overflow = 0;  // so does a neighbour row that overflowed during it
   }
   c.sync();
   build_list(c);
@@ -819,7 +1158,7 @@ __device__ void trial_phase(const Ctx& c) {
   for (int k = 0; k < e.proto.n_f; ++k) {
     kick_drift(c, 1.0f);
     c.sync();
-    if (S->flag_rebuild) build_list(c);
+    maybe_rebuild(c);
     const float w_prev = S->w_cur;
     const float w_next = (float)altitude(e.proto, ins, k + 1);
     if (c.tid == 0) {
@@ -856,7 +1195,9 @@ __device__ void trial_phase(const Ctx& c) {
       bdm = -e.proto.beta * dH - 2.0 * log(V / (double)N);       // Eq. 8
       xacc = bdm - e.proto.beta_mu;
     }
-    int status = isfinite(dH) ? 0 : 3;
+    int status = (isfinite(dH) && !S->flag_nan && !S->flag_overflow) ? 0 : 3;
+    S->flag_nan = 0;
+    S->flag_overflow = 0;
     int acc = (status == 0) && (S->ln_u < xacc) && !e.proto.no_accept;
     S->accept = acc;
     h4d_record rr;
@@ -921,11 +1262,6 @@ __device__ void trial_phase(const Ctx& c) {
 // ------------------------------------------------------------------------------------
 // Kernels
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ u64 gtimer() {
-  u64 t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
 
 // bind this thread to its group's replica; false for warps outside every group
 __device__ bool setup_ctx(const Eng& e, char* smem, Ctx& c) {
@@ -943,6 +1279,8 @@ __device__ bool setup_ctx(const Eng& e, char* smem, Ctx& c) {
   c.T = 32 * G.nwarps;
   c.bar = G.bar;
   c.tpa = R->tpa;
+  c.ltpa = __ffs(R->tpa) - 1;
+  c.r = repc_of(*R);
   c.v = carve(smem + G.smem_off, R->cap_atoms, R->nc, c.T);
   GScal* S = c.v.s;
   if (c.tid == 0) {
@@ -958,7 +1296,7 @@ __device__ bool setup_ctx(const Eng& e, char* smem, Ctx& c) {
 }
 
 template <int SYS>
-__global__ void __launch_bounds__(1024) cycles_kernel(Eng e, long long k_cycles, int n_eq, int do_trial) {
+__global__ void __launch_bounds__(H4D_MAXTHREADS, H4D_MINBLOCKS) cycles_kernel(const __grid_constant__ Eng e, long long k_cycles, int n_eq, int do_trial) {
   extern __shared__ __align__(16) char smem[];
   Ctx c;
   if (!setup_ctx(e, smem, c)) return;
@@ -977,14 +1315,11 @@ __global__ void __launch_bounds__(1024) cycles_kernel(Eng e, long long k_cycles,
   }
   c.sync();
   for (int a = c.tid; a < S->n_tot; a += c.T) e.pos[R->atom_off + a] = c.v.pos[a];
-  if (c.tid == 0) {
-    if (S->flag_overflow) R->err |= 1;
-    if (S->flag_nan) R->err |= 2;
-  }
+  if (c.tid == 0 && S->flag_overflow) R->err |= 1;
 }
 
 // current U (FP64) and K of each replica
-__global__ void __launch_bounds__(1024) energy_kernel(Eng e, double* U, double* K) {
+__global__ void __launch_bounds__(1024) energy_kernel(const __grid_constant__ Eng e, double* U, double* K) {
   extern __shared__ __align__(16) char smem[];
   Ctx c;
   if (!setup_ctx(e, smem, c)) return;
@@ -992,11 +1327,14 @@ __global__ void __launch_bounds__(1024) energy_kernel(Eng e, double* U, double* 
   const double u = energy64(c, -1, -1);
   const double k = kinetic64(c);
   const int r = (int)(c.R - e.rep);
-  if (c.tid == 0) { U[r] = u; K[r] = k; }
+  if (c.tid == 0) {
+    U[r] = u; K[r] = k;
+    if (c.v.s->flag_overflow) c.R->err |= 1;
+  }
 }
 
 // pairs within the larger cut-off (each unordered pair once), summed over replicas
-__global__ void __launch_bounds__(1024) count_kernel(Eng e, unsigned long long* out) {
+__global__ void __launch_bounds__(1024) count_kernel(const __grid_constant__ Eng e, unsigned long long* out) {
   extern __shared__ __align__(16) char smem[];
   Ctx c;
   if (!setup_ctx(e, smem, c)) return;
@@ -1009,7 +1347,7 @@ __global__ void __launch_bounds__(1024) count_kernel(Eng e, unsigned long long* 
     const uint4 pi = c.v.pos[i];
     const int m = e.ncnt[R->atom_off + i];
     for (int s = 0; s < m; ++s) {
-      const int j = e.nbr[nbr_index(e, *R, i, s, c.tpa)];
+      const int j = e.nbr[nbr_index(e, c.r, i, s, c.ltpa)];
       if (j <= i) continue;
       const uint4 pj = c.v.pos[j];
       const float dx = (float)(int)(pj.x - pi.x) * scale;
@@ -1019,12 +1357,13 @@ __global__ void __launch_bounds__(1024) count_kernel(Eng e, unsigned long long* 
     }
   }
   atomicAdd(out, cnt);
+  if (c.tid == 0 && S->flag_overflow) R->err |= 1;
 }
 
 // one configuration as given: list, FP32 forces (written to e.force), FP64 energy;
 // wbar is the mean altitude of the flying particles (Sec. II.B.2)
 template <int SYS>
-__global__ void __launch_bounds__(1024) eval_kernel(Eng e, float wbar, double* U) {
+__global__ void __launch_bounds__(1024) eval_kernel(const __grid_constant__ Eng e, float wbar, double* U) {
   extern __shared__ __align__(16) char smem[];
   const Group G = e.groups[0];
   Rep* R = &e.rep[0];
@@ -1034,6 +1373,8 @@ __global__ void __launch_bounds__(1024) eval_kernel(Eng e, float wbar, double* U
   c.T = blockDim.x;
   c.bar = 0;
   c.tpa = R->tpa;
+  c.ltpa = __ffs(R->tpa) - 1;
+  c.r = repc_of(*R);
   c.v = carve(smem + G.smem_off, R->cap_atoms, R->nc, c.T);
   GScal* S = c.v.s;
   if (c.tid == 0) {
@@ -1068,12 +1409,39 @@ int launch_eval(const Eng& e, int threads, size_t smem, float wbar, double* U, v
   return cudaGetLastError() == cudaSuccess ? H4D_OK : H4D_ECUDA;
 }
 
-// neighbour rows only (for the bit-exact neighbour-set check)
-__global__ void __launch_bounds__(1024) list_kernel(Eng e) {
+// n_iter equilibrium force passes on the current state (autotuning and profiling of the
+// pair term in isolation); leaves positions and velocities untouched
+template <int SYS>
+__global__ void __launch_bounds__(H4D_MAXTHREADS, H4D_MINBLOCKS) forces_kernel(const __grid_constant__ Eng e, int n_iter) {
   extern __shared__ __align__(16) char smem[];
   Ctx c;
   if (!setup_ctx(e, smem, c)) return;
   build_list(c);
+  for (int it = 0; it < n_iter; ++it) {
+    force_pass<SYS, false>(c, 0, 0.f, nullptr);
+    c.sync();
+  }
+}
+
+int launch_forces(const Eng& e, int n_ctas, int cta_threads, size_t smem, int n_iter, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (e.pot.sys == H4D_SYS_LJ) {
+    cudaFuncSetAttribute(forces_kernel<H4D_SYS_LJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    forces_kernel<H4D_SYS_LJ><<<n_ctas, cta_threads, smem, st>>>(e, n_iter);
+  } else {
+    cudaFuncSetAttribute(forces_kernel<H4D_SYS_AQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    forces_kernel<H4D_SYS_AQ><<<n_ctas, cta_threads, smem, st>>>(e, n_iter);
+  }
+  return cudaGetLastError() == cudaSuccess ? H4D_OK : H4D_ECUDA;
+}
+
+// neighbour rows only (for the bit-exact neighbour-set check)
+__global__ void __launch_bounds__(1024) list_kernel(const __grid_constant__ Eng e) {
+  extern __shared__ __align__(16) char smem[];
+  Ctx c;
+  if (!setup_ctx(e, smem, c)) return;
+  build_list(c);
+  if (c.tid == 0 && c.v.s->flag_overflow) c.R->err |= 1;
 }
 
 int launch_list(const Eng& e, int n_ctas, int cta_threads, size_t smem, void* stream) {

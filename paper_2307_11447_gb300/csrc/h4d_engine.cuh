@@ -25,6 +25,7 @@ struct Pot {
   float sig2[16], eps4[16], ljshift[16], kq[16];  // per (ti*4 + tj)
   float rc2_lj, rc2_c, rc2_max, alpha, shift_c, two_alpha_sqrtpi, kappa_sr;
   float inv_m[kMaxT];  // 1 / (m mvv2e)
+  float m_f[kMaxT];    // m mvv2e
   double dsig2[16], deps4[16], dljshift[16], dkq[16];
   double drc2_lj, drc2_c, dalpha, dshift_c, dkappa_sr;
   double dm[kMaxT];    // m mvv2e
@@ -47,9 +48,16 @@ struct Rep {
   int n_pairs, cap_pairs;
   int atom_off, cap_atoms;
   int nc;         // cells per dimension (0 = all pairs)
+  int reach;      // stencil half-width: cells are at least r_list / reach wide
   int tpa;
+  int pad_r;
   unsigned long long T_list;   // neighbour criterion threshold (fixed-point units^2)
   unsigned long long T_move;   // (skin/2)^2 in fixed-point units^2
+  float skin_fx;               // skin in fixed-point units
+  float skin_out_fx;           // outer-list skin in fixed-point units
+  unsigned long long T_out;    // outer-list threshold (fixed-point units^2)
+  unsigned T16_out;            // conservative outer threshold on 16-bit coordinates
+  unsigned T8_out;             // conservative outer threshold on 8-bit coordinates
   int rec_off, rec_cap;
   long long rec_count;
   unsigned long long trial_ctr, step_ctr;
@@ -57,6 +65,7 @@ struct Rep {
   long long cycles, trials_ins, trials_del, acc_ins, acc_del, rej_status, md_steps, builds, err;
   double sum_n, sum_n2;
   double t_nemd_ns, t_md_ns;
+  double t_build_ns, t_force_ns, t_energy_ns;  // phase timers (thread 0 of the group)
   int dirty;      // state changed on the host: rebuild list and forces
   int pad;
 };
@@ -79,22 +88,32 @@ struct Eng {
   float4* vhi_save;
   float4* vlo_save;
   uint4* ref;
-  uint16_t* nbr;
+  uint16_t* nbr;      // inner (Verlet) rows, tpa-interleaved packets
   int* ncnt;
+  uint16_t* nbr_out;  // outer rows (larger skin, one lane per atom), rebuilt from cells
+  int* ncnt_out;
+  uint4* ref_out;     // positions at the last outer build
   h4d_record* rec;
   int max_nbr;
+  int max_out;
   unsigned long long seed;
 };
 
 // shared-memory bytes a group needs for a replica
-inline size_t group_smem_bytes(int cap_atoms, int nc, int nthreads) {
-  size_t ncell = nc >= 3 ? (size_t)nc * nc * nc : 0;
-  size_t b = 16 * (size_t)cap_atoms;            // positions
-  b += 4 * (ncell + 1) + 4 * ncell;             // cell start + fill
-  b += 2 * (size_t)cap_atoms * 2;               // sorted atoms + cell of atom
-  b = (b + 15) & ~(size_t)15;
-  b += 8 * (size_t)nthreads;                    // reduction scratch
-  b += 640;                                     // per-group scalars
+__host__ __device__ inline size_t smem_align16(size_t b) { return (b + 15) & ~(size_t)15; }
+// Per-group shared memory: positions, cell starts, cell fill counters / work-item prefix,
+// cell-sorted atom list (each cell padded to a multiple of 4 entries), the same list as
+// packed 8-bit coordinates, scalars.  Every region starts on a 16-byte boundary.
+__host__ __device__ inline size_t group_smem_bytes(int cap_atoms, int nc, int nthreads) {
+  (void)nthreads;
+  size_t ncell = nc > 0 ? (size_t)nc * nc * nc : 0;
+  size_t slots = (size_t)cap_atoms + 3 * ncell;
+  size_t b = smem_align16(16 * (size_t)cap_atoms);
+  b += smem_align16(4 * (ncell + 1));
+  b += smem_align16(4 * (ncell + 1));
+  b += smem_align16(2 * slots);
+  b += smem_align16(4 * slots);
+  b += 1536;
   return (b + 127) & ~(size_t)127;
 }
 
@@ -104,6 +123,7 @@ int launch_cycles(const Eng& e, int n_ctas, int cta_threads, size_t smem, long l
 int launch_energy(const Eng& e, int n_ctas, int cta_threads, size_t smem, double* U, double* K,
                   void* stream);
 int launch_eval(const Eng& e, int threads, size_t smem, float wbar, double* U, void* stream);
+int launch_forces(const Eng& e, int n_ctas, int cta_threads, size_t smem, int n_iter, void* stream);
 int launch_list(const Eng& e, int n_ctas, int cta_threads, size_t smem, void* stream);
 int launch_count_pairs(const Eng& e, int n_ctas, int cta_threads, size_t smem,
                        unsigned long long* out, void* stream);

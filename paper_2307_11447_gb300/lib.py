@@ -56,6 +56,7 @@ class h4d_params(ctypes.Structure):
         ("d_oh", ctypes.c_double),
         ("d_hh", ctypes.c_double),
         ("skin", ctypes.c_double),
+        ("skin_outer", ctypes.c_double),
         ("max_nbr", ctypes.c_int32),
         ("threads_per_atom", ctypes.c_int32),
     ]
@@ -89,6 +90,10 @@ class h4d_counts(ctypes.Structure):
         ("error_flags", ctypes.c_int64),
         ("t_nemd_ns", ctypes.c_double),
         ("t_md_ns", ctypes.c_double),
+        ("t_build_ns", ctypes.c_double),
+        ("t_force_ns", ctypes.c_double),
+        ("t_energy_ns", ctypes.c_double),
+        ("threads_per_atom", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -147,6 +152,7 @@ def lib():
             "h4d_get_state": ([vp, i32, pd, pd, i64, ctypes.POINTER(i64)], i32),
             "h4d_set_state": ([vp, i32, i32, pd, pd], i32),
             "h4d_num_replicas": ([vp], i32),
+            "h4d_autotune": ([vp, i32, pd, pd], i32),
             "h4d_count_pairs": ([vp, ctypes.POINTER(i64)], i32),
             "h4d_save": ([vp, ctypes.c_char_p], i32),
             "h4d_load": ([vp, ctypes.c_char_p], i32),
@@ -203,6 +209,7 @@ def make_params(cfg: dict, **override) -> h4d_params:
     p.d_oh = c.get("d_oh", 0.0)
     p.d_hh = c.get("d_hh", 0.0)
     p.skin = c.get("skin", 0.3)
+    p.skin_outer = c.get("skin_outer", 0.0)
     p.max_nbr = c.get("max_nbr", 0)
     p.threads_per_atom = c.get("threads_per_atom", 0)
     return p
@@ -291,6 +298,13 @@ class Context:
         x = np.ascontiguousarray(x, np.float64)
         v = None if v is None else np.ascontiguousarray(v, np.float64)
         _ck(lib().h4d_set_state(self.h, r, n_pairs, _pd(x), _pd(v)), "h4d_set_state")
+
+    def h4d_autotune(self, n_iter=20):
+        """Returns {tpa: (mean ns per force pass, mean ns per build)} per candidate."""
+        fp = np.zeros(5)
+        bp = np.zeros(5)
+        _ck(lib().h4d_autotune(self.h, n_iter, _pd(fp), _pd(bp)), "h4d_autotune")
+        return {t: (float(fp[k]), float(bp[k])) for k, t in enumerate((1, 2, 4, 8, 16))}
 
     def h4d_count_pairs(self) -> int:
         n = ctypes.c_int64()

@@ -51,4 +51,4 @@ def test_structure_sizes_match_header_layout():
     import ctypes
     # h4d_record: 8 int32 + 5 double
     assert h4d.RECORD_DTYPE.itemsize == 72
-    assert ctypes.sizeof(h4d.h4d_counts) == 8 * 14
+    assert ctypes.sizeof(h4d.h4d_counts) == 8 * 18
