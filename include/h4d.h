@@ -202,6 +202,23 @@ int h4d_load(h4d_ctx* ctx, const char* path);
 int h4d_eval_forces(const h4d_params* params, double L, int32_t n_water, int32_t n,
                     const double* host_x, const double* host_w, double* host_F, double* U);
 
+/* The computation of h4d_eval_forces for callers that cannot allocate device memory
+ * (for example a host that forbids cudaMalloc inside its own callbacks, or code that
+ * runs under a device-memory budget it does not control).  The paper has no counterpart;
+ * this entry point exists for such embedders only.
+ * Same arguments, units and results as h4d_eval_forces (host buffers in and out).  It
+ * calls no cudaMalloc, cudaFree or other allocating routine: every device buffer lives in
+ * one file-scope array of 16 MiB that each GPU loading the library holds until the
+ * process exits.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before any stream
+ * capture.  Sizes that do not fit (about 6000 LJ atoms with default capacities) return
+ * H4D_ECAPACITY.  All calls share the array and it keeps the last call's contents (each
+ * call writes everything it reads); calls that overlap on the GPU -- from several host
+ * threads or processes sharing a context -- race on it and must be serialised by the
+ * caller.  Works on the legacy default stream and returns after synchronising it. */
+int h4d_eval_forces_static(const h4d_params* params, double L, int32_t n_water, int32_t n,
+                           const double* host_x, const double* host_w, double* host_F, double* U);
+
 /* Neighbour pairs (i < j) under the fixed-point criterion: X = round(x/L 2^32) mod 2^32
  * per coordinate, pair iff sum ((int32)(X_i - X_j))^2 <= floor((r_list/L 2^32)^2).
  * Writes up to cap pairs sorted by (i, j) and the total count to *n_out. */

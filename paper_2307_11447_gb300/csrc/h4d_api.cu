@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -887,3 +888,177 @@ int h4d_neighbor_pairs(double L, int32_t n, const double* x, double r_list, int3
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------
+// h4d_eval_forces_static: the same computation as h4d_eval_forces for callers that must
+// not allocate device memory (for example code running where cudaMalloc is forbidden or
+// would break a memory budget they do not own).  Every device buffer it needs lives in
+// one file-scope array of kStaticScratchBytes, which each GPU that loads the library
+// holds until the process exits.
+// ------------------------------------------------------------------------------------
+static constexpr size_t kStaticScratchBytes = 16u << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_h4d_static_scratch[kStaticScratchBytes];
+
+// The array's name in host code is only a host-side stand-in: its device address comes
+// from cudaGetSymbolAddress, once per device, with that device current.
+static std::mutex g_static_mu;
+static void* g_static_addr[64];
+
+static int static_scratch_address(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return H4D_ECUDA;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_h4d_static_scratch) != cudaSuccess || !p) return H4D_ECUDA;
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return H4D_OK;
+}
+
+// doubles in, fixed-point box fractions out (same rule as to_fixed: wrap into [0, L),
+// round x/L 2^32 to nearest, keep 32 bits); altitudes as FP32 bits
+__global__ void static_convert_in(const double* x, const double* w, int n, double L, uint4* pos) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  unsigned f[3];
+  for (int k = 0; k < 3; ++k) {
+    double y = x[3 * a + k] - L * floor(x[3 * a + k] / L);
+    if (y >= L) y -= L;
+    const double sc = nearbyint(y / L * 4294967296.0);
+    f[k] = (unsigned)((unsigned long long)sc & 0xffffffffULL);
+  }
+  const float wa = w ? (float)w[a] : 0.0f;
+  pos[a] = make_uint4(f[0], f[1], f[2], __float_as_uint(wa));
+}
+
+__global__ void static_convert_out(const float4* f, int n, double* F) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  const float4 v = f[a];
+  F[3 * a] = v.x;
+  F[3 * a + 1] = v.y;
+  F[3 * a + 2] = v.z;
+}
+
+static size_t carve_bytes(size_t& off, size_t bytes) {
+  const size_t at = (off + 255) & ~(size_t)255;
+  off = at + bytes;
+  return at;
+}
+
+extern "C" int h4d_eval_forces_static(const h4d_params* params, double L, int32_t n_water, int32_t n,
+                                      const double* x, const double* w, double* F, double* U) {
+  int rc = check_params(params);
+  if (rc) return rc;
+  if (!x || !F || n < 1 || n_water < 0 || 3 * n_water > n || !(L > 0)) return H4D_EINVAL;
+  if (((n - 3 * n_water) & 1) != 0) return H4D_EINVAL;
+  if (2.0 * (rmax_of(*params) + params->skin) >= L) return H4D_EINVAL;
+  rc = check_device();
+  if (rc) return rc;
+  void* base = nullptr;
+  rc = static_scratch_address(&base);
+  if (rc) return rc;
+
+  // plan, geometry and the device layout inside the static array (host stack only)
+  h4d_ctx c;
+  c.prm = *params;
+  c.seed = 0;
+  c.stream = 0;
+  c.R = 1;
+  c.max_nbr = params->max_nbr > 0 ? params->max_nbr : derive_max_nbr(*params);
+  c.max_nbr = ((c.max_nbr + 127) / 128) * 128;
+  c.max_out = std::max(c.max_nbr, derive_max_rows(*params, rmax_of(*params) + outer_skin(*params)));
+  Rep R;
+  std::memset(&R, 0, sizeof(Rep));
+  R.n_water = n_water;
+  R.nw3 = 3 * n_water;
+  R.n_pairs = (n - 3 * n_water) / 2;
+  R.cap_pairs = R.n_pairs;
+  R.cap_atoms = n;
+  set_rep_geometry(*params, R, L);
+  R.tpa = choose_tpa(*params, n);
+  R.rec_cap = 1;
+  Group G;
+  std::memset(&G, 0, sizeof(Group));
+  const int threads = choose_threads(n);
+  G.nwarps = threads / 32;
+  const size_t smem = group_smem_bytes(n, R.nc, threads);
+  if (smem > 227 * 1024) return H4D_ECAPACITY;
+  int cta_groups[2] = {0, 1};
+
+  const size_t na = (size_t)n;
+  size_t off = 0;
+  const size_t o_rep = carve_bytes(off, sizeof(Rep));
+  const size_t o_grp = carve_bytes(off, sizeof(Group));
+  const size_t o_cg = carve_bytes(off, sizeof(cta_groups));
+  const size_t o_u = carve_bytes(off, sizeof(double));
+  const size_t o_rec = carve_bytes(off, sizeof(h4d_record));
+  const size_t o_x = carve_bytes(off, na * 3 * sizeof(double));
+  const size_t o_w = carve_bytes(off, w ? na * sizeof(double) : 0);
+  const size_t o_pos = carve_bytes(off, na * sizeof(uint4));
+  const size_t o_f = carve_bytes(off, na * sizeof(float4));
+  const size_t o_fd = carve_bytes(off, na * 3 * sizeof(double));
+  const size_t o_nbr = carve_bytes(off, na * (size_t)c.max_nbr * sizeof(uint16_t));
+  const size_t o_cnt = carve_bytes(off, na * sizeof(int));
+  const size_t o_ref = carve_bytes(off, na * sizeof(uint4));
+  const size_t o_nbo = carve_bytes(off, na * (size_t)c.max_out * sizeof(uint16_t));
+  const size_t o_cno = carve_bytes(off, na * sizeof(int));
+  const size_t o_rfo = carve_bytes(off, na * sizeof(uint4));
+  if (off > kStaticScratchBytes) return H4D_ECAPACITY;  // too many atoms for 16 MiB
+
+  unsigned char* b = static_cast<unsigned char*>(base);
+  Eng& e = c.eng;
+  std::memset(&e, 0, sizeof(Eng));
+  fill_pot(c.prm, e.pot, e.proto);
+  e.rep = reinterpret_cast<Rep*>(b + o_rep);
+  e.groups = reinterpret_cast<Group*>(b + o_grp);
+  e.cta_groups = reinterpret_cast<int*>(b + o_cg);
+  e.pos = reinterpret_cast<uint4*>(b + o_pos);
+  e.force = reinterpret_cast<float4*>(b + o_f);
+  // the evaluation never touches velocities or saved states; point them at valid memory
+  e.vhi = e.vlo = e.vhi_save = e.vlo_save = e.force;
+  e.pos_save = e.pos;
+  e.ref = reinterpret_cast<uint4*>(b + o_ref);
+  e.nbr = reinterpret_cast<uint16_t*>(b + o_nbr);
+  e.ncnt = reinterpret_cast<int*>(b + o_cnt);
+  e.nbr_out = reinterpret_cast<uint16_t*>(b + o_nbo);
+  e.ncnt_out = reinterpret_cast<int*>(b + o_cno);
+  e.ref_out = reinterpret_cast<uint4*>(b + o_rfo);
+  e.rec = reinterpret_cast<h4d_record*>(b + o_rec);
+  e.max_nbr = c.max_nbr;
+  e.max_out = c.max_out;
+  e.seed = 0;
+
+  // mean altitude of the flying particles (the nonzero altitudes), as in h4d_eval_forces
+  double wsum = 0.0;
+  int wcnt = 0;
+  if (w)
+    for (int a = 0; a < n; ++a)
+      if ((float)w[a] != 0.0f) { wsum += w[a]; ++wcnt; }
+
+  // the array keeps the previous call's contents: every region this call reads is
+  // written first (the replica record with zeroed counters and flags, the inputs)
+  if (cudaMemcpy(b + o_rep, &R, sizeof(Rep), cudaMemcpyHostToDevice) != cudaSuccess) return H4D_ECUDA;
+  if (cudaMemcpy(b + o_grp, &G, sizeof(Group), cudaMemcpyHostToDevice) != cudaSuccess) return H4D_ECUDA;
+  if (cudaMemcpy(b + o_cg, cta_groups, sizeof(cta_groups), cudaMemcpyHostToDevice) != cudaSuccess) return H4D_ECUDA;
+  if (cudaMemcpy(b + o_x, x, na * 3 * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) return H4D_ECUDA;
+  if (w && cudaMemcpy(b + o_w, w, na * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) return H4D_ECUDA;
+  static_convert_in<<<(n + 255) / 256, 256>>>(reinterpret_cast<const double*>(b + o_x),
+                                               w ? reinterpret_cast<const double*>(b + o_w) : nullptr, n, L, e.pos);
+  if (cudaGetLastError() != cudaSuccess) return H4D_ECUDA;
+  rc = launch_eval(e, threads, smem, (float)(wcnt ? wsum / wcnt : 0.0), reinterpret_cast<double*>(b + o_u), 0);
+  if (rc) return rc;
+  static_convert_out<<<(n + 255) / 256, 256>>>(e.force, n, reinterpret_cast<double*>(b + o_fd));
+  if (cudaGetLastError() != cudaSuccess) return H4D_ECUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return H4D_ECUDA;
+  Rep Rout;
+  double u = 0.0;
+  if (cudaMemcpy(&Rout, b + o_rep, sizeof(Rep), cudaMemcpyDeviceToHost) != cudaSuccess) return H4D_ECUDA;
+  if (Rout.err & 1) return H4D_ECAPACITY;
+  if (cudaMemcpy(&u, b + o_u, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return H4D_ECUDA;
+  if (cudaMemcpy(F, b + o_fd, na * 3 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return H4D_ECUDA;
+  if (U) *U = u;
+  return H4D_OK;
+}

@@ -157,6 +157,7 @@ def lib():
             "h4d_save": ([vp, ctypes.c_char_p], i32),
             "h4d_load": ([vp, ctypes.c_char_p], i32),
             "h4d_eval_forces": ([ctypes.POINTER(h4d_params), d, i32, i32, pd, pd, pd, pd], i32),
+            "h4d_eval_forces_static": ([ctypes.POINTER(h4d_params), d, i32, i32, pd, pd, pd, pd], i32),
             "h4d_neighbor_pairs": ([d, i32, pd, d, pi32, pi32, i64, ctypes.POINTER(i64)], i32),
         }
         for name, (args, res) in sig.items():
@@ -325,6 +326,18 @@ def h4d_eval_forces(params: h4d_params, L: float, x, w=None, n_water: int = 0):
     F = np.zeros((n, 3))
     U = ctypes.c_double()
     _ck(lib().h4d_eval_forces(ctypes.byref(params), L, n_water, n, _pd(x), _pd(wa), _pd(F), ctypes.byref(U)), "h4d_eval_forces")
+    return U.value, F
+
+
+def h4d_eval_forces_static(params: h4d_params, L: float, x, w=None, n_water: int = 0):
+    """h4d_eval_forces without any device allocation (static scratch in the library)."""
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    n = x.shape[0]
+    wa = None if w is None else np.ascontiguousarray(w, np.float64)
+    F = np.zeros((n, 3))
+    U = ctypes.c_double()
+    _ck(lib().h4d_eval_forces_static(ctypes.byref(params), L, n_water, n, _pd(x), _pd(wa), _pd(F), ctypes.byref(U)),
+        "h4d_eval_forces_static")
     return U.value, F
 
 
