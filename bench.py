@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="h4d", choices=["h4d", "reference"])
     ap.add_argument("--chains", type=int, default=304)
+    ap.add_argument("--sequential", type=int, default=0,
+                    help="batched workload: also time this many replicas run one at a time (alone on the GPU)")
     ap.add_argument("--workload", default="lj4000")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--equil", type=int, default=1000)
@@ -60,6 +62,13 @@ def dist_env():
 def workload(name, chains, rank):
     from paper_2307_11447_gb300 import workloads as wl
 
+    if name == "batched256":
+        cfg, reps = wl.batched_system(256, seed=7 + rank)
+        if ARGS.n_eq is not None:
+            cfg["n_eq"] = ARGS.n_eq
+        if ARGS.n_f is not None:
+            cfg["n_f"] = ARGS.n_f
+        return cfg, reps
     cfg = dict(wl.CONFIGS[name])
     if ARGS.n_eq is not None:
         cfg["n_eq"] = ARGS.n_eq
@@ -220,6 +229,9 @@ def run_gpu(args):
     sm_mhz = clk.get("sm_max_mhz") or 2070.0
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
+    seq = None
+    if args.sequential and args.workload == "batched256":
+        seq = sequential_baseline(reps, cfg, args.sequential, n_eq)
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(ctx, reps, args, n_eq, n_f, stream, world, dist if world > 1 else None)
@@ -238,10 +250,7 @@ def run_gpu(args):
             "vs_baseline": None,
             "dtype": "f32 pair forces, f64 work/energies",
             "data": "synthetic (seeded uniform positions, equilibrated 1000 MD steps)",
-            "config": {"workload": f"LJ electrolyte 4000 ions rho=0.3 (L={cfg['L']:.3f}), N_f={n_f}, N_eq={n_eq}, "
-                                   f"{args.chains} chains/GPU", "chains_per_gpu": args.chains, "ions": cfg["n_ions"],
-                       "n_f": n_f, "n_eq": n_eq, "parallelism": f"replicas x{world}",
-                       "l2": "state > L2 (about 1.3 GB per GPU); no flush needed"},
+            "config": workload_config(args, cfg, reps, n_f, n_eq, world),
             "nemd_4d_atom_steps_per_s": tot[1] / (secs * nemd_frac) if nemd_frac > 0 else None,
             "accepted_exchanges_per_s": tot[2] / secs,
             "accepted": int(tot[2]),
@@ -260,12 +269,56 @@ def run_gpu(args):
                          "pairs_in_cutoff": pairs, "flops_per_pair": FLOPS_PER_PAIR},
             "e2e": e2e,
         }
+        if seq is not None:
+            out["sequential_one_replica_at_a_time"] = seq
+            out["batched_over_sequential"] = value / seq["value"]
         if rank == 0 and os.environ.get("H4D_BENCH_CPU", "1") == "1":
             out["cpu_baseline"] = cpu_baseline(args.workload, sample_steps=60)
         print(json.dumps(out), flush=True)
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def workload_config(args, cfg, reps, n_f, n_eq, world):
+    if args.workload == "batched256":
+        ns = [2 * r["n_pairs"] for r in reps]
+        return {"workload": f"batched: {len(reps)} LJ-electrolyte replicas, ions {min(ns)}-{max(ns)}, "
+                            f"rho 0.1-0.4, N_f={n_f}, N_eq={n_eq}", "replicas_per_gpu": len(reps),
+                "n_f": n_f, "n_eq": n_eq, "parallelism": f"replicas x{world}",
+                "l2": "state smaller than L2 after warm-up; every step re-reads it (persistent launch)"}
+    return {"workload": f"LJ electrolyte 4000 ions rho=0.3 (L={cfg['L']:.3f}), N_f={n_f}, N_eq={n_eq}, "
+                        f"{args.chains} chains/GPU", "chains_per_gpu": args.chains, "ions": cfg["n_ions"],
+            "n_f": n_f, "n_eq": n_eq, "parallelism": f"replicas x{world}",
+            "l2": "state > L2 (about 1.3 GB per GPU); no flush needed"}
+
+
+def sequential_baseline(reps, cfg, count, n_eq):
+    """The same cycle run replica by replica, each alone in its own context (the GPU idle
+    but for one replica), on `count` replicas spread over the size range; the rate is
+    their atom-steps over their summed time."""
+    import torch
+
+    from paper_2307_11447_gb300 import lib as h4d
+
+    idx = np.linspace(0, len(reps) - 1, count).astype(int)
+    t_sum, units = 0.0, 0.0
+    for k in idx:
+        ctx = h4d.Context(h4d.make_params(cfg), [reps[k]], seed=5)
+        ctx.h4d_run_md(200)
+        ctx.h4d_autotune(10)
+        ctx.h4d_run_trials(1, n_eq)
+        torch.cuda.synchronize()
+        c0 = ctx.h4d_get_counts(0)
+        t0 = time.perf_counter()
+        ctx.h4d_run_trials(1, n_eq)
+        torch.cuda.synchronize()
+        t_sum += time.perf_counter() - t0
+        c1 = ctx.h4d_get_counts(0)
+        units += 2.0 * c1["n_pairs"] * (n_eq + cfg["n_f"])
+        ctx.close()
+    return {"value": units / t_sum, "unit": "atom-steps/s", "replicas_timed": int(count),
+            "seconds_for_256_estimate": t_sum * len(reps) / count}
 
 
 def run_e2e(ctx, reps, args, n_eq, n_f, stream, world, dist):

@@ -8,8 +8,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "../../include/h4d.h"
@@ -21,6 +23,10 @@ struct h4d_ctx {
   h4d_params prm;
   uint64_t seed;
   cudaStream_t stream;
+  bool own_stream = false;
+  int sm_count = 152;
+  // captured launches of h4d_run_trials / h4d_run_md, keyed by (cycles, n_eq, do_trial)
+  std::map<std::tuple<long long, int, int>, cudaGraphExec_t> graphs;
   int R;
   int total_atoms;
   int max_nbr;
@@ -240,7 +246,7 @@ static int alloc_all(h4d_ctx* c) {
   CK(cudaMemset(c->d_rec, 0, nrec * sizeof(h4d_record)));
   CK(cudaMalloc(&c->d_rep, c->rep_h.size() * sizeof(Rep)));
   CK(cudaMalloc(&c->d_groups, c->groups_h.size() * sizeof(Group)));
-  CK(cudaMalloc(&c->d_cta_groups, c->cta_groups_h.size() * sizeof(int)));
+  CK(cudaMalloc(&c->d_cta_groups, (c->rep_h.size() + 1) * sizeof(int)));  // at most one CTA per replica
   CK(cudaMalloc(&c->d_scratch, 2 * c->rep_h.size() * sizeof(double)));
   CK(cudaMalloc(&c->d_count, sizeof(unsigned long long)));
   return H4D_OK;
@@ -361,31 +367,88 @@ static int check_device() {
   return H4D_OK;
 }
 
-// one group (a whole CTA) per replica; the CTA size follows the replica size
-static int make_plan(h4d_ctx* c) {
+// Launch plan.  Every replica is simulated by a group of whole warps; groups are packed
+// into CTAs of kCtaWarps warps (first-fit decreasing) with at most 15 groups (named
+// barriers 1..15) and kCtaSmem bytes of shared memory per CTA, so two CTAs share an SM.
+// A group's warp count follows the replica's weight (expected work, or the work the
+// autotuner measured), out of the warps the GPU holds at two CTAs per SM, so that
+// uneven replicas finish together.  A group spanning a whole CTA uses __syncthreads.
+static const int kCtaWarps = 16;
+static const size_t kCtaSmem = 113 * 1024;
+
+static double default_weight(const Rep& r) {
+  // pair count ~ atoms x density
+  const double n = (double)r.cap_atoms;
+  return n * n / (r.L * r.L * r.L) + 1.0;
+}
+
+static void invalidate_graphs(h4d_ctx* c) {
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+}
+
+static int make_plan(h4d_ctx* c, const std::vector<double>* weight = nullptr) {
+  invalidate_graphs(c);
+  const int R = c->R;
+  std::vector<double> w(R);
+  double W = 0.0;
+  for (int r = 0; r < R; ++r) {
+    w[r] = (weight && (*weight)[r] > 0) ? (*weight)[r] : default_weight(c->rep_h[r]);
+    W += w[r];
+  }
+  const double budget = (double)c->sm_count * 2.0 * kCtaWarps;
+  struct Item { int rep, nw; size_t smem; };
+  std::vector<Item> items(R);
+  for (int r = 0; r < R; ++r) {
+    int nw = (int)std::ceil(budget * w[r] / W);
+    nw = std::max(1, std::min(kCtaWarps, nw));
+    items[r] = {r, nw, group_smem_bytes(c->rep_h[r].cap_atoms, c->rep_h[r].nc, 32 * nw)};
+    if (items[r].smem > 227 * 1024) return H4D_ECAPACITY;
+  }
+  std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.nw > b.nw; });
+  struct Cta { int warps = 0; size_t smem = 0; std::vector<int> members; };
+  std::vector<Cta> ctas;
+  for (int k = 0; k < R; ++k) {
+    const Item& it = items[k];
+    int placed = -1;
+    for (size_t q = 0; q < ctas.size() && placed < 0; ++q) {
+      Cta& t = ctas[q];
+      if (t.warps + it.nw <= kCtaWarps && (int)t.members.size() < kMaxGroupsPerCta &&
+          t.smem + it.smem <= kCtaSmem)
+        placed = (int)q;
+    }
+    if (placed < 0) { ctas.emplace_back(); placed = (int)ctas.size() - 1; }
+    Cta& t = ctas[placed];
+    t.members.push_back(k);
+    t.warps += it.nw;
+    t.smem += it.smem;
+  }
   c->groups_h.clear();
   c->cta_groups_h.clear();
-  int threads = 32;
-  for (auto& r : c->rep_h) threads = std::max(threads, choose_threads(r.cap_atoms));
-  c->cta_threads = threads;
   size_t smem = 0;
-  for (int i = 0; i < c->R; ++i) {
-    Rep& r = c->rep_h[i];
-    Group g;
-    g.rep = i;
-    g.warp0 = 0;
-    g.nwarps = threads / 32;
-    g.bar = 0;
-    g.smem_off = 0;
-    g.pad = 0;
+  for (auto& t : ctas) {
     c->cta_groups_h.push_back((int)c->groups_h.size());
-    c->groups_h.push_back(g);
-    smem = std::max(smem, group_smem_bytes(r.cap_atoms, r.nc, threads));
+    int warp0 = 0, bar = 1;
+    size_t off = 0;
+    const bool whole = t.members.size() == 1 && items[t.members[0]].nw == kCtaWarps;
+    for (int k : t.members) {
+      Group g;
+      g.rep = items[k].rep;
+      g.warp0 = warp0;
+      g.nwarps = items[k].nw;
+      g.bar = whole ? 0 : bar++;
+      g.smem_off = (int)off;
+      g.pad = 0;
+      c->groups_h.push_back(g);
+      warp0 += g.nwarps;
+      off += items[k].smem;
+    }
+    smem = std::max(smem, off);
   }
   c->cta_groups_h.push_back((int)c->groups_h.size());
-  c->n_ctas = c->R;
+  c->n_ctas = (int)ctas.size();
+  c->cta_threads = 32 * kCtaWarps;
   c->smem = smem;
-  if (smem > 227 * 1024) return H4D_ECAPACITY;
   return H4D_OK;
 }
 
@@ -417,6 +480,16 @@ int h4d_create(const h4d_params* params, const h4d_system* sys, uint64_t seed, v
   c->prm = *params;
   c->seed = seed;
   c->stream = (cudaStream_t)cuda_stream;
+  if (!c->stream) {  // graph capture needs a stream other than the legacy default stream
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return H4D_ECUDA; }
+    c->own_stream = true;
+  }
+  {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
+      c->sm_count = prop.multiProcessorCount;
+  }
   c->R = sys->n_replicas;
   c->max_nbr = params->max_nbr > 0 ? params->max_nbr : derive_max_nbr(*params);
   c->rep_h.resize(c->R);
@@ -474,6 +547,8 @@ void h4d_destroy(h4d_ctx* c) {
                   c->d_scratch, c->d_count, c->d_nbr_out, c->d_ncnt_out, c->d_ref_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  invalidate_graphs(c);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
 
@@ -481,6 +556,7 @@ int h4d_set_mu(h4d_ctx* c, double beta_mu) {
   if (!c || !std::isfinite(beta_mu)) return H4D_EINVAL;
   c->prm.beta_mu = beta_mu;
   c->eng.proto.beta_mu = beta_mu;
+  invalidate_graphs(c);
   return H4D_OK;
 }
 
@@ -495,14 +571,17 @@ int h4d_set_protocol(h4d_ctx* c, int32_t n_f, double w_max, double dt, double ka
   int rc = pull_reps(c);
   if (rc) return rc;
   for (auto& r : c->rep_h) r.c_drift = (float)(dt * kTwo32 / r.L);
+  const int no_acc = c->eng.proto.no_accept;
   fill_pot(c->prm, c->eng.pot, c->eng.proto);
-  c->eng.proto.no_accept = c->eng.proto.no_accept;
+  c->eng.proto.no_accept = no_acc;
+  invalidate_graphs(c);
   return push_plan(c);
 }
 
 int h4d_set_no_accept(h4d_ctx* c, int32_t on) {
   if (!c) return H4D_EINVAL;
   c->eng.proto.no_accept = on ? 1 : 0;
+  invalidate_graphs(c);
   return H4D_OK;
 }
 
@@ -516,16 +595,39 @@ static int check_errors(h4d_ctx* c) {
   return H4D_OK;
 }
 
+// persistent launch through a cached CUDA graph (captured on first use of a key)
+static int run_cached(h4d_ctx* c, long long k, int n_eq, int do_trial) {
+  const auto key = std::make_tuple(k, n_eq, do_trial);
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_cycles(c->eng, c->n_ctas, c->cta_threads, c->smem, k, n_eq, do_trial, c->stream);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (rc || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return rc ? rc : H4D_ECUDA;
+    }
+    cudaError_t e3 = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) return H4D_ECUDA;
+    it = c->graphs.emplace(key, ge).first;
+  }
+  CK(cudaGraphLaunch(it->second, c->stream));
+  return H4D_OK;
+}
+
 int h4d_run_md(h4d_ctx* c, int64_t n_steps) {
   if (!c || n_steps < 0 || n_steps > (int64_t)1 << 30) return H4D_EINVAL;
   if (n_steps == 0) return H4D_OK;
-  return launch_cycles(c->eng, c->n_ctas, c->cta_threads, c->smem, 1, (int)n_steps, 0, c->stream);
+  return run_cached(c, 1, (int)n_steps, 0);
 }
 
 int h4d_run_trials(h4d_ctx* c, int64_t k_cycles, int32_t n_eq) {
   if (!c || k_cycles < 0 || n_eq < 0) return H4D_EINVAL;
   if (k_cycles == 0) return H4D_OK;
-  return launch_cycles(c->eng, c->n_ctas, c->cta_threads, c->smem, k_cycles, n_eq, 1, c->stream);
+  return run_cached(c, k_cycles, n_eq, 1);
 }
 
 int32_t h4d_num_replicas(h4d_ctx* c) { return c ? c->R : 0; }
@@ -564,6 +666,14 @@ int h4d_autotune(h4d_ctx* c, int32_t n_iter, double* pass_ns, double* build_ns) 
     c->rep_h[r] = saved[r];
     c->rep_h[r].tpa = best[r];
   }
+  // re-plan: a replica's weight is the work it measured (time x warps it had), so the
+  // new warp counts equalise the time per step across replicas
+  std::vector<double> weight(c->R);
+  std::vector<int> nw_of(c->R, 1);
+  for (const Group& g : c->groups_h) nw_of[g.rep] = g.nwarps;
+  for (int r = 0; r < c->R; ++r) weight[r] = best_t[r] * nw_of[r];
+  rc = make_plan(c, &weight);
+  if (rc) return rc;
   rc = push_plan(c);
   if (rc) return rc;
   CK(cudaStreamSynchronize(c->stream));

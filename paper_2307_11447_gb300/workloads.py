@@ -163,10 +163,28 @@ def lj_positions(n_pairs: int, L: float, seed: int, min_dist: float = 0.8) -> np
 
 
 def batched_replicas(n_rep: int = 256, seed: int = 7, n_min: int = 100, n_max: int = 1000,
-                     rho_min: float = 0.1, rho_max: float = 0.4):
-    """Ion counts uniform in [n_min, n_max] rounded to even and densities uniform in
-    [rho_min, rho_max], one (n_ions, rho, L) triple per replica."""
+                     rho_min: float = 0.1, rho_max: float = 0.4, min_box: float = 8.6):
+    """Ion counts uniform in [n_min, n_max] (even) and densities uniform in
+    [rho_min, rho_max], one (n_ions, rho, L) triple per replica.  Draws whose box is
+    smaller than min_box (twice the largest cut-off plus skin, so that every pair has a
+    single minimum image) are redrawn."""
     rng = np.random.default_rng(seed)
-    n = rng.integers(n_min // 2, n_max // 2 + 1, size=n_rep) * 2
-    rho = rng.uniform(rho_min, rho_max, size=n_rep)
-    return [(int(n[i]), float(rho[i]), box_for(int(n[i]), float(rho[i]))) for i in range(n_rep)]
+    out = []
+    while len(out) < n_rep:
+        n = int(rng.integers(n_min // 2, n_max // 2 + 1)) * 2
+        rho = float(rng.uniform(rho_min, rho_max))
+        L = box_for(n, rho)
+        if L >= min_box:
+            out.append((n, rho, L))
+    return out
+
+
+def batched_system(n_rep: int = 256, seed: int = 7):
+    """The batched workload: LJ-electrolyte physics of the 250-ion system, one replica per
+    (n, rho, L) draw, seeded positions per replica."""
+    cfg = lj_config(250, 0.2, 100, n_eq=1000, beta_mu=-6.0)
+    reps = []
+    for k, (n, rho, L) in enumerate(batched_replicas(n_rep, seed)):
+        cap = n // 2 + max(16, (3 * n) // 20)
+        reps.append(dict(L=L, n_pairs=n // 2, cap_pairs=cap, x=lj_positions(n // 2, L, 10000 + k), rho=rho))
+    return cfg, reps
