@@ -319,6 +319,35 @@ static void split_ff(double v, float& hi, float& lo) {
   lo = (float)(v - (double)hi);
 }
 
+// Remove the bond-parallel relative velocities of every rigid water (the velocity stage
+// of RATTLE), so that drawn Maxwell-Boltzmann velocities respect the constraints.
+static double min_image(double d, double L) { return d - L * std::nearbyint(d / L); }
+static void project_water_velocities(const h4d_params& p, int n_water, double L, const double* x, double* v) {
+  const int A[3] = {0, 0, 1}, B[3] = {1, 2, 2};
+  const double d2[3] = {p.d_oh * p.d_oh, p.d_oh * p.d_oh, p.d_hh * p.d_hh};
+  const double im[3] = {1.0 / p.mass[2], 1.0 / p.mass[3], 1.0 / p.mass[3]};
+  for (int m = 0; m < n_water; ++m) {
+    for (int it = 0; it < 500; ++it) {
+      double worst = 0.0;
+      for (int q = 0; q < 3; ++q) {
+        const int a = 3 * m + A[q], b = 3 * m + B[q];
+        double rab[3], dv = 0.0;
+        for (int k = 0; k < 3; ++k) {
+          rab[k] = min_image(x[3 * a + k] - x[3 * b + k], L);
+          dv += rab[k] * (v[3 * a + k] - v[3 * b + k]);
+        }
+        worst = std::max(worst, std::fabs(dv) / d2[q]);
+        const double kk = dv / (d2[q] * (im[A[q]] + im[B[q]]));
+        for (int k = 0; k < 3; ++k) {
+          v[3 * a + k] -= kk * im[A[q]] * rab[k];
+          v[3 * b + k] += kk * im[B[q]] * rab[k];
+        }
+      }
+      if (worst < 1e-15) break;
+    }
+  }
+}
+
 static int upload_replica(h4d_ctx* c, int r, int n_pairs, const double* x, const double* v) {
   Rep& R = c->rep_h[r];
   if (n_pairs < 0 || n_pairs > R.cap_pairs) return H4D_ECAPACITY;
@@ -326,6 +355,7 @@ static int upload_replica(h4d_ctx* c, int r, int n_pairs, const double* x, const
   int n = R.nw3 + 2 * n_pairs;
   std::vector<uint4> pos(n);
   std::vector<float4> vh(n), vl(n);
+  std::vector<double> vdraw(v ? 0 : 3 * (size_t)n);
   for (int a = 0; a < n; ++a) {
     pos[a] = make_uint4(to_fixed(x[3 * a], R.L), to_fixed(x[3 * a + 1], R.L), to_fixed(x[3 * a + 2], R.L), 0u);
     double vv[3];
@@ -341,12 +371,24 @@ static int upload_replica(h4d_ctx* c, int r, int n_pairs, const double* x, const
       vv[0] = sd * rad0 * std::cos(2.0 * M_PI * h_u01(q[1]));
       vv[1] = sd * rad0 * std::sin(2.0 * M_PI * h_u01(q[1]));
       vv[2] = sd * rad1 * std::cos(2.0 * M_PI * h_u01(q[3]));
+      vdraw[3 * a] = vv[0]; vdraw[3 * a + 1] = vv[1]; vdraw[3 * a + 2] = vv[2];
     }
+    if (!v && R.n_water > 0) continue;  // waters are projected below, then split
     float h, l;
     split_ff(vv[0], h, l); vh[a].x = h; vl[a].x = l;
     split_ff(vv[1], h, l); vh[a].y = h; vl[a].y = l;
     split_ff(vv[2], h, l); vh[a].z = h; vl[a].z = l;
     vh[a].w = vl[a].w = 0.f;
+  }
+  if (!v && R.n_water > 0) {
+    project_water_velocities(c->prm, R.n_water, R.L, x, vdraw.data());
+    for (int a = 0; a < n; ++a) {
+      float h, l;
+      split_ff(vdraw[3 * a], h, l); vh[a].x = h; vl[a].x = l;
+      split_ff(vdraw[3 * a + 1], h, l); vh[a].y = h; vl[a].y = l;
+      split_ff(vdraw[3 * a + 2], h, l); vh[a].z = h; vl[a].z = l;
+      vh[a].w = vl[a].w = 0.f;
+    }
   }
   if (n > 0) {
     CK(cudaMemcpyAsync(c->d_pos + R.atom_off, pos.data(), n * sizeof(uint4), cudaMemcpyHostToDevice, c->stream));

@@ -153,7 +153,10 @@ __device__ __forceinline__ float pair_fr(const Pot& P, const PairCoef<SYS>& c, f
   float r = r2 * rinv;
   float x = P.alpha * r;
   float ex = exp_neg_sq(x);
-  float erfcx = as_erfc_poly(x) * ex;
+  // LJ electrolyte: alpha r <= 1.2, where the A&S form (absolute error 1.5e-7) is ~1e-6
+  // relative; aqueous: alpha r reaches 2.5, where only a relatively accurate erfc keeps
+  // the cancelling water Coulomb sums at 1e-5, so the CUDA library erfcf is used there
+  float erfcx = (SYS == H4D_SYS_LJ) ? as_erfc_poly(x) * ex : erfcf(x);
   float fr_c = c.kq * g * fmaf(erfcx, rinv, P.two_alpha_sqrtpi * ex) * rinv2;
   fr_c = (r2 < P.rc2_c) ? fr_c : 0.0f;
   return fr_lj + fr_c;
@@ -171,7 +174,7 @@ __device__ __forceinline__ float pair_u32(const Pot& P, const PairCoef<SYS>& c, 
   }
   if (r2 < P.rc2_c) {
     float x = P.alpha * r2 * rinv;
-    float erfcx = as_erfc_poly(x) * exp_neg_sq(x);
+    float erfcx = (SYS == H4D_SYS_LJ) ? as_erfc_poly(x) * exp_neg_sq(x) : erfcf(x);
     u += c.kq * g * (erfcx * rinv - P.shift_c);
   }
   return u;
@@ -661,6 +664,9 @@ __device__ void force_pass_impl(const Ctx& c, int mode, float w_prev, double* ki
     const int i = a0 + sub;
     const bool active = i < n;
     float fx = 0.f, fy = 0.f, fz = 0.f, dwk = 0.f;
+    // aqueous: the per-atom force is a sum of hundreds of large, cancelling Coulomb
+    // terms, so it is accumulated with Kahan compensation (cx, cy, cz)
+    float cx = 0.f, cy = 0.f, cz = 0.f;
     const bool iflyer = NEMD && active && (i == fly0 || i == fly1);
     if (active) {
       const uint4 pi = v.pos[i];
@@ -697,9 +703,20 @@ __device__ void force_pass_impl(const Ctx& c, int mode, float w_prev, double* ki
           r2 = valid ? r2 : 1.0e30f;
           const PairCoef<SYS> cf = coef<SYS>(P, ti, type_t<SYS>(jj[u] & 0x7FFF, R.nw3));
           const float fr = pair_fr<SYS>(P, cf, r2, g);
-          fx = fmaf(-fr, dx, fx);
-          fy = fmaf(-fr, dy, fy);
-          fz = fmaf(-fr, dz, fz);
+          if (SYS == H4D_SYS_AQ) {
+            const float tx = -fr * dx - cx, ty = -fr * dy - cy, tz = -fr * dz - cz;
+            const float sx = fx + tx, sy = fy + ty, sz = fz + tz;
+            cx = (sx - fx) - tx;
+            cy = (sy - fy) - ty;
+            cz = (sz - fz) - tz;
+            fx = sx;
+            fy = sy;
+            fz = sz;
+          } else {
+            fx = fmaf(-fr, dx, fx);
+            fy = fmaf(-fr, dy, fy);
+            fz = fmaf(-fr, dz, fz);
+          }
         }
         q = qn;
       }
@@ -722,6 +739,11 @@ __device__ void force_pass_impl(const Ctx& c, int mode, float w_prev, double* ki
           dwk += un - uo;
         }
       }
+    }
+    if (SYS == H4D_SYS_AQ) {
+      fx -= cx;
+      fy -= cy;
+      fz -= cz;
     }
     for (int o = tpa >> 1; o > 0; o >>= 1) {
       fx += __shfl_xor_sync(0xffffffffu, fx, o, tpa);
@@ -757,6 +779,180 @@ __device__ void force_pass_impl(const Ctx& c, int mode, float w_prev, double* ki
 // ------------------------------------------------------------------------------------
 // Kick + drift pass: optional thermostat scale, half kick, fixed-point drift, move check
 // ------------------------------------------------------------------------------------
+// Rigid water, position stage of RATTLE (SHAKE): half kick of the three atoms, an
+// unconstrained drift, then pairwise corrections along the previous bond vectors until
+// O-H, O-H and H-H hold (the same impulses correct the half-step velocities).  Works in
+// FP32 coordinates relative to the old O position, taken from exact fixed-point
+// differences; the constrained displacements are added back in fixed point.
+__device__ __forceinline__ void top2(float d, float& a, float& b) {
+  if (d > a) { b = a; a = d; } else if (d > b) { b = d; }
+}
+__device__ void water_kick_drift(const Ctx& c, int m, float alpha, float& d1, float& d2, float& o1, float& o2,
+                                 int& bad) {
+  const Eng& e = *c.e;
+  const RepC& R = c.r;
+  const Pot& P = e.pot;
+  const GView& v = c.v;
+  const float h = (float)e.proto.dt;
+  const float imv[3] = {P.inv_m[2], P.inv_m[3], P.inv_m[3]};  // 1/(m mvv2e): O, H, H
+  const float mw[3] = {1.0f / P.inv_m[2], 1.0f / P.inv_m[3], 1.0f / P.inv_m[3]};
+  float4 vh[3], vl[3];
+  uint4 po[3];
+  float x[3][3], ro[3][3];
+  const int a0 = 3 * m;
+  for (int k = 0; k < 3; ++k) {
+    const int ga = R.atom_off + a0 + k;
+    vh[k] = e.vhi[ga];
+    vl[k] = e.vlo[ga];
+    if (alpha != 1.0f) {
+      ff_scale(vh[k].x, vl[k].x, alpha);
+      ff_scale(vh[k].y, vl[k].y, alpha);
+      ff_scale(vh[k].z, vl[k].z, alpha);
+    }
+    const float4 f = e.force[ga];
+    const float cm = 0.5f * h * imv[k];
+    ff_add(vh[k].x, vl[k].x, f.x * cm);
+    ff_add(vh[k].y, vl[k].y, f.y * cm);
+    ff_add(vh[k].z, vl[k].z, f.z * cm);
+    po[k] = v.pos[a0 + k];
+  }
+  // old positions relative to the old O; unconstrained new positions
+  for (int k = 0; k < 3; ++k) {
+    ro[k][0] = (float)(int)(po[k].x - po[0].x) * R.scale;
+    ro[k][1] = (float)(int)(po[k].y - po[0].y) * R.scale;
+    ro[k][2] = (float)(int)(po[k].z - po[0].z) * R.scale;
+    x[k][0] = ro[k][0] + (vh[k].x + vl[k].x) * h;
+    x[k][1] = ro[k][1] + (vh[k].y + vl[k].y) * h;
+    x[k][2] = ro[k][2] + (vh[k].z + vl[k].z) * h;
+  }
+  const int ca[3] = {0, 0, 1}, cb[3] = {1, 2, 2};
+  const float dd[3] = {(float)P.d_oh2, (float)P.d_oh2, (float)P.d_hh2};
+  float dv[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  for (int it = 0; it < 100; ++it) {
+    float worst = 0.f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int a = ca[q], b = cb[q];
+      float rn[3], rr[3], rn2 = 0.f, dot = 0.f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        rn[k] = x[a][k] - x[b][k];
+        rr[k] = ro[a][k] - ro[b][k];
+        rn2 = fmaf(rn[k], rn[k], rn2);
+        dot = fmaf(rn[k], rr[k], dot);
+      }
+      const float diff = rn2 - dd[q];
+      worst = fmaxf(worst, fabsf(diff) / dd[q]);
+      const float g = diff / (2.0f * dot * (1.0f / mw[a] + 1.0f / mw[b]));
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float da = -g * rr[k] / mw[a], db = g * rr[k] / mw[b];
+        x[a][k] += da;
+        x[b][k] += db;
+        dv[a][k] += da;
+        dv[b][k] += db;
+      }
+    }
+    if (worst < 2e-7f) break;
+  }
+  for (int k = 0; k < 3; ++k) {
+    const int ga = R.atom_off + a0 + k;
+    ff_add(vh[k].x, vl[k].x, dv[k][0] / h);
+    ff_add(vh[k].y, vl[k].y, dv[k][1] / h);
+    ff_add(vh[k].z, vl[k].z, dv[k][2] / h);
+    e.vhi[ga] = vh[k];
+    e.vlo[ga] = vl[k];
+    const float sx = (x[k][0] - ro[k][0]) / R.scale, sy = (x[k][1] - ro[k][1]) / R.scale,
+                sz = (x[k][2] - ro[k][2]) / R.scale;
+    if (!(fabsf(sx) < 1.0e9f && fabsf(sy) < 1.0e9f && fabsf(sz) < 1.0e9f)) { bad = 1; continue; }
+    uint4 p = po[k];
+    p.x += (unsigned)__float2int_rn(sx);
+    p.y += (unsigned)__float2int_rn(sy);
+    p.z += (unsigned)__float2int_rn(sz);
+    v.pos[a0 + k] = p;
+    top2(sqrtf((float)fixed_d2(p, e.ref[ga])), d1, d2);
+    top2(sqrtf((float)fixed_d2(p, e.ref_out[ga])), o1, o2);
+  }
+}
+
+// Rigid water, velocity stage of RATTLE: remove the bond-parallel relative velocities;
+// returns the kinetic energy of all atoms when want_k (after the projection)
+__device__ double rattle_pass(const Ctx& c, bool want_k) {
+  const Eng& e = *c.e;
+  const RepC& R = c.r;
+  const Pot& P = e.pot;
+  const GView& v = c.v;
+  const int n = v.s->n_tot;
+  const int fly0 = v.s->fly0, fly1 = v.s->fly1;
+  const float imv[3] = {P.inv_m[2], P.inv_m[3], P.inv_m[3]};
+  const int ca[3] = {0, 0, 1}, cb[3] = {1, 2, 2};
+  const float dd[3] = {(float)P.d_oh2, (float)P.d_oh2, (float)P.d_hh2};
+  double kin = 0.0;
+  for (int m = c.tid; m < R.n_water; m += c.T) {
+    const int a0 = 3 * m;
+    float4 vh[3], vl[3];
+    uint4 po[3];
+    float r[3][3], vv[3][3], dv[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    for (int k = 0; k < 3; ++k) {
+      const int ga = R.atom_off + a0 + k;
+      vh[k] = e.vhi[ga];
+      vl[k] = e.vlo[ga];
+      po[k] = v.pos[a0 + k];
+      vv[k][0] = vh[k].x + vl[k].x;
+      vv[k][1] = vh[k].y + vl[k].y;
+      vv[k][2] = vh[k].z + vl[k].z;
+    }
+    for (int k = 0; k < 3; ++k) {
+      r[k][0] = (float)(int)(po[k].x - po[0].x) * R.scale;
+      r[k][1] = (float)(int)(po[k].y - po[0].y) * R.scale;
+      r[k][2] = (float)(int)(po[k].z - po[0].z) * R.scale;
+    }
+    for (int it = 0; it < 100; ++it) {
+      float worst = 0.f;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int a = ca[q], b = cb[q];
+        float rab[3], dvv = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          rab[k] = r[a][k] - r[b][k];
+          dvv = fmaf(rab[k], (vv[a][k] + dv[a][k]) - (vv[b][k] + dv[b][k]), dvv);
+        }
+        worst = fmaxf(worst, fabsf(dvv) / dd[q]);
+        const float kk = dvv / (dd[q] * (imv[a] + imv[b]));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          dv[a][k] -= kk * imv[a] * rab[k];
+          dv[b][k] += kk * imv[b] * rab[k];
+        }
+      }
+      if (worst < 1e-7f) break;
+    }
+    for (int k = 0; k < 3; ++k) {
+      const int ga = R.atom_off + a0 + k;
+      ff_add(vh[k].x, vl[k].x, dv[k][0]);
+      ff_add(vh[k].y, vl[k].y, dv[k][1]);
+      ff_add(vh[k].z, vl[k].z, dv[k][2]);
+      e.vhi[ga] = vh[k];
+      e.vlo[ga] = vl[k];
+      if (want_k) {
+        const float x = vh[k].x + vl[k].x, y = vh[k].y + vl[k].y, z = vh[k].z + vl[k].z;
+        kin += 0.5 * (double)(1.0f / imv[k]) * (double)fmaf(x, x, fmaf(y, y, z * z));
+      }
+    }
+  }
+  if (!want_k) return 0.0;
+  for (int a = R.nw3 + c.tid; a < n; a += c.T) {
+    if (a == fly0 || a == fly1) continue;
+    const int ga = R.atom_off + a;
+    const float4 h = e.vhi[ga], l = e.vlo[ga];
+    const float x = h.x + l.x, y = h.y + l.y, z = h.z + l.z;
+    kin += 0.5 * (double)P.m_f[type_of(a, R.nw3)] * (double)fmaf(x, x, fmaf(y, y, z * z));
+  }
+  return group_sum(c, kin);
+}
+
+template <int SYS>
 __device__ void kick_drift(const Ctx& c, float alpha) {
   const Eng& e = *c.e;
   const RepC& R = c.r;
@@ -768,7 +964,13 @@ __device__ void kick_drift(const Ctx& c, float alpha) {
   int bad = 0;
   float d1 = 0.f, d2 = 0.f;  // this thread's two largest displacements (Verlet list)
   float o1 = 0.f, o2 = 0.f;  // the same against the outer-list reference
-  for (int a = c.tid; a < n; a += c.T) {
+  const int n_units = R.n_water + (n - R.nw3);  // rigid waters first, then ions
+  for (int u = c.tid; u < n_units; u += c.T) {
+    if (SYS == H4D_SYS_AQ && u < R.n_water) {
+      water_kick_drift(c, u, alpha, d1, d2, o1, o2, bad);
+      continue;
+    }
+    const int a = R.nw3 + (u - R.n_water);
     if (a == fly0 || a == fly1) continue;  // flyers keep their 3D state (Sec. II.B.1)
     const int ga = R.atom_off + a;
     float4 h = e.vhi[ga], l = e.vlo[ga];
@@ -794,10 +996,8 @@ __device__ void kick_drift(const Ctx& c, float alpha) {
     p.y += (unsigned)__float2int_rn(sy);
     p.z += (unsigned)__float2int_rn(sz);
     v.pos[a] = p;
-    const float dd = sqrtf((float)fixed_d2(p, e.ref[ga]));
-    if (dd > d1) { d2 = d1; d1 = dd; } else if (dd > d2) { d2 = dd; }
-    const float de = sqrtf((float)fixed_d2(p, e.ref_out[ga]));
-    if (de > o1) { o2 = o1; o1 = de; } else if (de > o2) { o2 = de; }
+    top2(sqrtf((float)fixed_d2(p, e.ref[ga])), d1, d2);
+    top2(sqrtf((float)fixed_d2(p, e.ref_out[ga])), o1, o2);
   }
   // A list stays valid while the two largest displacements since its build sum to less
   // than its skin (no pair distance can have shrunk by more).  Warp-level top-2 merges;
@@ -1015,11 +1215,17 @@ __device__ void md_phase(const Ctx& c, int n_steps) {
   initial_forces<SYS>(c);
   float alpha = 1.0f;
   for (int st = 0; st < n_steps; ++st) {
-    kick_drift(c, alpha);
+    kick_drift<SYS>(c, alpha);
     c.sync();
     maybe_rebuild(c);
     double K = 0.0;
-    force_pass<SYS, false>(c, 1 | 2, 0.f, &K);  // ends with group syncs
+    if (SYS == H4D_SYS_AQ && c.r.n_water > 0) {
+      force_pass<SYS, false>(c, 1, 0.f, nullptr);
+      c.sync();
+      K = rattle_pass(c, true);  // ends with group syncs
+    } else {
+      force_pass<SYS, false>(c, 1 | 2, 0.f, &K);  // ends with group syncs
+    }
     if (c.tid == 0) {
       const int n = S->n_tot;
       double a = csvr_alpha(e, R, (u64)(c.R - e.rep), R.step_ctr, K, n);
@@ -1156,7 +1362,7 @@ __device__ void trial_phase(const Ctx& c) {
   force_pass<SYS>(c, 0, 0.f, nullptr);
   c.sync();
   for (int k = 0; k < e.proto.n_f; ++k) {
-    kick_drift(c, 1.0f);
+    kick_drift<SYS>(c, 1.0f);
     c.sync();
     maybe_rebuild(c);
     const float w_prev = S->w_cur;
@@ -1173,6 +1379,10 @@ __device__ void trial_phase(const Ctx& c) {
     c.sync();
     force_pass<SYS>(c, 1 | 4, w_prev, nullptr);
     c.sync();
+    if (SYS == H4D_SYS_AQ && c.r.n_water > 0) {
+      rattle_pass(c, false);
+      c.sync();
+    }
     if (c.tid == 0) {
       const double y = (S->dW[0] + S->dW[1]) - S->wprot_c;
       const double t = S->wprot + y;

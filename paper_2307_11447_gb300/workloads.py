@@ -162,6 +162,38 @@ def lj_positions(n_pairs: int, L: float, seed: int, min_dist: float = 0.8) -> np
     return np.mod(x, L)
 
 
+def aqueous_positions(n_water: int, n_pairs: int, L: float, seed: int, d_oh: float = 1.0,
+                      hoh_deg: float = 109.47) -> np.ndarray:
+    """Rigid waters (O,H,H) and interleaved Na/Cl on randomly chosen sites of a cubic
+    lattice filling the box, each water with a uniformly random orientation."""
+    rng = np.random.default_rng(seed)
+    n_sites = n_water + 2 * n_pairs
+    m = int(math.ceil(n_sites ** (1.0 / 3.0)))
+    a = L / m
+    g = (np.stack(np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij"), -1).reshape(-1, 3) + 0.5) * a
+    sites = g[rng.permutation(len(g))[:n_sites]]
+    th = math.radians(hoh_deg)
+    ref = np.array([[0.0, 0.0, 0.0], [d_oh, 0.0, 0.0], [d_oh * math.cos(th), d_oh * math.sin(th), 0.0]])
+    out = np.zeros((3 * n_water + 2 * n_pairs, 3))
+    for w in range(n_water):
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        a0, b, c, d = q
+        rot = np.array([[a0 * a0 + b * b - c * c - d * d, 2 * (b * c - a0 * d), 2 * (b * d + a0 * c)],
+                        [2 * (b * c + a0 * d), a0 * a0 - b * b + c * c - d * d, 2 * (c * d - a0 * b)],
+                        [2 * (b * d - a0 * c), 2 * (c * d + a0 * b), a0 * a0 - b * b - c * c + d * d]])
+        out[3 * w: 3 * w + 3] = sites[w] + ref @ rot.T
+    out[3 * n_water:] = sites[n_water:]
+    return np.mod(out, L)
+
+
+def aq_config(n_water: int, n_pairs: int, L: float, n_f: int, **extra) -> dict:
+    cfg = dict(AQ_PHYSICS)
+    cfg.update(n_water=n_water, n_pairs=n_pairs, L=L, n_f=n_f)
+    cfg.update(extra)
+    return cfg
+
+
 def batched_replicas(n_rep: int = 256, seed: int = 7, n_min: int = 100, n_max: int = 1000,
                      rho_min: float = 0.1, rho_max: float = 0.4, min_box: float = 8.6):
     """Ion counts uniform in [n_min, n_max] (even) and densities uniform in
@@ -188,3 +220,12 @@ def batched_system(n_rep: int = 256, seed: int = 7):
         cap = n // 2 + max(16, (3 * n) // 20)
         reps.append(dict(L=L, n_pairs=n // 2, cap_pairs=cap, x=lj_positions(n // 2, L, 10000 + k), rho=rho))
     return cfg, reps
+
+
+# aqueous NaCl (~1 m): 3000 rigid waters + 55 Na+ + 55 Cl-, L = 45 A, NaCl-pair NEMD over
+# 1000 steps of 1 fs, 2000 equilibrium steps between trials
+def _aq_main():
+    return aq_config(3000, 55, 45.0, 1000, n_eq=2000, cap_pairs=80, beta_mu=-60.0)
+
+
+CONFIGS["nacl_aq"] = _aq_main()
