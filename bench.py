@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="h4d", choices=["h4d", "reference"])
-    ap.add_argument("--chains", type=int, default=304)
+    ap.add_argument("--chains", type=int, default=None, help="chains per GPU (default: 304 LJ, 152 aqueous)")
     ap.add_argument("--sequential", type=int, default=0,
                     help="batched workload: also time this many replicas run one at a time (alone on the GPU)")
     ap.add_argument("--workload", default="lj4000")
@@ -74,6 +74,13 @@ def workload(name, chains, rank):
         cfg["n_eq"] = ARGS.n_eq
     if ARGS.n_f is not None:
         cfg["n_f"] = ARGS.n_f
+    if name == "nacl_aq":
+        reps = []
+        for c in range(chains):
+            x = wl.aqueous_positions(cfg["n_water"], cfg["n_pairs"], cfg["L"], 2000 * (rank + 1) + c)
+            reps.append(dict(L=cfg["L"], n_pairs=cfg["n_pairs"], cap_pairs=cfg["cap_pairs"], x=x,
+                             n_water=cfg["n_water"]))
+        return cfg, reps
     reps = []
     for c in range(chains):
         seed = 1000 * (rank + 1) + c
@@ -196,9 +203,9 @@ def run_gpu(args):
     atom_steps = 0.0
     nemd_atom_steps = 0.0
     accepted = 0
-    for a, b in zip(c0, c1):
+    for r, (a, b) in enumerate(zip(c0, c1)):
         mean_pairs = (b["sum_n"] - a["sum_n"]) / max(b["cycles"] - a["cycles"], 1)
-        n_atoms = 2.0 * mean_pairs
+        n_atoms = 2.0 * mean_pairs + 3.0 * reps[r].get("n_water", 0)
         atom_steps += n_atoms * (n_eq + n_f) * args.steps
         nemd_atom_steps += n_atoms * n_f * args.steps
         accepted += (b["accepted_ins"] + b["accepted_del"]) - (a["accepted_ins"] + a["accepted_del"])
@@ -281,6 +288,11 @@ def run_gpu(args):
 
 
 def workload_config(args, cfg, reps, n_f, n_eq, world):
+    if args.workload == "nacl_aq":
+        return {"workload": f"aqueous NaCl: {cfg['n_water']} rigid waters + {cfg['n_pairs']} NaCl, L={cfg['L']} A, "
+                            f"N_f={n_f}, N_eq={n_eq}, {len(reps)} chains/GPU", "chains_per_gpu": len(reps),
+                "n_f": n_f, "n_eq": n_eq, "parallelism": f"replicas x{world}",
+                "l2": "state > L2; no flush needed"}
     if args.workload == "batched256":
         ns = [2 * r["n_pairs"] for r in reps]
         return {"workload": f"batched: {len(reps)} LJ-electrolyte replicas, ions {min(ns)}-{max(ns)}, "
@@ -340,14 +352,15 @@ def run_e2e(ctx, reps, args, n_eq, n_f, stream, world, dist):
     for k in range(args.steps):
         for r in range(ctx.R):
             x = xs[r].numpy()
-            ctx.h4d_set_state(r, x.shape[0] // 2, x, vs[r].numpy())
+            nw = reps[r].get("n_water", 0)
+            ctx.h4d_set_state(r, (x.shape[0] - 3 * nw) // 2, x, vs[r].numpy())
         ctx.h4d_run_trials(1, n_eq)
         d2h = 0
         for r in range(ctx.R):
             c = ctx.h4d_get_counts(r)
             rec = ctx.h4d_get_work(r, 1)
             d2h += 8 * 14 + rec.nbytes
-            atom_steps += 2.0 * c["n_pairs"] * (n_eq + n_f)
+            atom_steps += (2.0 * c["n_pairs"] + 3.0 * reps[r].get("n_water", 0)) * (n_eq + n_f)
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
     if dist is not None:
@@ -441,6 +454,8 @@ ARGS = None
 def main():
     global ARGS
     args = parse()
+    if args.chains is None:
+        args.chains = 152 if args.workload == "nacl_aq" else 304
     ARGS = args
     if args.impl == "reference":
         run_reference(args)

@@ -174,15 +174,15 @@ def aqueous_positions(n_water: int, n_pairs: int, L: float, seed: int, d_oh: flo
     sites = g[rng.permutation(len(g))[:n_sites]]
     th = math.radians(hoh_deg)
     ref = np.array([[0.0, 0.0, 0.0], [d_oh, 0.0, 0.0], [d_oh * math.cos(th), d_oh * math.sin(th), 0.0]])
+    q = rng.normal(size=(n_water, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    a0, b, c, d = q.T
+    rot = np.stack([
+        np.stack([a0 * a0 + b * b - c * c - d * d, 2 * (b * c - a0 * d), 2 * (b * d + a0 * c)], -1),
+        np.stack([2 * (b * c + a0 * d), a0 * a0 - b * b + c * c - d * d, 2 * (c * d - a0 * b)], -1),
+        np.stack([2 * (b * d - a0 * c), 2 * (c * d + a0 * b), a0 * a0 - b * b - c * c + d * d], -1)], 1)
     out = np.zeros((3 * n_water + 2 * n_pairs, 3))
-    for w in range(n_water):
-        q = rng.normal(size=4)
-        q /= np.linalg.norm(q)
-        a0, b, c, d = q
-        rot = np.array([[a0 * a0 + b * b - c * c - d * d, 2 * (b * c - a0 * d), 2 * (b * d + a0 * c)],
-                        [2 * (b * c + a0 * d), a0 * a0 - b * b + c * c - d * d, 2 * (c * d - a0 * b)],
-                        [2 * (b * d - a0 * c), 2 * (c * d + a0 * b), a0 * a0 - b * b - c * c + d * d]])
-        out[3 * w: 3 * w + 3] = sites[w] + ref @ rot.T
+    out[: 3 * n_water] = (sites[:n_water, None, :] + np.einsum("kj,wij->wki", ref, rot)).reshape(-1, 3)
     out[3 * n_water:] = sites[n_water:]
     return np.mod(out, L)
 
