@@ -562,6 +562,137 @@ double orc_nemd_path(const orc_params* p, orc_state* s, const int32_t* flyers, i
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* Learned insertion-site proposal (definitions in h4d_oracle.h)                         */
+/* ------------------------------------------------------------------------------------ */
+static int species_of(int type) { return type <= 2 ? type : -1; } /* water H is not counted */
+
+/* cell coordinate of a fixed-point coordinate X: floor(X G / 2^32) */
+static int cell_coord(uint32_t X, int G) { return (int)(((uint64_t)X * (uint64_t)G) >> 32); }
+
+static int cell_of_atom(const double* x, double L, int G) {
+  int gx = cell_coord(fixpt(x[0], L), G), gy = cell_coord(fixpt(x[1], L), G), gz = cell_coord(fixpt(x[2], L), G);
+  return (gx * G + gy) * G + gz;
+}
+
+int orc_proposal_features(const orc_params* p, int G, int n, const double* x, int ex0, int ex1,
+                          double* feat) {
+  int nc = G * G * G;
+  double h = p->L / G;
+  memset(feat, 0, sizeof(double) * (size_t)nc * ORC_NFEAT);
+  for (int a = 0; a < n; ++a) {
+    if (a == ex0 || a == ex1) continue;
+    int t = orc_atom_type(p, a);
+    int sp = species_of(t);
+    double qa = p->q[t];
+    int g[3];
+    for (int k = 0; k < 3; ++k) g[k] = cell_coord(fixpt(x[3 * a + k], p->L), G);
+    for (int dx = -1; dx <= 1; ++dx)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dz = -1; dz <= 1; ++dz) {
+          /* cell c = g + d sees this atom at neighbour offset -d */
+          int c[3] = {(g[0] + dx + G) % G, (g[1] + dy + G) % G, (g[2] + dz + G) % G};
+          double* f = feat + (size_t)((c[0] * G + c[1]) * G + c[2]) * ORC_NFEAT;
+          int slot = (1 - dx) * 9 + (1 - dy) * 3 + (1 - dz);
+          if (sp >= 0) f[sp * 27 + slot] += 0.25;
+          if (qa != 0.0) {
+            double d[3], r2 = 0.0;
+            for (int k = 0; k < 3; ++k) {
+              d[k] = minimg((c[k] + 0.5) * h - x[3 * a + k], p->L);
+              r2 += d[k] * d[k];
+            }
+            double r = fmax(sqrt(r2), 0.5);
+            for (int k = 0; k < 3; ++k) f[81 + k] += 0.1 * qa * d[k] / (r * r * r);
+          }
+        }
+  }
+  return 0;
+}
+
+/* round to bfloat16 (nearest, ties to even) through binary32 */
+static double bf16r(double v) {
+  float f = (float)v;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  u &= 0xffff0000u;
+  memcpy(&f, &u, 4);
+  return (double)f;
+}
+
+/* one dense layer y = act(x W + b) of nin -> nout (W row-major [nin][nout]) */
+static void dense(const double* xin, int nin, const double* W, const double* b, int nout, int relu,
+                  int bf16, double* y) {
+  for (int j = 0; j < nout; ++j) {
+    double s = 0.0;
+    for (int i = 0; i < nin; ++i) {
+      double wij = W[(size_t)i * nout + j];
+      s += (bf16 ? bf16r(xin[i]) * bf16r(wij) : xin[i] * wij);
+    }
+    if (bf16) s = (double)((float)s + (float)b[j]);
+    else s += b[j];
+    y[j] = (relu && s < 0.0) ? 0.0 : s;
+  }
+}
+
+int orc_proposal_logits(const orc_params* p, const orc_proposal* q, int n, const double* x,
+                        int ex0, int ex1, double* logits) {
+  int nc = q->G * q->G * q->G;
+  double* feat = (double*)malloc(sizeof(double) * (size_t)nc * ORC_NFEAT);
+  orc_proposal_features(p, q->G, n, x, ex0, ex1, feat);
+  const double* W1 = q->w;
+  const double* b1 = W1 + ORC_NFEAT * ORC_HID;
+  const double* W2 = b1 + ORC_HID;
+  const double* b2 = W2 + ORC_HID * ORC_HID;
+  const double* W3 = b2 + ORC_HID;
+  const double* b3 = W3 + ORC_HID * 2;
+  double h1[ORC_HID], h2[ORC_HID];
+  for (int c = 0; c < nc; ++c) {
+    dense(feat + (size_t)c * ORC_NFEAT, ORC_NFEAT, W1, b1, ORC_HID, 1, q->bf16, h1);
+    dense(h1, ORC_HID, W2, b2, ORC_HID, 1, q->bf16, h2);
+    dense(h2, ORC_HID, W3, b3, 2, 0, q->bf16, logits + 2 * (size_t)c);
+  }
+  free(feat);
+  return 0;
+}
+
+/* softmax weights e_k = exp(l_k - max l) of species s and their sum */
+static double soft_weights(const double* logits, int s, int nc, double* e) {
+  double m = -INFINITY, Z = 0.0;
+  for (int k = 0; k < nc; ++k) m = fmax(m, logits[2 * k + s]);
+  for (int k = 0; k < nc; ++k) {
+    e[k] = exp(logits[2 * k + s] - m);
+    Z += e[k];
+  }
+  return Z;
+}
+
+/* draw a cell of species s: with probability eps a uniform cell, else inverse CDF of the
+ * softmax (first cell whose running sum exceeds u Z) */
+static int draw_cell(const double* e, double Z, int nc, double eps, uint64_t r_mix, uint64_t r_cell) {
+  if (u01(r_mix) < eps) return pick(r_cell, nc);
+  double target = u01(r_cell) * Z, cum = 0.0;
+  int last = 0;
+  for (int k = 0; k < nc; ++k) {
+    if (e[k] > 0.0) last = k;
+    cum += e[k];
+    if (cum > target) return k;
+  }
+  return last;
+}
+
+static double ln_qn(const double* e, double Z, int nc, double eps, int k) {
+  return log(((1.0 - eps) * e[k] / Z + eps / nc) * nc);
+}
+
+/* a fixed-point coordinate uniform over the cell's coordinates: X in [ceil(g 2^32/G),
+ * ceil((g+1) 2^32/G)) */
+static uint32_t place_in_cell(int g, int G, uint32_t r32) {
+  uint64_t lo = (((uint64_t)g << 32) + (uint64_t)G - 1) / (uint64_t)G;
+  uint64_t hi = (((uint64_t)(g + 1) << 32) + (uint64_t)G - 1) / (uint64_t)G;
+  return (uint32_t)(lo + (((uint64_t)r32 * (hi - lo)) >> 32));
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* One pair-exchange trial                                                               */
 /* ------------------------------------------------------------------------------------ */
 static void flip_all(double* v, int n) {
@@ -575,6 +706,9 @@ static void flip_all(double* v, int n) {
  *            insertion: [0..2] cation x,y,z and [3] anion x as 32-bit box fractions
  *   block 2: insertion: [0..1] anion y,z
  *   blocks 3-4: Maxwell-Boltzmann velocities of the inserted cation and anion
+ *   block 5: learned proposal only: [0], [1] choose the uniform component (u < eps) for
+ *            the cation and the anion cell, [2], [3] draw the cation and the anion cell;
+ *            the 32-bit draws of blocks 1-2 then place each ion inside its cell
  * Readings: insertion and deletion are proposed with probability 1/2 each; the cation
  * and the anion are chosen independently (Eq. 3 squares 1/(N+1)); the momentum
  * reversal flips every velocity with probability 1/2 before NEMD and again after the
@@ -584,14 +718,16 @@ static void flip_all(double* v, int n) {
  * flyers' kinetic energy is left out: insertion draws it from Maxwell-Boltzmann and a
  * deletion discards it, so it cancels against the e^{-beta K}/N_k factors of Eqs. 3-4.
  */
-int orc_trial(const orc_params* p, orc_state* s, orc_record* rec) {
+int orc_trial_prop(const orc_params* p, const orc_proposal* q, orc_state* s, orc_record* rec,
+                   double* site_feat, double* site_y) {
   uint64_t t = s->trial_ctr++;
-  uint64_t b0[4], b1[4], b2[4], b3[4], b4[4];
+  uint64_t b0[4], b1[4], b2[4], b3[4], b4[4], b5[4];
   draw(p, t, 0, ORC_PUR_TRIAL, b0);
   draw(p, t, 1, ORC_PUR_TRIAL, b1);
   draw(p, t, 2, ORC_PUR_TRIAL, b2);
   draw(p, t, 3, ORC_PUR_TRIAL, b3);
   draw(p, t, 4, ORC_PUR_TRIAL, b4);
+  draw(p, t, 5, ORC_PUR_TRIAL, b5);
   int insertion = (int)(b0[0] >> 63);
   int flip_start = (int)(b0[1] >> 63), flip_end = (int)(b0[2] >> 63);
   double ln_u = log(u01_open(b0[3]));
@@ -605,7 +741,11 @@ int orc_trial(const orc_params* p, orc_state* s, orc_record* rec) {
   rec->n_before = N;
   rec->n_after = N;
   rec->cation = rec->anion = -1;
+  rec->cell_c = rec->cell_a = -1;
   rec->ln_u = ln_u;
+  int learned = q && q->mode == 1;
+  int G = q ? q->G : 0, nc = G * G * G;
+  double ln_q = 0.0;
 
   if (flip_start) flip_all(s->v, n);
   if ((!insertion && N == 0) || (insertion && N >= s->cap_pairs)) {
@@ -628,12 +768,39 @@ int orc_trial(const orc_params* p, orc_state* s, orc_record* rec) {
     ci = base + 2 * N;
     ai = ci + 1;
     double h = p->L / 4294967296.0;
-    s->x[3 * ci + 0] = (double)(uint32_t)(b1[0] >> 32) * h;
-    s->x[3 * ci + 1] = (double)(uint32_t)(b1[1] >> 32) * h;
-    s->x[3 * ci + 2] = (double)(uint32_t)(b1[2] >> 32) * h;
-    s->x[3 * ai + 0] = (double)(uint32_t)(b1[3] >> 32) * h;
-    s->x[3 * ai + 1] = (double)(uint32_t)(b2[0] >> 32) * h;
-    s->x[3 * ai + 2] = (double)(uint32_t)(b2[1] >> 32) * h;
+    uint32_t X[6] = {(uint32_t)(b1[0] >> 32), (uint32_t)(b1[1] >> 32), (uint32_t)(b1[2] >> 32),
+                     (uint32_t)(b1[3] >> 32), (uint32_t)(b2[0] >> 32), (uint32_t)(b2[1] >> 32)};
+    if (learned) {
+      /* draw the two cells from the proposal of the start state (flyers absent), then
+       * place each ion uniformly inside its cell with the same 32-bit draws */
+      double* lg = (double*)malloc(sizeof(double) * 2 * (size_t)nc);
+      double* e = (double*)malloc(sizeof(double) * (size_t)nc);
+      orc_proposal_logits(p, q, n, s->x, -1, -1, lg);
+      for (int sp = 0; sp < 2; ++sp) {
+        double Z = soft_weights(lg, sp, nc, e);
+        int k = draw_cell(e, Z, nc, q->eps, b5[sp], b5[2 + sp]);
+        ln_q += ln_qn(e, Z, nc, q->eps, k);
+        int g[3] = {k / (G * G), (k / G) % G, k % G};
+        for (int d = 0; d < 3; ++d) X[3 * sp + d] = place_in_cell(g[d], G, X[3 * sp + d]);
+      }
+      free(lg);
+      free(e);
+    }
+    for (int d = 0; d < 3; ++d) {
+      s->x[3 * ci + d] = (double)X[d] * h;
+      s->x[3 * ai + d] = (double)X[3 + d] * h;
+    }
+    if (q) {
+      rec->cell_c = cell_of_atom(&s->x[3 * ci], p->L, G);
+      rec->cell_a = cell_of_atom(&s->x[3 * ai], p->L, G);
+      if (site_feat) {
+        double* f = (double*)malloc(sizeof(double) * (size_t)nc * ORC_NFEAT);
+        orc_proposal_features(p, G, n, s->x, -1, -1, f);
+        memcpy(site_feat, f + (size_t)rec->cell_c * ORC_NFEAT, sizeof(double) * ORC_NFEAT);
+        memcpy(site_feat + ORC_NFEAT, f + (size_t)rec->cell_a * ORC_NFEAT, sizeof(double) * ORC_NFEAT);
+        free(f);
+      }
+    }
     double sdc = sqrt(1.0 / (p->beta * p->mass[0] * p->mvv2e));
     double sda = sqrt(1.0 / (p->beta * p->mass[1] * p->mvv2e));
     s->v[3 * ci + 0] = sdc * gauss_cos(b3[0], b3[1]);
@@ -666,6 +833,29 @@ int orc_trial(const orc_params* p, orc_state* s, orc_record* rec) {
     Uend = orc_energy_forces(p, n, s->x, NULL, gone, NULL);
     Kend = orc_kinetic(p, n, s->v, fly);
     free(gone);
+    if (q) {
+      /* the reverse insertion would draw these cells from the end state, flyers removed */
+      rec->cell_c = cell_of_atom(&s->x[3 * ci], p->L, G);
+      rec->cell_a = cell_of_atom(&s->x[3 * ai], p->L, G);
+      if (learned) {
+        double* lg = (double*)malloc(sizeof(double) * 2 * (size_t)nc);
+        double* e = (double*)malloc(sizeof(double) * (size_t)nc);
+        orc_proposal_logits(p, q, n, s->x, ci, ai, lg);
+        for (int sp = 0; sp < 2; ++sp) {
+          double Z = soft_weights(lg, sp, nc, e);
+          ln_q += ln_qn(e, Z, nc, q->eps, sp == 0 ? rec->cell_c : rec->cell_a);
+        }
+        free(lg);
+        free(e);
+      }
+      if (site_feat) {
+        double* f = (double*)malloc(sizeof(double) * (size_t)nc * ORC_NFEAT);
+        orc_proposal_features(p, G, n, s->x, ci, ai, f);
+        memcpy(site_feat, f + (size_t)rec->cell_c * ORC_NFEAT, sizeof(double) * ORC_NFEAT);
+        memcpy(site_feat + ORC_NFEAT, f + (size_t)rec->cell_a * ORC_NFEAT, sizeof(double) * ORC_NFEAT);
+        free(f);
+      }
+    }
   }
   double dH = (Uend + Kend) - (Ustart + Kstart);
   rec->dH = dH;
@@ -678,6 +868,10 @@ int orc_trial(const orc_params* p, orc_state* s, orc_record* rec) {
     rec->beta_dM = -p->beta * dH - 2.0 * log(V / (double)N);
     x_acc = rec->beta_dM - p->beta_mu;
   }
+  if (site_y) *site_y = insertion ? x_acc : -x_acc;
+  /* the proposal density relative to uniform: q(site) G^3 per ion */
+  x_acc += insertion ? -ln_q : ln_q;
+  rec->ln_q = ln_q;
   rec->x_acc = x_acc;
   int accept = isfinite(dH) && (ln_u < x_acc);
   if (!isfinite(dH)) rec->status = 3;
@@ -709,10 +903,19 @@ int orc_trial(const orc_params* p, orc_state* s, orc_record* rec) {
   return 0;
 }
 
-int orc_run_cycles(const orc_params* p, orc_state* s, int64_t n_cycles, int64_t n_eq, orc_record* recs) {
+int orc_trial(const orc_params* p, orc_state* s, orc_record* rec) {
+  return orc_trial_prop(p, NULL, s, rec, NULL, NULL);
+}
+
+int orc_run_cycles_prop(const orc_params* p, const orc_proposal* q, orc_state* s, int64_t n_cycles,
+                        int64_t n_eq, orc_record* recs) {
   for (int64_t c = 0; c < n_cycles; ++c) {
     if (n_eq > 0) orc_md(p, s, n_eq);
-    orc_trial(p, s, &recs[c]);
+    orc_trial_prop(p, q, s, &recs[c], NULL, NULL);
   }
   return 0;
+}
+
+int orc_run_cycles(const orc_params* p, orc_state* s, int64_t n_cycles, int64_t n_eq, orc_record* recs) {
+  return orc_run_cycles_prop(p, NULL, s, n_cycles, n_eq, recs);
 }

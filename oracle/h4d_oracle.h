@@ -71,12 +71,14 @@ typedef struct {
   int32_t n_before, n_after;
   int32_t status;     /* 0 ok, 1 deletion from empty system, 2 capacity, 3 non-finite energy */
   int32_t cation, anion;  /* chosen pair (deletion) or -1 */
+  int32_t cell_c, cell_a; /* proposal-grid cells of the exchanged cation and anion, or -1 */
   int32_t pad;
   double dH;          /* H_end - H_start in energy units */
   double beta_dM;     /* beta * Delta M, insertion-direction convention (Eqs. 6, 8) */
   double w_prot;      /* protocol work sum_k [U(w_{k+1}) - U(w_k)] at fixed positions */
   double ln_u;        /* log of the uniform acceptance draw */
   double x_acc;       /* exponent compared with ln_u */
+  double ln_q;        /* log proposal-density factor included in x_acc (0 for uniform) */
 } orc_record;
 
 void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
@@ -124,6 +126,52 @@ int orc_run_cycles(const orc_params* p, orc_state* s, int64_t n_cycles, int64_t 
 
 /* draw initial Maxwell-Boltzmann velocities for all atoms */
 void orc_init_velocities(const orc_params* p, orc_state* s);
+
+/* ------------------------------------------------------------------------------------ */
+/* Learned insertion-site proposal.  The box is cut into G^3 cells (cell index           */
+/* (gx*G + gy)*G + gz, an atom with fixed-point coordinate X is in gx = floor(X G / 2^32)). */
+/* Each cell has 96 features: for species s (cation, anion, water O) and each of the 27  */
+/* cells of its 3x3x3 neighbourhood (slot (ex+1)*9 + (ey+1)*3 + (ez+1) for offset e),     */
+/* 0.25 x the number of atoms (81); 0.1 x sum_j q_j d_j / max(|d_j|, 0.5)^3 over the      */
+/* charges of those 27 cells, d_j = minimum image of (cell centre - x_j) (3); 12 zeros.  */
+/* An MLP 96-64-64-2 (ReLU) maps them to a cation and an anion logit; the proposal of    */
+/* species s is q_s = (1 - eps) softmax_cells(logit_s) + eps / G^3, and an ion is placed */
+/* uniformly inside the drawn cell.  The ratio of this density to the uniform 1/V enters */
+/* the acceptance exponent (the role of B^ins / B^del in Eqs. 15-16): insertion adds     */
+/* -ln(q_c G^3) - ln(q_a G^3) with q from the start state, deletion adds                 */
+/* +ln(q_c G^3) + ln(q_a G^3) with q from the end state (flyers removed).                */
+/* ------------------------------------------------------------------------------------ */
+#define ORC_NFEAT 96
+#define ORC_HID 64
+#define ORC_PROP_NW (ORC_NFEAT * ORC_HID + ORC_HID + ORC_HID * ORC_HID + ORC_HID + ORC_HID * 2 + 2)
+
+typedef struct {
+  int32_t mode;     /* 0 uniform placement, 1 learned density */
+  int32_t G;        /* cells per box edge (>= 3) */
+  int32_t bf16;     /* 1: round features, weights and hidden activations to bfloat16 and
+                       sum each layer in binary32, the precision in which the GPU kernel
+                       takes the cell decision; 0: plain FP64 */
+  int32_t pad;
+  double eps;       /* weight of the uniform component */
+  const double* w;  /* ORC_PROP_NW weights, flat: W1[96][64], b1[64], W2[64][64], b2[64],
+                       W3[64][2], b3[2] (row index = input unit) */
+} orc_proposal;
+
+/* features of every cell of n atoms (ex0/ex1 = atoms to leave out, or -1) */
+int orc_proposal_features(const orc_params* p, int G, int n, const double* x, int ex0, int ex1,
+                          double* feat);
+/* logits [G^3][2] of every cell */
+int orc_proposal_logits(const orc_params* p, const orc_proposal* q, int n, const double* x,
+                        int ex0, int ex1, double* logits);
+/* one trial with the given proposal (q NULL: uniform, no cells).  If site_feat is given
+ * (and q is), it receives the features of the cation's and the anion's cell [2][96] in the
+ * N-pair state of the move (start state of an insertion, end state of a deletion) and
+ * site_y the insertion-direction exponent without the proposal factor (x_acc of an
+ * insertion, -x_acc of a deletion) -- the training record of the move. */
+int orc_trial_prop(const orc_params* p, const orc_proposal* q, orc_state* s, orc_record* rec,
+                   double* site_feat, double* site_y);
+int orc_run_cycles_prop(const orc_params* p, const orc_proposal* q, orc_state* s, int64_t n_cycles,
+                        int64_t n_eq, orc_record* recs);
 
 #ifdef __cplusplus
 }

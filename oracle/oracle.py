@@ -86,14 +86,46 @@ RECORD_DTYPE = np.dtype(
         ("status", np.int32),
         ("cation", np.int32),
         ("anion", np.int32),
+        ("cell_c", np.int32),
+        ("cell_a", np.int32),
         ("pad", np.int32),
         ("dH", np.float64),
         ("beta_dM", np.float64),
         ("w_prot", np.float64),
         ("ln_u", np.float64),
         ("x_acc", np.float64),
+        ("ln_q", np.float64),
     ]
 )
+PROP_NW = 96 * 64 + 64 + 64 * 64 + 64 + 64 * 2 + 2
+
+
+class Proposal(ctypes.Structure):
+    """learned insertion-site proposal (mode 0 uniform, 1 learned); keeps its weights alive"""
+    _fields_ = [
+        ("mode", ctypes.c_int32),
+        ("G", ctypes.c_int32),
+        ("bf16", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+        ("eps", ctypes.c_double),
+        ("w", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+def make_proposal(G: int, weights=None, eps: float = 0.1, bf16: bool = True) -> Proposal:
+    q = Proposal()
+    q.G = int(G)
+    q.eps = float(eps)
+    q.bf16 = int(bf16)
+    if weights is None:
+        q.mode = 0
+        q._w = np.zeros(PROP_NW)
+    else:
+        q.mode = 1
+        q._w = np.ascontiguousarray(weights, np.float64)
+        assert q._w.size == PROP_NW
+    q.w = _ptr(q._w)
+    return q
 
 _lib = None
 
@@ -128,6 +160,11 @@ def lib():
         _lib.orc_run_cycles.argtypes = [P, S, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
         _lib.orc_init_velocities.argtypes = [P, S]
         _lib.orc_atom_type.argtypes = [P, ctypes.c_int]
+        Q = ctypes.POINTER(Proposal)
+        _lib.orc_proposal_features.argtypes = [P, ctypes.c_int, ctypes.c_int, pd, ctypes.c_int, ctypes.c_int, pd]
+        _lib.orc_proposal_logits.argtypes = [P, Q, ctypes.c_int, pd, ctypes.c_int, ctypes.c_int, pd]
+        _lib.orc_trial_prop.argtypes = [P, Q, S, ctypes.c_void_p, pd, pd]
+        _lib.orc_run_cycles_prop.argtypes = [P, Q, S, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
     return _lib
 
 
@@ -287,3 +324,36 @@ def init_velocities(p: Params, st: State) -> None:
 
 def atom_type(p: Params, a: int) -> int:
     return lib().orc_atom_type(ctypes.byref(p), a)
+
+
+def proposal_features(p: Params, G: int, x: np.ndarray, exclude=(-1, -1)) -> np.ndarray:
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    out = np.zeros((G**3, 96), np.float64)
+    lib().orc_proposal_features(ctypes.byref(p), G, x.shape[0], _ptr(x), int(exclude[0]), int(exclude[1]), _ptr(out))
+    return out
+
+
+def proposal_logits(p: Params, q: Proposal, x: np.ndarray, exclude=(-1, -1)) -> np.ndarray:
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    out = np.zeros((q.G**3, 2), np.float64)
+    lib().orc_proposal_logits(ctypes.byref(p), ctypes.byref(q), x.shape[0], _ptr(x), int(exclude[0]),
+                              int(exclude[1]), _ptr(out))
+    return out
+
+
+def trial_prop(p: Params, q: Proposal | None, st: State, want_site: bool = False):
+    """one trial with the proposal q; with want_site also the move's training record
+    (features [2, 96] of the cation and anion cells, insertion-direction exponent)"""
+    rec = np.zeros(1, RECORD_DTYPE)
+    feat = np.zeros((2, 96), np.float64) if want_site else None
+    y = np.zeros(1, np.float64) if want_site else None
+    lib().orc_trial_prop(ctypes.byref(p), None if q is None else ctypes.byref(q), ctypes.byref(st.s),
+                         rec.ctypes.data, _ptr(feat), _ptr(y))
+    return (rec[0], feat, float(y[0])) if want_site else rec[0]
+
+
+def run_cycles_prop(p: Params, q: Proposal | None, st: State, n_cycles: int, n_eq: int) -> np.ndarray:
+    recs = np.zeros(n_cycles, RECORD_DTYPE)
+    lib().orc_run_cycles_prop(ctypes.byref(p), None if q is None else ctypes.byref(q), ctypes.byref(st.s),
+                              n_cycles, n_eq, recs.ctypes.data)
+    return recs
