@@ -156,6 +156,41 @@ static double pair_term(const orc_params* p, const double* x, const double* w, c
   double dw = w ? (w[i] - w[j]) : 0.0;
   double r4 = sqrt(r2 + dw * dw);
   double rmax = p->rc_lj > p->rc_coul ? p->rc_lj : p->rc_coul;
+#ifdef ORC_FP32_FORCES
+  /* Tolerance-derivation build only (liboracle_fp32.so): the same pair force evaluated in
+   * binary32 (distance, cut-off test, LJ and Coulomb derivative), everything else FP64.
+   * Comparing it with the FP64 build measures how far FP32 pair forces alone move a
+   * trajectory's work. */
+  if (F) {
+    int ti = orc_atom_type(p, i), tj = orc_atom_type(p, j);
+    float df[3] = {(float)d[0], (float)d[1], (float)d[2]};
+    float dwf = (float)dw;
+    float r2f = df[0] * df[0] + df[1] * df[1] + df[2] * df[2] + dwf * dwf;
+    float rmf = (float)rmax;
+    if (r2f >= rmf * rmf) return 0.0;
+    float rf = sqrtf(r2f);
+    float sig = (float)(0.5 * (p->sig[ti] + p->sig[tj])), eps = (float)sqrt(p->eps[ti] * p->eps[tj]);
+    float du = 0.f;
+    if (eps > 0.f && r2f < (float)(p->rc_lj * p->rc_lj)) {
+      float s2 = sig * sig / r2f, s6 = s2 * s2 * s2;
+      du += 4.f * eps * (-12.f * s6 * s6 + 6.f * s6) / rf;
+    }
+    if (p->q[ti] * p->q[tj] != 0.0 && r2f < (float)(p->rc_coul * p->rc_coul)) {
+      float a = (float)p->alpha;
+      float kq = (float)(p->kcoul * p->q[ti] * p->q[tj] * screen(p, fly, i, j, wbar));
+      du += kq * (-erfcf(a * rf) / r2f - 2.f * a / sqrtf((float)M_PI) * expf(-a * a * r2f) / rf);
+    }
+    for (int c = 0; c < 3; ++c) {
+      float f = du * df[c] / rf;
+      F[3 * i + c] += f;
+      F[3 * j + c] -= f;
+    }
+    if (r4 >= rmax) return 0.0;
+    double u, dudr;
+    orc_pair(p, ti, tj, r4, screen(p, fly, i, j, wbar), &u, &dudr);
+    return u;
+  }
+#endif
   if (r4 >= rmax) return 0.0;
   double u, dudr;
   orc_pair(p, orc_atom_type(p, i), orc_atom_type(p, j), r4, screen(p, fly, i, j, wbar), &u, &dudr);

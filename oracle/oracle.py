@@ -23,15 +23,36 @@ MAXT = 4
 SCHED = {"linear": 0, "wv": 1, "wx": 2}
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with the host C compiler (no GPU, no CUDA)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
+_LIB32 = os.path.join(_HERE, "liboracle_fp32.so")
+
+
+def build(force: bool = False, fp32_forces: bool = False) -> str:
+    """Compile the oracle with the host C compiler (no GPU, no CUDA).  fp32_forces builds
+    the tolerance-derivation variant whose dynamics use binary32 pair forces."""
+    out = _LIB32 if fp32_forces else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        defs = ["-DORC_FP32_FORCES"] if fp32_forces else []
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+            ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", *defs, "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
         )
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, out)
+    return out
+
+
+class fp32_forces:
+    """context manager: oracle calls inside use the binary32-pair-force build"""
+
+    def __enter__(self):
+        global _lib, _lib_path
+        self._saved = (_lib, _lib_path)
+        _lib, _lib_path = None, build(fp32_forces=True)
+        return self
+
+    def __exit__(self, *exc):
+        global _lib, _lib_path
+        _lib, _lib_path = self._saved
+        return False
 
 
 class Params(ctypes.Structure):
@@ -128,12 +149,13 @@ def make_proposal(G: int, weights=None, eps: float = 0.1, bf16: bool = True) -> 
     return q
 
 _lib = None
+_lib_path = None
 
 
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
+        _lib = ctypes.CDLL(_lib_path or build())
         d = ctypes.c_double
         pd = ctypes.POINTER(ctypes.c_double)
         pu8 = ctypes.POINTER(ctypes.c_uint8)

@@ -109,18 +109,29 @@ def bf16(a):
 
 
 def forward(flat, X, emulate_bf16=False):
-    """logits [n, 2] of feature rows X [n, 96]; emulate_bf16 rounds features, weights and
-    hidden activations to bfloat16 and each layer's sum to binary32, the precision in which
-    the GPU kernel decides which cell to draw"""
+    """logits [n, 2] of feature rows X [n, 96] and the activations the backward pass needs;
+    emulate_bf16 rounds features, weights and hidden activations to bfloat16 and each
+    layer's sum to binary32, the precision in which the GPU kernel evaluates the network
+    (and so takes its ReLU and cell decisions)"""
     w = unpack(flat)
     r = bf16 if emulate_bf16 else (lambda a: np.asarray(a, np.float64))
     f32 = (lambda a: np.asarray(a, np.float32).astype(np.float64)) if emulate_bf16 else (lambda a: a)
-    z1 = f32(f32(r(X) @ r(w["W1"])) + w["b1"])
-    h1 = np.maximum(z1, 0.0)
-    z2 = f32(f32(r(h1) @ r(w["W2"])) + w["b2"])
-    h2 = np.maximum(z2, 0.0)
-    logits = f32(f32(r(h2) @ r(w["W3"])) + w["b3"])
-    return logits, (X, z1, h1, z2, h2)
+    Xr = r(X)
+    z1 = f32(f32(Xr @ r(w["W1"])) + w["b1"])
+    h1 = r(np.maximum(z1, 0.0))
+    z2 = f32(f32(h1 @ r(w["W2"])) + w["b2"])
+    h2 = r(np.maximum(z2, 0.0))
+    logits = f32(f32(h2 @ r(w["W3"])) + w["b3"])
+    return logits, (Xr, z1, h1, z2, h2, emulate_bf16)
+
+
+def forward_abs(flat, X):
+    """the forward pass on absolute values with every unit active: bounds |logit| and how
+    far operand rounding can move each logit"""
+    w = unpack(flat)
+    a1 = np.abs(X) @ np.abs(w["W1"]) + np.abs(w["b1"])
+    a2 = a1 @ np.abs(w["W2"]) + np.abs(w["b2"])
+    return a2 @ np.abs(w["W3"]) + np.abs(w["b3"])
 
 
 def backward(flat, cache, dlogits, absolute=False):
@@ -128,16 +139,17 @@ def backward(flat, cache, dlogits, absolute=False):
     absolute=True runs the same products on absolute values, which bounds how far rounding
     of the operands can move each gradient element"""
     w = unpack(flat)
-    X, z1, h1, z2, h2 = cache
+    X, z1, h1, z2, h2, emulate = cache
+    r = bf16 if emulate else (lambda v: v)
     a = np.abs if absolute else (lambda v: v)
     g = {}
     g["W3"] = a(h2).T @ a(dlogits)
     g["b3"] = a(dlogits).sum(0)
-    dh2 = a(dlogits) @ a(w["W3"]).T
+    dh2 = a(dlogits) @ a(r(w["W3"])).T
     dz2 = dh2 * (z2 > 0)
     g["W2"] = a(h1).T @ dz2
     g["b2"] = dz2.sum(0)
-    dh1 = dz2 @ a(w["W2"]).T
+    dh1 = dz2 @ a(r(w["W2"])).T
     dz1 = dh1 * (z1 > 0)
     g["W1"] = a(X).T @ dz1
     g["b1"] = dz1.sum(0)
@@ -157,12 +169,12 @@ def bce(logit, t):
     return np.maximum(logit, 0.0) - logit * t + np.log1p(np.exp(-np.abs(logit)))
 
 
-def bce_loss_grad(flat, Xc, Xa, tc, ta, absolute=False):
+def bce_loss_grad(flat, Xc, Xa, tc, ta, absolute=False, emulate_bf16=False):
     """loss = (1/n) sum_records [BCE(cation logit of the cation cell, t_c) +
     BCE(anion logit of the anion cell, t_a)] and its flat gradient"""
     n = len(tc)
-    lc, cc = forward(flat, Xc)
-    la, ca = forward(flat, Xa)
+    lc, cc = forward(flat, Xc, emulate_bf16)
+    la, ca = forward(flat, Xa, emulate_bf16)
     loss = (bce(lc[:, 0], tc).sum() + bce(la[:, 1], ta).sum()) / n
     sig = lambda z: 0.5 * (1.0 + np.tanh(0.5 * z))
     dc = np.zeros_like(lc)
