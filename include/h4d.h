@@ -84,7 +84,9 @@ typedef struct h4d_params {
   int32_t schedule;       /* H4D_SCHED_* */
   double d_oh, d_hh;      /* rigid water bond lengths (O-H, H-H) */
   double skin;            /* Verlet-list skin: rebuilt when the two largest displacements sum to it */
-  double skin_outer;      /* skin of the outer list the Verlet list is filtered from (0 = 4 skin) */
+  double skin_outer;      /* skin of the outer list the Verlet list is filtered from (0 = 4 skin);
+                             a Verlet refresh rebuilds both lists once the two largest
+                             displacements since the outer build exceed skin_outer - skin */
   int32_t max_nbr;        /* neighbour-row capacity per atom; 0 = derived from density */
   int32_t threads_per_atom; /* 1,2,4,8,16 or 32; 0 = autotune per replica size */
 } h4d_params;

@@ -1023,8 +1023,8 @@ __device__ void kick_drift(const Ctx& c, float alpha) {
 }
 
 // after the barrier that follows kick_drift: fold the warp slots (same answer in every
-// thread) and rebuild what is stale -- everything when the outer list is, else only the
-// Verlet rows
+// thread) and, when the Verlet rows are stale, refresh them from the outer rows or, when
+// those cannot cover the Verlet radius any more, rebuild both
 __device__ __forceinline__ void fold_top2(const float* a1, const float* a2, int nw, float& d1, float& d2) {
   d1 = 0.f;
   d2 = 0.f;
@@ -1040,8 +1040,14 @@ __device__ void maybe_rebuild(const Ctx& c) {
   float d1, d2, o1, o2;
   fold_top2(c.v.s->d1w, c.v.s->d2w, c.T >> 5, d1, d2);
   fold_top2(c.v.s->o1w, c.v.s->o2w, c.T >> 5, o1, o2);
-  if (o1 + o2 > c.r.skin_out_fx) build_list(c);
-  else if (d1 + d2 > c.r.skin_fx) refresh_list(c);
+  // The Verlet rows are refreshed from the outer rows, which hold every pair within the
+  // outer radius at the outer build.  A pair now within the Verlet radius was then within
+  // it plus o1 + o2, so the outer rows are complete only while o1 + o2 <= skin_out - skin;
+  // past that the refresh rebuilds everything.
+  if (d1 + d2 > c.r.skin_fx) {
+    if (o1 + o2 > c.r.skin_out_fx - c.r.skin_fx) build_list(c);
+    else refresh_list(c);
+  }
 }
 
 __device__ void scale_velocities(const Ctx& c, float alpha) {

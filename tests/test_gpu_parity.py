@@ -144,6 +144,32 @@ def test_single_trials_match_oracle():
     assert moves == {0, 1}
 
 
+@pytest.mark.parametrize("seed", [6, 8])
+def test_nve_energy_matches_oracle_through_list_refreshes(seed):
+    """30 NVE steps from a state with pairs just inside the cut-offs and fast atoms: the
+    Verlet rows are refreshed from the outer rows several times, and every pair that comes
+    within the cut-off must be in them (a refresh from outer rows that no longer covered
+    the Verlet radius once cost 5.6e-4 kT here)"""
+    cfg = dict(wl.CONFIGS["lj250"])
+    cfg.update(seed=seed, replica=0, tau_t=0.0)
+    L = cfg["L"]
+    po = orc.make_params(cfg, use_cells=0)
+    st = orc.State(po, quantize(wl.lj_positions(cfg["n_pairs"], L, seed), L), None, cfg["n_pairs"], cfg["cap_pairs"])
+    orc.init_velocities(po, st)
+    orc.md(po, st, 200)
+    x0, v0 = quantize(st.positions(), L), st.velocities()
+    ctx = h4d.Context(h4d.make_params(cfg), [dict(L=L, n_pairs=cfg["n_pairs"], cap_pairs=cfg["cap_pairs"], x=x0, v=v0)],
+                      seed=seed)
+    ctx.h4d_run_md(30)
+    Ug, Kg = ctx.h4d_get_energies(0)
+    so = orc.State(po, x0, v0, cfg["n_pairs"], cfg["cap_pairs"])
+    orc.nve(po, so, 30)
+    Eo = orc.energy_forces(po, so.positions())[0] + orc.kinetic(po, so.velocities())
+    builds = ctx.h4d_get_counts(0)["nbr_builds"]
+    print(f"seed {seed}: E gpu - oracle after 30 NVE steps {(Ug + Kg) - Eo:+.2e} ({builds} list builds)")
+    assert abs((Ug + Kg) - Eo) < 1e-4
+
+
 def test_energy_getter_matches_oracle():
     cfg, x0, v0 = _equilibrated_c0(seed=2, steps=50)
     L = cfg["L"]
