@@ -129,12 +129,17 @@ typedef struct h4d_record {
   int32_t n_before, n_after;
   int32_t status;     /* 0 ok, 1 deletion from empty system, 2 capacity, 3 non-finite work */
   int32_t cation, anion; /* chosen pair index (deletion), else -1 */
+  int32_t cell_c, cell_a; /* proposal-grid cells of the exchanged cation and anion, or -1
+                             when no proposal grid is enabled */
   int32_t pad;
   double dH;          /* H_end - H_start (energy units, FP64) */
   double beta_dM;     /* beta Delta M */
   double w_prot;      /* protocol work sum_k [U(w_{k+1}) - U(w_k)] (FP32 pairs, FP64 sum) */
   double ln_u;        /* log of the acceptance uniform */
-  double x_acc;       /* exponent compared with ln_u */
+  double x_acc;       /* exponent compared with ln_u (includes the proposal factor) */
+  double ln_q;        /* log proposal factor ln(q_c G^3) + ln(q_a G^3) of the learned
+                         proposal (subtracted for an insertion, added for a deletion; 0
+                         with uniform placement) */
 } h4d_record;
 
 /* ---- context lifetime ---- */
@@ -189,6 +194,66 @@ int32_t h4d_num_replicas(h4d_ctx* ctx);
 /* total pairs inside the larger cut-off over all replicas at the current state (each
  * unordered pair once); the algorithmic work unit of the pair kernel */
 int h4d_count_pairs(h4d_ctx* ctx, int64_t* n_pairs_in_cutoff);
+
+/* ---- learned insertion-site proposal ----
+ * A proposal density over a grid of G^3 cells per replica (G = max(3, floor(L/cell_len)),
+ * at most 32) replaces the uniform placement of an inserted ion (Eq. 4).  Each cell has 96
+ * features: for the cation, the anion and the water O, 0.25 x the atom count of each of
+ * the 27 cells of its 3x3x3 neighbourhood (81); 0.1 x the field sum_j q_j d_j /
+ * max(|d_j|, 0.5)^3 at the cell centre from the charges of those cells (3); zeros (12).
+ * An MLP 96-64-64-2 (ReLU; BF16 operands, FP32 accumulation on the tensor cores) gives a
+ * cation and an anion logit per cell; species s draws its cell from
+ * q_s = (1 - eps) softmax(logit_s) + eps / G^3 and is placed uniformly inside it.  The
+ * density ratio to uniform placement enters the acceptance exponent as the bias factors
+ * B^ins / B^del do in Eqs. 15-16, so detailed balance holds for any weights: an insertion
+ * subtracts ln(q_c G^3) + ln(q_a G^3) evaluated on the start state, a deletion adds it
+ * evaluated on the end state with the flyers removed (record field ln_q).
+ * Random draws: block 5 of the trial (counter {trial, 5, 1, 0}): words 0 and 1 choose the
+ * uniform component (u < eps) for the cation and the anion, words 2 and 3 the cell; the
+ * 32-bit position draws of blocks 1-2 place the ion inside the cell.
+ * Flat weight layout (row index = input unit, doubles on the host, FP32 masters on the
+ * device): W1[96][64], b1[64], W2[64][64], b2[64], W3[64][2], b3[2]. */
+#define H4D_PROPOSAL_UNIFORM 0
+#define H4D_PROPOSAL_LEARNED 1
+#define H4D_PROP_NFEAT 96
+#define H4D_PROP_NW (96 * 64 + 64 + 64 * 64 + 64 + 64 * 2 + 2) /* 10498 */
+
+/* Enable the proposal grid on every replica.  mode UNIFORM keeps uniform placement (for
+ * collecting training records), LEARNED draws cells from q (weights start at zero, i.e.
+ * uniform, until set or trained).  eps in (0, 1].  records_per_replica > 0 allocates a
+ * ring of training records per replica: every trial with status 0 or 3 stores the
+ * features of the cation's and the anion's cell in the N-pair state of the move (start
+ * state of an insertion, end state of a deletion) and the insertion-direction exponent y
+ * (x_acc of an insertion, -x_acc of a deletion, both without the proposal factor).
+ * Calling it again re-sizes the grid and empties the rings; the network is kept.
+ * Allocates device memory; synchronises the stream. */
+int h4d_proposal(h4d_ctx* ctx, int32_t mode, double cell_len, double eps, int32_t records_per_replica);
+/* set / read the H4D_PROP_NW weights; setting resets the optimiser state */
+int h4d_proposal_set_weights(h4d_ctx* ctx, const double* host_w, int64_t n);
+int h4d_proposal_get_weights(h4d_ctx* ctx, double* host_w, int64_t n);
+/* the most recent training records of a replica, oldest first: host_feat [n][2][96]
+ * (cation cell, anion cell), host_y [n], host_move [n], host_status [n]; any output may be
+ * NULL */
+int h4d_proposal_records(h4d_ctx* ctx, int32_t replica, float* host_feat, double* host_y,
+                         int32_t* host_move, int32_t* host_status, int64_t cap, int64_t* n);
+/* logits [G^3][2] (and features [G^3][96] when host_feat is not NULL) of every cell of a
+ * replica's current state; H4D_ECAPACITY when cap_cells < G^3 */
+int h4d_proposal_logits(h4d_ctx* ctx, int32_t replica, float* host_logits, float* host_feat,
+                        int64_t cap_cells, int64_t* n_cells);
+/* steps of Adam (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the recorded
+ * trials of all replicas (status 0, finite y).  Loss of n records: (1/n) sum [BCE(cation
+ * logit of the cation cell, t) + BCE(anion logit of the anion cell, t)] with
+ * t = min(1, exp(y - y0)).  Each step draws batch records uniformly (Philox counter
+ * {step, k/4, 5, 0}, key {seed, 2^63}); batch >= the number of valid records uses all of
+ * them in ring order.  *host_loss receives the loss of the last step.  Synchronises. */
+int h4d_train_proposal(h4d_ctx* ctx, int64_t steps, int32_t batch, double lr, double y0, uint64_t seed,
+                       double* host_loss);
+/* stateless: loss (as above) and its gradient [H4D_PROP_NW] for weights host_w on
+ * n_rec records host_feat [n][2][96] with targets host_t [n][2] (cation row, anion row),
+ * computed by the same BF16 forward and backward kernels as training.  Allocates device
+ * scratch per call; synchronises the default stream. */
+int h4d_proposal_grad(const double* host_w, int64_t n_rec, const float* host_feat, const float* host_t,
+                      double* loss, double* host_grad);
 
 /* ---- checkpoint ---- */
 int h4d_save(h4d_ctx* ctx, const char* path);

@@ -19,6 +19,120 @@
 
 using namespace h4d;
 
+// device buffers of the proposal network and its training (one set per context, or a
+// temporary set for the stateless gradient entry point)
+struct PropDev {
+  float* w = nullptr;      // [kPropNW] FP32 masters
+  float* m = nullptr;      // Adam first moments
+  float* v = nullptr;      // Adam second moments
+  float* grad = nullptr;   // [kPropNW]
+  uint2* w1 = nullptr;
+  uint2* w2 = nullptr;
+  uint2* w3 = nullptr;
+  uint2* w2t = nullptr;
+  float* w3r = nullptr;
+  float* b = nullptr;
+  long long adam_t = 0;
+  // grid
+  int cells = 0;
+  int4* cnt = nullptr;
+  long long* fld = nullptr;
+  float2* logit = nullptr;
+  double2* chunk = nullptr;
+  // records
+  int n_rec = 0;
+  float* rfeat = nullptr;
+  double* ry = nullptr;
+  int2* rmeta = nullptr;
+  // training scratch for up to cap_rows rows
+  int cap_rows = 0;
+  int* valid = nullptr;
+  int* n_valid = nullptr;
+  float* bfeat = nullptr;
+  float* btgt = nullptr;
+  uint16_t *xT = nullptr, *h1T = nullptr, *dz1T = nullptr, *h2T = nullptr, *dz2T = nullptr, *dlT = nullptr;
+  float* loss_rows = nullptr;
+  double* loss = nullptr;
+  float* fout = nullptr;  // [cells][96] feature dump of h4d_proposal_logits
+};
+
+static void prop_free_train(PropDev* P) {
+  void* ptrs[] = {P->bfeat, P->btgt, P->xT, P->h1T, P->dz1T, P->h2T, P->dz2T, P->dlT, P->loss_rows};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  P->bfeat = P->btgt = nullptr;
+  P->xT = P->h1T = P->dz1T = P->h2T = P->dz2T = P->dlT = nullptr;
+  P->loss_rows = nullptr;
+  P->cap_rows = 0;
+}
+
+static void prop_free(PropDev* P) {
+  if (!P) return;
+  prop_free_train(P);
+  void* ptrs[] = {P->w, P->m, P->v, P->grad, P->w1, P->w2, P->w3, P->w2t, P->w3r, P->b, P->cnt, P->fld,
+                  P->logit, P->chunk, P->rfeat, P->ry, P->rmeta, P->valid, P->n_valid, P->loss, P->fout};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete P;
+}
+
+#define CKP(x)                                 \
+  do {                                         \
+    if ((x) != cudaSuccess) return H4D_ECUDA; \
+  } while (0)
+
+static int prop_alloc_net(PropDev* P) {
+  CKP(cudaMalloc(&P->w, kPropNW * sizeof(float)));
+  CKP(cudaMalloc(&P->m, kPropNW * sizeof(float)));
+  CKP(cudaMalloc(&P->v, kPropNW * sizeof(float)));
+  CKP(cudaMalloc(&P->grad, kPropNW * sizeof(float)));
+  CKP(cudaMalloc(&P->w1, 1536 * sizeof(uint2)));
+  CKP(cudaMalloc(&P->w2, 1024 * sizeof(uint2)));
+  CKP(cudaMalloc(&P->w3, 128 * sizeof(uint2)));
+  CKP(cudaMalloc(&P->w2t, 1024 * sizeof(uint2)));
+  CKP(cudaMalloc(&P->w3r, 128 * sizeof(float)));
+  CKP(cudaMalloc(&P->b, 130 * sizeof(float)));
+  CKP(cudaMalloc(&P->loss, sizeof(double)));
+  CKP(cudaMemset(P->w, 0, kPropNW * sizeof(float)));
+  CKP(cudaMemset(P->m, 0, kPropNW * sizeof(float)));
+  CKP(cudaMemset(P->v, 0, kPropNW * sizeof(float)));
+  return H4D_OK;
+}
+
+// training scratch for `rows` rows (a multiple of 16)
+static int prop_ensure_rows(PropDev* P, int rows) {
+  if (rows <= P->cap_rows) return H4D_OK;
+  prop_free_train(P);
+  const size_t r = (size_t)rows;
+  CKP(cudaMalloc(&P->bfeat, r * 96 * sizeof(float)));
+  CKP(cudaMalloc(&P->btgt, r * sizeof(float)));
+  CKP(cudaMalloc(&P->xT, 96 * r * sizeof(uint16_t)));
+  CKP(cudaMalloc(&P->h1T, 64 * r * sizeof(uint16_t)));
+  CKP(cudaMalloc(&P->dz1T, 64 * r * sizeof(uint16_t)));
+  CKP(cudaMalloc(&P->h2T, 64 * r * sizeof(uint16_t)));
+  CKP(cudaMalloc(&P->dz2T, 64 * r * sizeof(uint16_t)));
+  CKP(cudaMalloc(&P->dlT, 8 * r * sizeof(uint16_t)));
+  CKP(cudaMalloc(&P->loss_rows, r * sizeof(float)));
+  CKP(cudaMemset(P->dlT, 0, 8 * r * sizeof(uint16_t)));  // rows 2..7 of dl stay zero
+  P->cap_rows = rows;
+  return H4D_OK;
+}
+
+static PropNet prop_net(const PropDev* P) {
+  PropNet n;
+  n.w1 = P->w1; n.w2 = P->w2; n.w3 = P->w3; n.w2t = P->w2t; n.w3r = P->w3r; n.b = P->b;
+  return n;
+}
+
+// loss and gradient of n records already in P->bfeat / P->btgt (rows_pad rows)
+static int prop_loss_grad(PropDev* P, int n, int rows_pad, cudaStream_t s) {
+  int rc = launch_prop_fwd_bwd(prop_net(P), P->bfeat, P->btgt, n, 1.0f / (float)n, P->xT, P->h1T, P->dz1T, P->h2T,
+                               P->dz2T, P->dlT, P->loss_rows, rows_pad, s);
+  if (rc) return rc;
+  return launch_prop_wgrad(P->xT, P->h1T, P->dz1T, P->h2T, P->dz2T, P->dlT, P->loss_rows, rows_pad, P->grad,
+                           P->loss, s);
+}
+
 struct h4d_ctx {
   h4d_params prm;
   uint64_t seed;
@@ -58,6 +172,9 @@ struct h4d_ctx {
   h4d_record* d_rec = nullptr;
   double* d_scratch = nullptr;
   unsigned long long* d_count = nullptr;
+  // learned proposal: network (FP32 masters, Adam moments, packed bf16 fragments), grid,
+  // training records and training scratch
+  PropDev* prop = nullptr;
 };
 
 #define CK(x)                                  \
@@ -149,6 +266,7 @@ static void fill_pot(const h4d_params& p, Pot& P, Proto& pr) {
   }
   P.d_oh2 = p.d_oh * p.d_oh;
   P.d_hh2 = p.d_hh * p.d_hh;
+  for (int t = 0; t < 4; ++t) P.q[t] = (t < p.ntypes) ? (float)p.q[t] : 0.f;
   std::memset(&pr, 0, sizeof(pr));
   pr.n_f = p.n_f;
   pr.schedule = p.schedule;
@@ -589,6 +707,7 @@ void h4d_destroy(h4d_ctx* c) {
                   c->d_scratch, c->d_count, c->d_nbr_out, c->d_ncnt_out, c->d_ref_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  prop_free(c->prop);
   invalidate_graphs(c);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -613,9 +732,12 @@ int h4d_set_protocol(h4d_ctx* c, int32_t n_f, double w_max, double dt, double ka
   int rc = pull_reps(c);
   if (rc) return rc;
   for (auto& r : c->rep_h) r.c_drift = (float)(dt * kTwo32 / r.L);
-  const int no_acc = c->eng.proto.no_accept;
+  const Proto keep = c->eng.proto;
   fill_pot(c->prm, c->eng.pot, c->eng.proto);
-  c->eng.proto.no_accept = no_acc;
+  c->eng.proto.no_accept = keep.no_accept;
+  c->eng.proto.prop_mode = keep.prop_mode;
+  c->eng.proto.prop_record = keep.prop_record;
+  c->eng.proto.prop_eps = keep.prop_eps;
   invalidate_graphs(c);
   return push_plan(c);
 }
@@ -834,7 +956,7 @@ int h4d_count_pairs(h4d_ctx* c, int64_t* n) {
 }
 
 // ---- checkpoint: a flat binary image of the replica table and per-atom state ----
-static const uint64_t kMagic = 0x3130303044344848ULL;  // "HH4D0001"
+static const uint64_t kMagic = 0x3230303044344848ULL;  // "HH4D0002"
 
 int h4d_save(h4d_ctx* c, const char* path) {
   if (!c || !path) return H4D_EINVAL;
@@ -883,8 +1005,15 @@ int h4d_load(h4d_ctx* c, const char* path) {
   ok = ok && std::fread(rec.data(), sizeof(h4d_record), nrec, f) == nrec;
   std::fclose(f);
   if (!ok) return H4D_EINVAL;
-  for (int r = 0; r < c->R; ++r)
+  for (int r = 0; r < c->R; ++r) {
     if (reps[r].atom_off != c->rep_h[r].atom_off || reps[r].cap_atoms != c->rep_h[r].cap_atoms) return H4D_EINVAL;
+    // the proposal grid and record rings belong to this context, not to the checkpoint
+    reps[r].prop_G = c->rep_h[r].prop_G;
+    reps[r].prop_off = c->rep_h[r].prop_off;
+    reps[r].prec_off = c->rep_h[r].prec_off;
+    reps[r].prec_cap = c->rep_h[r].prec_cap;
+    reps[r].prec_count = c->rep_h[r].prec_count;
+  }
   c->seed = hdr[3];
   c->eng.seed = hdr[3];
   c->rep_h = reps;
@@ -1214,3 +1343,259 @@ extern "C" int h4d_eval_forces_static(const h4d_params* params, double L, int32_
   if (U) *U = u;
   return H4D_OK;
 }
+
+// ------------------------------------------------------------------------------------
+// Learned insertion-site proposal
+// ------------------------------------------------------------------------------------
+static void prop_bind(h4d_ctx* c) {
+  Eng& e = c->eng;
+  PropDev* P = c->prop;
+  e.net = prop_net(P);
+  e.pg_cnt = P->cnt;
+  e.pg_fld = P->fld;
+  e.pg_logit = P->logit;
+  e.pg_chunk = P->chunk;
+  e.prec_feat = P->rfeat;
+  e.prec_y = P->ry;
+  e.prec_meta = P->rmeta;
+}
+
+static int prop_pack(PropDev* P, cudaStream_t s) {
+  return launch_prop_pack(P->w, P->w1, P->w2, P->w3, P->w2t, P->w3r, P->b, s);
+}
+
+extern "C" {
+
+int h4d_proposal(h4d_ctx* c, int32_t mode, double cell_len, double eps, int32_t records_per_replica) {
+  if (!c || (mode != H4D_PROPOSAL_UNIFORM && mode != H4D_PROPOSAL_LEARNED) || !(cell_len > 0) || !(eps > 0) ||
+      !(eps <= 1) || records_per_replica < 0 || records_per_replica > (1 << 20))
+    return H4D_EINVAL;
+  int rc = pull_reps(c);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  if (!c->prop) {
+    c->prop = new (std::nothrow) PropDev();
+    if (!c->prop) return H4D_ECUDA;
+    rc = prop_alloc_net(c->prop);
+    if (rc) return rc;
+    rc = prop_pack(c->prop, c->stream);
+    if (rc) return rc;
+  }
+  PropDev* P = c->prop;
+  // grid: G = max(3, floor(L / cell_len)) per replica, capped at kPropMaxG
+  int cells = 0;
+  for (auto& R : c->rep_h) {
+    int G = (int)std::floor(R.L / cell_len);
+    G = std::max(3, std::min(kPropMaxG, G));
+    R.prop_G = G;
+    R.prop_off = cells;
+    cells += ((G * G * G + 31) / 32) * 32;
+  }
+  if (cells > P->cells) {
+    void* old[] = {P->cnt, P->fld, P->logit, P->chunk, P->fout};
+    for (void* q : old)
+      if (q) cudaFree(q);
+    P->cnt = nullptr; P->fld = nullptr; P->logit = nullptr; P->chunk = nullptr; P->fout = nullptr;
+    CK(cudaMalloc(&P->cnt, (size_t)cells * sizeof(int4)));
+    CK(cudaMalloc(&P->fld, (size_t)cells * 4 * sizeof(long long)));
+    CK(cudaMalloc(&P->logit, (size_t)cells * sizeof(float2)));
+    CK(cudaMalloc(&P->chunk, (size_t)(cells / 32) * sizeof(double2)));
+    P->cells = cells;
+  }
+  // training-record rings
+  const int n_rec = c->R * records_per_replica;
+  if (n_rec != P->n_rec) {
+    void* old[] = {P->rfeat, P->ry, P->rmeta, P->valid, P->n_valid};
+    for (void* q : old)
+      if (q) cudaFree(q);
+    P->rfeat = nullptr; P->ry = nullptr; P->rmeta = nullptr; P->valid = nullptr; P->n_valid = nullptr;
+    if (n_rec > 0) {
+      CK(cudaMalloc(&P->rfeat, (size_t)n_rec * 192 * sizeof(float)));
+      CK(cudaMalloc(&P->ry, (size_t)n_rec * sizeof(double)));
+      CK(cudaMalloc(&P->rmeta, (size_t)n_rec * sizeof(int2)));
+      CK(cudaMalloc(&P->valid, (size_t)n_rec * sizeof(int)));
+      CK(cudaMalloc(&P->n_valid, sizeof(int)));
+    }
+    P->n_rec = n_rec;
+  }
+  if (n_rec > 0) CK(cudaMemsetAsync(P->rmeta, 0xff, (size_t)n_rec * sizeof(int2), c->stream));  // empty slots
+  for (int r = 0; r < c->R; ++r) {
+    Rep& R = c->rep_h[r];
+    R.prec_off = r * records_per_replica;
+    R.prec_cap = records_per_replica;
+    R.prec_count = 0;
+  }
+  c->eng.proto.prop_mode = mode;
+  c->eng.proto.prop_record = records_per_replica > 0 ? 1 : 0;
+  c->eng.proto.prop_eps = eps;
+  prop_bind(c);
+  invalidate_graphs(c);
+  rc = push_plan(c);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return H4D_OK;
+}
+
+int h4d_proposal_set_weights(h4d_ctx* c, const double* w, int64_t n) {
+  if (!c || !c->prop || !w || n != kPropNW) return H4D_EINVAL;
+  std::vector<float> f(kPropNW);
+  for (int i = 0; i < kPropNW; ++i) {
+    if (!std::isfinite(w[i])) return H4D_EINVAL;
+    f[i] = (float)w[i];
+  }
+  PropDev* P = c->prop;
+  CK(cudaMemcpyAsync(P->w, f.data(), kPropNW * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(P->m, 0, kPropNW * sizeof(float), c->stream));
+  CK(cudaMemsetAsync(P->v, 0, kPropNW * sizeof(float), c->stream));
+  P->adam_t = 0;
+  int rc = prop_pack(P, c->stream);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return H4D_OK;
+}
+
+int h4d_proposal_get_weights(h4d_ctx* c, double* w, int64_t n) {
+  if (!c || !c->prop || !w || n != kPropNW) return H4D_EINVAL;
+  std::vector<float> f(kPropNW);
+  CK(cudaMemcpyAsync(f.data(), c->prop->w, kPropNW * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < kPropNW; ++i) w[i] = (double)f[i];
+  return H4D_OK;
+}
+
+int h4d_proposal_records(h4d_ctx* c, int32_t r, float* feat, double* y, int32_t* move, int32_t* status, int64_t cap,
+                         int64_t* n) {
+  if (!c || !c->prop || r < 0 || r >= c->R || cap < 0) return H4D_EINVAL;
+  int rc = pull_reps(c);
+  if (rc) return rc;
+  const Rep& R = c->rep_h[r];
+  PropDev* P = c->prop;
+  const int64_t have = std::min<int64_t>(R.prec_count, R.prec_cap);
+  const int64_t take = std::min<int64_t>(have, cap);
+  if (n) *n = take;
+  if (take == 0) return H4D_OK;
+  std::vector<float> fb((size_t)R.prec_cap * 192);
+  std::vector<double> yb(R.prec_cap);
+  std::vector<int2> mb(R.prec_cap);
+  CK(cudaMemcpyAsync(fb.data(), P->rfeat + (size_t)R.prec_off * 192, fb.size() * sizeof(float),
+                     cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(yb.data(), P->ry + R.prec_off, yb.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(mb.data(), P->rmeta + R.prec_off, mb.size() * sizeof(int2), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int64_t k = 0; k < take; ++k) {
+    const int64_t idx = (R.prec_count - take + k) % R.prec_cap;
+    if (feat) std::memcpy(feat + k * 192, fb.data() + idx * 192, 192 * sizeof(float));
+    if (y) y[k] = yb[idx];
+    if (move) move[k] = mb[idx].x;
+    if (status) status[k] = mb[idx].y;
+  }
+  return H4D_OK;
+}
+
+int h4d_proposal_logits(h4d_ctx* c, int32_t r, float* logits, float* feat, int64_t cap_cells, int64_t* n_cells) {
+  if (!c || !c->prop || r < 0 || r >= c->R) return H4D_EINVAL;
+  int rc = pull_reps(c);
+  if (rc) return rc;
+  const Rep& R = c->rep_h[r];
+  const int nc = R.prop_G * R.prop_G * R.prop_G;
+  if (n_cells) *n_cells = nc;
+  if (nc == 0) return H4D_EINVAL;
+  if (nc > cap_cells) return H4D_ECAPACITY;
+  PropDev* P = c->prop;
+  float* fo = nullptr;
+  if (feat) {
+    if (P->fout) cudaFree(P->fout);
+    P->fout = nullptr;
+    CK(cudaMalloc(&P->fout, (size_t)nc * kPropNFeat * sizeof(float)));
+    fo = P->fout;
+  }
+  rc = launch_prop_eval(c->eng, c->n_ctas, c->cta_threads, c->smem, r, fo, c->stream);
+  if (rc) return rc;
+  std::vector<float2> lg(nc);
+  CK(cudaMemcpyAsync(lg.data(), P->logit + R.prop_off, nc * sizeof(float2), cudaMemcpyDeviceToHost, c->stream));
+  if (feat) CK(cudaMemcpyAsync(feat, fo, (size_t)nc * kPropNFeat * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (logits)
+    for (int i = 0; i < nc; ++i) {
+      logits[2 * i] = lg[i].x;
+      logits[2 * i + 1] = lg[i].y;
+    }
+  return H4D_OK;
+}
+
+int h4d_train_proposal(h4d_ctx* c, int64_t steps, int32_t batch, double lr, double y0, uint64_t seed,
+                       double* loss_out) {
+  if (!c || !c->prop || steps < 0 || batch < 1 || batch > (1 << 22) || !(lr >= 0) || !std::isfinite(y0))
+    return H4D_EINVAL;
+  PropDev* P = c->prop;
+  if (P->n_rec == 0) return H4D_EINVAL;
+  int rc = launch_prop_compact(P->rmeta, P->ry, P->n_rec, P->valid, P->n_valid, c->stream);
+  if (rc) return rc;
+  int n_valid = 0;
+  CK(cudaMemcpyAsync(&n_valid, P->n_valid, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (n_valid == 0) return H4D_EINVAL;
+  const int nb = std::min(batch, n_valid);
+  const int rows_pad = ((2 * nb + 15) / 16) * 16;
+  rc = prop_ensure_rows(P, rows_pad);
+  if (rc) return rc;
+  for (int64_t s = 0; s < steps; ++s) {
+    rc = launch_prop_gather(P->rfeat, P->ry, P->valid, n_valid, nb, seed, (long long)P->adam_t, (float)y0, P->bfeat,
+                            P->btgt, c->stream);
+    if (rc) return rc;
+    rc = prop_loss_grad(P, nb, rows_pad, c->stream);
+    if (rc) return rc;
+    P->adam_t++;
+    rc = launch_prop_adam(P->w, P->m, P->v, P->grad, (int)std::min<long long>(P->adam_t, 1 << 30), (float)lr,
+                          c->stream);
+    if (rc) return rc;
+    rc = prop_pack(P, c->stream);
+    if (rc) return rc;
+  }
+  if (loss_out) {
+    double l = 0.0;
+    if (steps > 0) {
+      CK(cudaMemcpyAsync(&l, P->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+    }
+    *loss_out = l / nb;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return H4D_OK;
+}
+
+int h4d_proposal_grad(const double* w, int64_t n_rec, const float* feat, const float* tgt, double* loss,
+                      double* grad) {
+  if (!w || !feat || !tgt || n_rec < 1 || n_rec > (1 << 22)) return H4D_EINVAL;
+  int rc = check_device();
+  if (rc) return rc;
+  PropDev* P = new (std::nothrow) PropDev();
+  if (!P) return H4D_ECUDA;
+  cudaStream_t s = 0;
+  const int n = (int)n_rec;
+  const int rows_pad = ((2 * n + 15) / 16) * 16;
+  std::vector<float> f(kPropNW);
+  for (int i = 0; i < kPropNW; ++i) f[i] = (float)w[i];
+  rc = prop_alloc_net(P);
+  if (!rc) rc = prop_ensure_rows(P, rows_pad);
+  if (!rc && cudaMemcpy(P->w, f.data(), kPropNW * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) rc = H4D_ECUDA;
+  if (!rc && cudaMemcpy(P->bfeat, feat, (size_t)n * 192 * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = H4D_ECUDA;
+  if (!rc && cudaMemcpy(P->btgt, tgt, (size_t)n * 2 * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = H4D_ECUDA;
+  if (!rc) rc = prop_pack(P, s);
+  if (!rc) rc = prop_loss_grad(P, n, rows_pad, s);
+  double l = 0.0;
+  if (!rc && cudaMemcpy(&l, P->loss, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) rc = H4D_ECUDA;
+  if (!rc && cudaMemcpy(f.data(), P->grad, kPropNW * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = H4D_ECUDA;
+  if (!rc) {
+    if (loss) *loss = l / n;
+    if (grad)
+      for (int i = 0; i < kPropNW; ++i) grad[i] = (double)f[i];
+  }
+  prop_free(P);
+  return rc;
+}
+
+}  // extern "C"

@@ -12,6 +12,8 @@
 #include <cstdint>
 
 #include "h4d_engine.cuh"
+#include "h4d_philox.cuh"
+#include "h4d_prop.cuh"
 
 // Engine launch bounds: threads per CTA and CTAs per SM the register allocation targets
 #ifndef H4D_MAXTHREADS
@@ -22,40 +24,6 @@
 #endif
 
 namespace h4d {
-
-typedef unsigned long long u64;
-
-// ------------------------------------------------------------------------------------
-// Philox4x64-10 (Salmon et al., SC'11).  Counter {c0, c1, purpose, 0}, key {seed, replica}.
-// ------------------------------------------------------------------------------------
-enum : u64 { kPurTrial = 1, kPurGamma = 2, kPurThermo = 3, kPurVinit = 4 };
-
-__device__ __forceinline__ void philox4x64(u64 c[4], u64 k0, u64 k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const u64 m0 = 0xD2E7470EE14C6C93ULL, m1 = 0xCA5A826395121157ULL;
-    u64 lo0 = m0 * c[0], hi0 = __umul64hi(m0, c[0]);
-    u64 lo1 = m1 * c[2], hi1 = __umul64hi(m1, c[2]);
-    u64 n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
-    k0 += 0x9E3779B97F4A7C15ULL;
-    k1 += 0xBB67AE8584CAA73BULL;
-  }
-}
-
-__device__ __forceinline__ void draw4(u64 seed, u64 rep, u64 c0, u64 c1, u64 pur, u64 out[4]) {
-  out[0] = c0; out[1] = c1; out[2] = pur; out[3] = 0;
-  philox4x64(out, seed, rep);
-}
-__device__ __forceinline__ double u01(u64 r) { return (double)(r >> 11) * 0x1.0p-53; }
-__device__ __forceinline__ double u01_open(u64 r) { return (double)((r >> 11) + 1) * 0x1.0p-53; }
-__device__ __forceinline__ int pick_index(u64 r, int n) { return (int)(((r >> 32) * (u64)n) >> 32); }
-__device__ __forceinline__ double gauss_c(u64 a, u64 b) {
-  return sqrt(-2.0 * log(u01_open(a))) * cos(2.0 * 3.141592653589793 * u01(b));
-}
-__device__ __forceinline__ double gauss_s(u64 a, u64 b) {
-  return sqrt(-2.0 * log(u01_open(a))) * sin(2.0 * 3.141592653589793 * u01(b));
-}
 
 // ------------------------------------------------------------------------------------
 // small helpers
@@ -213,7 +181,15 @@ struct GScal {
   float d1w[32], d2w[32];  // per-warp largest and second-largest displacement since the build
   float o1w[32], o2w[32];  // the same since the outer-list build
   int next_item, n_items;  // dynamic work items of the outer build
+  // learned proposal of the current trial
+  float pm[2];             // largest cation / anion logit
+  float pmw[2][32];        // per-warp maxima
+  double pZ[2];            // softmax normalisers sum_k exp(l_k - max)
+  double lnq;              // log proposal factor of the trial
+  int cell_c, cell_a;      // grid cells of the exchanged cation and anion
+  int prec_slot, pad_p;    // training-record slot of the trial (-1 = none)
 };
+static_assert(sizeof(GScal) <= 1536, "per-group scalars exceed their shared-memory slot");
 
 struct GView {
   uint4* pos;
@@ -1255,6 +1231,243 @@ __device__ void md_phase(const Ctx& c, int n_steps) {
 //    a rejection restores the state saved after the first reversal;
 //  - Delta H = H_{N+1}(end, all in 3D) - H_N(start, flyers absent) for insertion and the
 //    reverse for deletion, flyers' kinetic energy left out (it cancels against Eqs. 3-4).
+
+// ------------------------------------------------------------------------------------
+// Learned insertion-site proposal (grid features, BF16 MLP, softmax, cell draw).
+// Cells: G per edge, cell (gx*G + gy)*G + gz with gx = floor(X G / 2^32) of the 32-bit
+// coordinate.  Features of a cell: 0.25 x the cation, anion and water-O counts of the 27
+// cells of its 3x3x3 neighbourhood (slot (ex+1)*9 + (ey+1)*3 + (ez+1) for offset e), then
+// 0.1 sum_j q_j d_j / max(|d_j|, 0.5)^3 over the charges of those cells, d_j the minimum
+// image of (cell centre - x_j), then zeros up to 96.  The proposal of species s draws a
+// cell from q_s = (1 - eps) softmax(logit_s) + eps / G^3 and places the ion uniformly
+// inside it; the density ratio to uniform placement, q_s G^3 per ion, enters the
+// acceptance exponent (the role of B^ins / B^del in Eqs. 15-16): insertion uses q of the
+// start state, deletion q of the end state without the flyers.
+// ------------------------------------------------------------------------------------
+struct PropView {
+  int G, nc;
+  int4* cnt;
+  long long* fld;
+  float2* logit;
+  double2* chunk;
+};
+
+__device__ __forceinline__ PropView prop_view(const Eng& e, const Rep& R) {
+  PropView v;
+  v.G = R.prop_G;
+  v.nc = R.prop_G * R.prop_G * R.prop_G;
+  v.cnt = e.pg_cnt + R.prop_off;
+  v.fld = e.pg_fld + 4 * (size_t)R.prop_off;
+  v.logit = e.pg_logit + R.prop_off;
+  v.chunk = e.pg_chunk + R.prop_off / 32;
+  return v;
+}
+
+__device__ __forceinline__ int prop_cell_of(unsigned X, unsigned Y, unsigned Z, int G) {
+  return ((int)__umulhi(X, (unsigned)G) * G + (int)__umulhi(Y, (unsigned)G)) * G + (int)__umulhi(Z, (unsigned)G);
+}
+
+__device__ __forceinline__ int wrap_g(int x, int G) { return x < 0 ? x + G : (x >= G ? x - G : x); }
+
+// cell at neighbour slot n of cell c
+__device__ __forceinline__ int prop_nb(int c, int n, int G) {
+  const int gx = c / (G * G), gy = (c / G) % G, gz = c % G;
+  return (wrap_g(gx + n / 9 - 1, G) * G + wrap_g(gy + (n / 3) % 3 - 1, G)) * G + wrap_g(gz + n % 3 - 1, G);
+}
+
+// feature k of cell c (grid counts and field must be complete).  The grid is written with
+// atomics in L2, so it is read past L1.
+__device__ __forceinline__ float prop_feature(const PropView& pv, int c, int k) {
+  if (k < 81) {
+    const int s = k / 27;
+    const int4 q = __ldcg(pv.cnt + prop_nb(c, k - 27 * s, pv.G));
+    return 0.25f * (float)(s == 0 ? q.x : (s == 1 ? q.y : q.z));
+  }
+  if (k < 84) return (float)((double)__ldcg(pv.fld + 4 * (size_t)c + (k - 81)) * 0x1.0p-40);
+  return 0.f;
+}
+
+// coordinate of the centre of cell coordinate g (rounded down to the 32-bit grid)
+__device__ __forceinline__ unsigned prop_centre(int g, int G) {
+  return (unsigned)((((u64)(2 * g + 1)) << 31) / (u64)G);
+}
+
+// counts and field of the atoms [0, n_tot) other than ex0, ex1; integer atomics (the
+// field in fixed point), so the sums do not depend on the order of the additions
+__device__ void prop_grid(const Ctx& c, const PropView& pv, int ex0, int ex1) {
+  const Eng& e = *c.e;
+  for (int i = c.tid; i < pv.nc; i += c.T) {
+    pv.cnt[i] = make_int4(0, 0, 0, 0);
+    reinterpret_cast<longlong2*>(pv.fld)[2 * i] = make_longlong2(0, 0);
+    reinterpret_cast<longlong2*>(pv.fld)[2 * i + 1] = make_longlong2(0, 0);
+  }
+  c.sync();
+  const int n = c.v.s->n_tot, G = pv.G;
+  for (int a = c.tid; a < n; a += c.T) {
+    if (a == ex0 || a == ex1) continue;
+    const uint4 p = c.v.pos[a];
+    const int ty = type_of(a, c.r.nw3);
+    const int gx = (int)__umulhi(p.x, (unsigned)G), gy = (int)__umulhi(p.y, (unsigned)G),
+              gz = (int)__umulhi(p.z, (unsigned)G);
+    if (ty <= 2) atomicAdd(reinterpret_cast<int*>(pv.cnt + (gx * G + gy) * G + gz) + ty, 1);
+    const float q = e.pot.q[ty];
+    if (q == 0.f) continue;
+    for (int d = 0; d < 27; ++d) {
+      const int cx = wrap_g(gx + d / 9 - 1, G), cy = wrap_g(gy + (d / 3) % 3 - 1, G), cz = wrap_g(gz + d % 3 - 1, G);
+      const float dx = (float)(int)(prop_centre(cx, G) - p.x) * c.r.scale;
+      const float dy = (float)(int)(prop_centre(cy, G) - p.y) * c.r.scale;
+      const float dz = (float)(int)(prop_centre(cz, G) - p.z) * c.r.scale;
+      const float r = fmaxf(sqrtf(dx * dx + dy * dy + dz * dz), 0.5f);
+      const float f = 0.1f * q / (r * r * r);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(pv.fld + 4 * (size_t)((cx * G + cy) * G + cz));
+      atomicAdd(dst + 0, (unsigned long long)__double2ll_rn((double)(f * dx) * 0x1.0p40));
+      atomicAdd(dst + 1, (unsigned long long)__double2ll_rn((double)(f * dy) * 0x1.0p40));
+      atomicAdd(dst + 2, (unsigned long long)__double2ll_rn((double)(f * dz) * 0x1.0p40));
+    }
+  }
+  c.sync();
+}
+
+// logits of every cell: warps of the group take 16-cell tiles in turn
+__device__ void prop_mlp_all(const Ctx& c, const PropView& pv) {
+  const Eng& e = *c.e;
+  const int lane = c.tid & 31, warp = c.tid >> 5, nw = c.T >> 5, g = lane >> 2, t = lane & 3;
+  const int ntiles = (pv.nc + 15) >> 4;
+  for (int tile = warp; tile < ntiles; tile += nw) {
+    const int r0 = 16 * tile + g, r1 = r0 + 8;
+    auto loadA = [&](int ks, unsigned (&a)[4]) {
+      const int k = 16 * ks + 2 * t;
+      const bool v0 = r0 < pv.nc, v1 = r1 < pv.nc;
+      a[0] = v0 ? pack_bf16(prop_feature(pv, r0, k), prop_feature(pv, r0, k + 1)) : 0u;
+      a[1] = v1 ? pack_bf16(prop_feature(pv, r1, k), prop_feature(pv, r1, k + 1)) : 0u;
+      a[2] = v0 ? pack_bf16(prop_feature(pv, r0, k + 8), prop_feature(pv, r0, k + 9)) : 0u;
+      a[3] = v1 ? pack_bf16(prop_feature(pv, r1, k + 8), prop_feature(pv, r1, k + 9)) : 0u;
+    };
+    float out[4];
+    mlp_tile_forward(e.net, loadA, out);
+    if (t == 0) {
+      if (r0 < pv.nc) pv.logit[r0] = make_float2(out[0], out[1]);
+      if (r1 < pv.nc) pv.logit[r1] = make_float2(out[2], out[3]);
+    }
+  }
+  c.sync();
+}
+
+// largest logits and softmax normalisers; partial sums per 32-cell chunk in a fixed order
+__device__ void prop_stats(const Ctx& c, const PropView& pv) {
+  GScal* S = c.v.s;
+  float m0 = -INFINITY, m1 = -INFINITY;
+  for (int i = c.tid; i < pv.nc; i += c.T) {
+    const float2 l = __ldcg(pv.logit + i);
+    m0 = fmaxf(m0, l.x);
+    m1 = fmaxf(m1, l.y);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+  }
+  if ((c.tid & 31) == 0) {
+    S->pmw[0][c.tid >> 5] = m0;
+    S->pmw[1][c.tid >> 5] = m1;
+  }
+  c.sync();
+  if (c.tid == 0) {
+    float a = -INFINITY, b = -INFINITY;
+    for (int w = 0; w < (c.T >> 5); ++w) {
+      a = fmaxf(a, S->pmw[0][w]);
+      b = fmaxf(b, S->pmw[1][w]);
+    }
+    S->pm[0] = a;
+    S->pm[1] = b;
+  }
+  c.sync();
+  const double M0 = (double)S->pm[0], M1 = (double)S->pm[1];
+  const int nch = (pv.nc + 31) >> 5;
+  for (int j = c.tid; j < nch; j += c.T) {
+    double s0 = 0.0, s1 = 0.0;
+    const int end = min(32 * j + 32, pv.nc);
+    for (int i = 32 * j; i < end; ++i) {
+      const float2 l = __ldcg(pv.logit + i);
+      s0 += exp((double)l.x - M0);
+      s1 += exp((double)l.y - M1);
+    }
+    pv.chunk[j] = make_double2(s0, s1);
+  }
+  c.sync();
+  if (c.tid == 0) {
+    double z0 = 0.0, z1 = 0.0;
+    for (int j = 0; j < nch; ++j) {
+      const double2 z = __ldcg(pv.chunk + j);
+      z0 += z.x;
+      z1 += z.y;
+    }
+    S->pZ[0] = z0;
+    S->pZ[1] = z1;
+  }
+  c.sync();
+}
+
+__device__ __forceinline__ double prop_weight(const PropView& pv, const GScal* S, int s, int k) {
+  const float2 l = __ldcg(pv.logit + k);
+  return exp((double)(s ? l.y : l.x) - (double)S->pm[s]);
+}
+
+// log of the proposal density relative to uniform, ln(q_s(k) G^3)
+__device__ __forceinline__ double prop_lnq(const PropView& pv, const GScal* S, int s, int k, double eps) {
+  return log(((1.0 - eps) * prop_weight(pv, S, s, k) / S->pZ[s] + eps / pv.nc) * pv.nc);
+}
+
+// cell of species s: with probability eps a uniform cell, else the first cell whose running
+// softmax sum exceeds u Z (thread 0 only)
+__device__ __noinline__ int prop_draw(const PropView& pv, const GScal* S, int s, u64 r_mix, u64 r_cell, double eps) {
+  if (u01(r_mix) < eps) return pick_index(r_cell, pv.nc);
+  const double target = u01(r_cell) * S->pZ[s];
+  const int nch = (pv.nc + 31) >> 5;
+  double cum = 0.0;
+  for (int j = 0; j < nch; ++j) {
+    const double2 z = __ldcg(pv.chunk + j);
+    const double cs = s ? z.y : z.x;
+    if (cum + cs > target) {  // the cell lies in this chunk (a rounding miss moves on)
+      const double tt = target - cum;
+      double part = 0.0;
+      const int end = min(32 * j + 32, pv.nc);
+      for (int i = 32 * j; i < end; ++i) {
+        part += prop_weight(pv, S, s, i);
+        if (part > tt) return i;
+      }
+    }
+    cum += cs;
+  }
+  for (int i = pv.nc - 1; i > 0; --i)  // target not reached through rounding: last live cell
+    if (prop_weight(pv, S, s, i) > 0.0) return i;
+  return 0;
+}
+
+// a 32-bit coordinate uniform over cell coordinate g: [ceil(g 2^32/G), ceil((g+1) 2^32/G))
+__device__ __forceinline__ unsigned prop_place(int g, int G, unsigned r32) {
+  const u64 lo = ((((u64)g) << 32) + (u64)G - 1) / (u64)G;
+  const u64 hi = ((((u64)(g + 1)) << 32) + (u64)G - 1) / (u64)G;
+  return (unsigned)(lo + (((u64)r32 * (hi - lo)) >> 32));
+}
+
+// training record of the trial: features of the cation and the anion cell
+__device__ __noinline__ void prop_record_features(const Ctx& c, const PropView& pv, int slot, int cell_c, int cell_a) {
+  const Eng& e = *c.e;
+  float* dst = e.prec_feat + (size_t)(c.R->prec_off + slot) * 192;
+  for (int i = c.tid; i < 192; i += c.T) dst[i] = prop_feature(pv, i < 96 ? cell_c : cell_a, i % 96);
+}
+
+// grid (and, with the learned proposal, logits and normalisers) of the current state
+// without ex0, ex1 (kept out of line: it runs once per trial)
+__device__ __noinline__ void prop_prepare(const Ctx& c, const PropView& pv, int ex0, int ex1) {
+  prop_grid(c, pv, ex0, ex1);
+  if (c.e->proto.prop_mode) {
+    prop_mlp_all(c, pv);
+    prop_stats(c, pv);
+  }
+}
+
 template <int SYS>
 __device__ void trial_phase(const Ctx& c) {
   const Eng& e = *c.e;
@@ -1280,6 +1493,9 @@ __device__ void trial_phase(const Ctx& c) {
     if (S->ins && N >= R.cap_pairs) S->status = 2;
     S->cat = -1;
     S->ani = -1;
+    S->lnq = 0.0;
+    S->cell_c = S->cell_a = -1;
+    S->prec_slot = -1;
     if (S->ins) {
       S->xfly[0] = (unsigned)(b1[0] >> 32); S->xfly[1] = (unsigned)(b1[1] >> 32);
       S->xfly[2] = (unsigned)(b1[2] >> 32); S->xfly[3] = (unsigned)(b1[3] >> 32);
@@ -1308,8 +1524,8 @@ __device__ void trial_phase(const Ctx& c) {
     if (c.tid == 0) {
       h4d_record rr;
       rr.move = ins; rr.accepted = 0; rr.n_before = N; rr.n_after = N; rr.status = S->status;
-      rr.cation = -1; rr.anion = -1; rr.pad = 0;
-      rr.dH = 0.0; rr.beta_dM = 0.0; rr.w_prot = 0.0; rr.ln_u = S->ln_u; rr.x_acc = 0.0;
+      rr.cation = -1; rr.anion = -1; rr.cell_c = -1; rr.cell_a = -1; rr.pad = 0;
+      rr.dH = 0.0; rr.beta_dM = 0.0; rr.w_prot = 0.0; rr.ln_u = S->ln_u; rr.x_acc = 0.0; rr.ln_q = 0.0;
       e.rec[R.rec_off + (int)(R.rec_count % R.rec_cap)] = rr;
       R.rec_count++;
       R.cycles++;
@@ -1320,6 +1536,35 @@ __device__ void trial_phase(const Ctx& c) {
     }
     c.sync();
     return;
+  }
+  // proposal grid: an insertion draws its cells from the start state (flyers absent)
+  const bool grid = R.prop_G > 0 && (e.proto.prop_mode || e.proto.prop_record);
+  if (grid && ins) {
+    const PropView pv = prop_view(e, R);
+    prop_prepare(c, pv, -1, -1);
+    if (c.tid == 0) {
+      if (e.proto.prop_mode) {
+        // draw block 5: [0], [1] uniform-component choice, [2], [3] cell of the cation, anion;
+        // the 32-bit position draws then place each ion inside its cell
+        u64 b5[4];
+        draw4(e.seed, rep_id, R.trial_ctr - 1, 5, kPurTrial, b5);
+        const int G = pv.G;
+        double lnq = 0.0;
+        for (int sp = 0; sp < 2; ++sp) {
+          const int k = prop_draw(pv, S, sp, b5[sp], b5[2 + sp], e.proto.prop_eps);
+          lnq += prop_lnq(pv, S, sp, k, e.proto.prop_eps);
+          S->xfly[3 * sp + 0] = prop_place(k / (G * G), G, S->xfly[3 * sp + 0]);
+          S->xfly[3 * sp + 1] = prop_place((k / G) % G, G, S->xfly[3 * sp + 1]);
+          S->xfly[3 * sp + 2] = prop_place(k % G, G, S->xfly[3 * sp + 2]);
+        }
+        S->lnq = lnq;
+      }
+      S->cell_c = prop_cell_of(S->xfly[0], S->xfly[1], S->xfly[2], pv.G);
+      S->cell_a = prop_cell_of(S->xfly[3], S->xfly[4], S->xfly[5], pv.G);
+      S->prec_slot = (e.proto.prop_record && R.prec_cap > 0) ? (int)(R.prec_count % R.prec_cap) : -1;
+    }
+    c.sync();
+    if (S->prec_slot >= 0) prop_record_features(c, pv, S->prec_slot, S->cell_c, S->cell_a);
   }
   // save the state for a rejection (positions from shared memory, velocities)
   for (int a = c.tid; a < n; a += c.T) {
@@ -1400,6 +1645,22 @@ __device__ void trial_phase(const Ctx& c) {
   // H_end: insertion has everyone in 3D, deletion leaves the flyers out
   const double Ue = ins ? energy64(c, -1, -1) : energy64(c, f0, f1);
   const double Ke = kinetic64(c);
+  // proposal grid: the reverse insertion of a deletion draws from the end state, flyers
+  // removed, the cells the flyers occupy
+  if (grid && !ins) {
+    const PropView pv = prop_view(e, R);
+    prop_prepare(c, pv, f0, f1);
+    if (c.tid == 0) {
+      const uint4 pc = c.v.pos[f0], pa = c.v.pos[f1];
+      S->cell_c = prop_cell_of(pc.x, pc.y, pc.z, pv.G);
+      S->cell_a = prop_cell_of(pa.x, pa.y, pa.z, pv.G);
+      if (e.proto.prop_mode)
+        S->lnq = prop_lnq(pv, S, 0, S->cell_c, e.proto.prop_eps) + prop_lnq(pv, S, 1, S->cell_a, e.proto.prop_eps);
+      S->prec_slot = (e.proto.prop_record && R.prec_cap > 0) ? (int)(R.prec_count % R.prec_cap) : -1;
+    }
+    c.sync();
+    if (S->prec_slot >= 0) prop_record_features(c, pv, S->prec_slot, S->cell_c, S->cell_a);
+  }
   if (c.tid == 0) {
     const double dH = (Ue + Ke) - (Us + Ks);
     const double V = R.L * R.L * R.L;
@@ -1411,6 +1672,8 @@ __device__ void trial_phase(const Ctx& c) {
       bdm = -e.proto.beta * dH - 2.0 * log(V / (double)N);       // Eq. 8
       xacc = bdm - e.proto.beta_mu;
     }
+    const double x_phys = xacc;
+    xacc += ins ? -S->lnq : S->lnq;  // proposal density relative to uniform placement
     int status = (isfinite(dH) && !S->flag_nan && !S->flag_overflow) ? 0 : 3;
     S->flag_nan = 0;
     S->flag_overflow = 0;
@@ -1420,8 +1683,15 @@ __device__ void trial_phase(const Ctx& c) {
     rr.move = ins; rr.accepted = acc; rr.n_before = N;
     rr.n_after = N + (acc ? (ins ? 1 : -1) : 0);
     rr.status = status;
-    rr.cation = ins ? -1 : S->cat; rr.anion = ins ? -1 : S->ani; rr.pad = 0;
-    rr.dH = dH; rr.beta_dM = bdm; rr.w_prot = S->wprot; rr.ln_u = S->ln_u; rr.x_acc = xacc;
+    rr.cation = ins ? -1 : S->cat; rr.anion = ins ? -1 : S->ani;
+    rr.cell_c = S->cell_c; rr.cell_a = S->cell_a; rr.pad = 0;
+    rr.dH = dH; rr.beta_dM = bdm; rr.w_prot = S->wprot; rr.ln_u = S->ln_u; rr.x_acc = xacc; rr.ln_q = S->lnq;
+    if (S->prec_slot >= 0) {
+      const int gi = R.prec_off + S->prec_slot;
+      e.prec_y[gi] = ins ? x_phys : -x_phys;
+      e.prec_meta[gi] = make_int2(ins, status);
+      R.prec_count++;
+    }
     e.rec[R.rec_off + (int)(R.rec_count % R.rec_cap)] = rr;
     R.rec_count++;
     R.cycles++;
@@ -1535,6 +1805,26 @@ __global__ void __launch_bounds__(H4D_MAXTHREADS, H4D_MINBLOCKS) cycles_kernel(c
 }
 
 // current U (FP64) and K of each replica
+// proposal logits (and optionally every feature) of one replica's current state
+__global__ void __launch_bounds__(1024) prop_eval_kernel(const __grid_constant__ Eng e, int replica, float* feat_out) {
+  extern __shared__ __align__(16) char smem[];
+  Ctx c;
+  if (!setup_ctx(e, smem, c)) return;
+  if ((int)(c.R - e.rep) != replica) return;
+  const PropView pv = prop_view(e, *c.R);
+  prop_grid(c, pv, -1, -1);
+  prop_mlp_all(c, pv);
+  if (feat_out)
+    for (int i = c.tid; i < pv.nc * kPropNFeat; i += c.T) feat_out[i] = prop_feature(pv, i / kPropNFeat, i % kPropNFeat);
+}
+
+int launch_prop_eval(const Eng& e, int n_ctas, int cta_threads, size_t smem, int replica, float* feat_out,
+                     void* stream) {
+  cudaFuncSetAttribute(prop_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  prop_eval_kernel<<<n_ctas, cta_threads, smem, (cudaStream_t)stream>>>(e, replica, feat_out);
+  return cudaGetLastError() == cudaSuccess ? H4D_OK : H4D_ECUDA;
+}
+
 __global__ void __launch_bounds__(1024) energy_kernel(const __grid_constant__ Eng e, double* U, double* K) {
   extern __shared__ __align__(16) char smem[];
   Ctx c;

@@ -14,6 +14,7 @@
 #include <cstdint>
 
 #include "../../include/h4d.h"
+#include "h4d_prop.cuh"
 
 namespace h4d {
 
@@ -31,13 +32,18 @@ struct Pot {
   double dm[kMaxT];    // m mvv2e
   double d_oh2, d_hh2;  // squared water bond lengths
   double inv_m_d[kMaxT];
+  float q[kMaxT];       // charges per type (proposal field feature)
 };
 
 struct Proto {
   int n_f, schedule;
   double w_max, sched_n, dt, tau_t;
   double beta, beta_mu;
-  int no_accept, pad;
+  int no_accept;
+  int prop_mode;    // 0 uniform placement, 1 learned proposal density
+  int prop_record;  // write a training record for every trial
+  int pad;
+  double prop_eps;  // weight of the uniform component of the learned proposal
 };
 
 struct Rep {
@@ -67,7 +73,10 @@ struct Rep {
   double t_nemd_ns, t_md_ns;
   double t_build_ns, t_force_ns, t_energy_ns;  // phase timers (thread 0 of the group)
   int dirty;      // state changed on the host: rebuild list and forces
-  int pad;
+  int prop_G;     // proposal grid cells per edge (0 = no grid)
+  int prop_off;   // first cell of this replica in the grid arrays (a multiple of 32)
+  int prec_off, prec_cap;  // training-record ring of this replica
+  long long prec_count;
 };
 
 struct Group {
@@ -94,6 +103,15 @@ struct Eng {
   int* ncnt_out;
   uint4* ref_out;     // positions at the last outer build
   h4d_record* rec;
+  // learned proposal: packed network, per-cell grid of every replica, training records
+  PropNet net;
+  int4* pg_cnt;         // [cells] cation, anion, water-O counts of the cell itself
+  long long* pg_fld;    // [cells][4] field at the cell centre, fixed point 2^-40
+  float2* pg_logit;     // [cells] cation and anion logits
+  double2* pg_chunk;    // [cells / 32] softmax partial sums per 32-cell chunk
+  float* prec_feat;     // [records][2][96] features of the cation and the anion cell
+  double* prec_y;       // [records] insertion-direction exponent without proposal factor
+  int2* prec_meta;      // [records] move, status (-1 = empty slot)
   int max_nbr;
   int max_out;
   unsigned long long seed;
@@ -127,5 +145,7 @@ int launch_forces(const Eng& e, int n_ctas, int cta_threads, size_t smem, int n_
 int launch_list(const Eng& e, int n_ctas, int cta_threads, size_t smem, void* stream);
 int launch_count_pairs(const Eng& e, int n_ctas, int cta_threads, size_t smem,
                        unsigned long long* out, void* stream);
+int launch_prop_eval(const Eng& e, int n_ctas, int cta_threads, size_t smem, int replica, float* feat_out,
+                     void* stream);
 
 }  // namespace h4d

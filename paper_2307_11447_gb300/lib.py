@@ -109,14 +109,20 @@ RECORD_DTYPE = np.dtype(
         ("status", np.int32),
         ("cation", np.int32),
         ("anion", np.int32),
+        ("cell_c", np.int32),
+        ("cell_a", np.int32),
         ("pad", np.int32),
         ("dH", np.float64),
         ("beta_dM", np.float64),
         ("w_prot", np.float64),
         ("ln_u", np.float64),
         ("x_acc", np.float64),
+        ("ln_q", np.float64),
     ]
 )
+H4D_PROPOSAL_UNIFORM = 0
+H4D_PROPOSAL_LEARNED = 1
+H4D_PROP_NW = 96 * 64 + 64 + 64 * 64 + 64 + 64 * 2 + 2
 
 _lib = None
 
@@ -159,6 +165,13 @@ def lib():
             "h4d_eval_forces": ([ctypes.POINTER(h4d_params), d, i32, i32, pd, pd, pd, pd], i32),
             "h4d_eval_forces_static": ([ctypes.POINTER(h4d_params), d, i32, i32, pd, pd, pd, pd], i32),
             "h4d_neighbor_pairs": ([d, i32, pd, d, pi32, pi32, i64, ctypes.POINTER(i64)], i32),
+            "h4d_proposal": ([vp, i32, d, d, i32], i32),
+            "h4d_proposal_set_weights": ([vp, pd, i64], i32),
+            "h4d_proposal_get_weights": ([vp, pd, i64], i32),
+            "h4d_proposal_records": ([vp, i32, vp, pd, pi32, pi32, i64, ctypes.POINTER(i64)], i32),
+            "h4d_proposal_logits": ([vp, i32, vp, vp, i64, ctypes.POINTER(i64)], i32),
+            "h4d_train_proposal": ([vp, i64, i32, d, d, ctypes.c_uint64, pd], i32),
+            "h4d_proposal_grad": ([pd, i64, vp, vp, pd, pd], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -318,6 +331,51 @@ class Context:
     def h4d_load(self, path):
         _ck(lib().h4d_load(self.h, path.encode()), "h4d_load")
 
+    # ---- learned insertion-site proposal ----
+    def h4d_proposal(self, mode, cell_len, eps=0.1, records_per_replica=0):
+        _ck(lib().h4d_proposal(self.h, int(mode), cell_len, eps, int(records_per_replica)), "h4d_proposal")
+
+    def h4d_proposal_set_weights(self, w):
+        w = np.ascontiguousarray(w, np.float64)
+        _ck(lib().h4d_proposal_set_weights(self.h, _pd(w), w.size), "h4d_proposal_set_weights")
+
+    def h4d_proposal_get_weights(self) -> np.ndarray:
+        w = np.zeros(H4D_PROP_NW)
+        _ck(lib().h4d_proposal_get_weights(self.h, _pd(w), w.size), "h4d_proposal_get_weights")
+        return w
+
+    def h4d_proposal_records(self, r=0, cap=1 << 20):
+        """(features [n, 2, 96] float32, y [n], move [n], status [n]) of replica r"""
+        n = ctypes.c_int64()
+        _ck(lib().h4d_proposal_records(self.h, r, None, None, None, None, cap, ctypes.byref(n)), "h4d_proposal_records")
+        k = n.value
+        f = np.zeros((max(k, 1), 2, 96), np.float32)
+        y = np.zeros(max(k, 1))
+        mv = np.zeros(max(k, 1), np.int32)
+        st = np.zeros(max(k, 1), np.int32)
+        pi = ctypes.POINTER(ctypes.c_int32)
+        _ck(lib().h4d_proposal_records(self.h, r, f.ctypes.data, _pd(y), mv.ctypes.data_as(pi), st.ctypes.data_as(pi),
+                                       k, ctypes.byref(n)), "h4d_proposal_records")
+        return f[:k], y[:k], mv[:k], st[:k]
+
+    def h4d_proposal_logits(self, r=0, features=False):
+        n = ctypes.c_int64()
+        rc = lib().h4d_proposal_logits(self.h, r, None, None, 0, ctypes.byref(n))
+        if rc not in (H4D_OK, H4D_ECAPACITY):
+            _ck(rc, "h4d_proposal_logits")
+        nc = n.value
+        lg = np.zeros((nc, 2), np.float32)
+        ft = np.zeros((nc, 96), np.float32) if features else None
+        _ck(lib().h4d_proposal_logits(self.h, r, lg.ctypes.data, None if ft is None else ft.ctypes.data, nc,
+                                      ctypes.byref(n)), "h4d_proposal_logits")
+        return (lg, ft) if features else lg
+
+    def h4d_train_proposal(self, steps, batch, lr, y0, seed=0) -> float:
+        loss = ctypes.c_double()
+        _ck(lib().h4d_train_proposal(self.h, int(steps), int(batch), lr, y0, seed, ctypes.byref(loss)),
+            "h4d_train_proposal")
+        return loss.value
+
 
 def h4d_eval_forces(params: h4d_params, L: float, x, w=None, n_water: int = 0):
     x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
@@ -354,3 +412,16 @@ def h4d_neighbor_pairs(L: float, x, r_list: float):
         "h4d_neighbor_pairs",
     )
     return oi[: m.value], oj[: m.value]
+
+
+def h4d_proposal_grad(w, feat, tgt):
+    """loss and gradient of the proposal network on records feat [n, 2, 96] with targets
+    tgt [n, 2], through the library's BF16 forward/backward kernels"""
+    w = np.ascontiguousarray(w, np.float64)
+    f = np.ascontiguousarray(feat, np.float32).reshape(-1, 2, 96)
+    t = np.ascontiguousarray(tgt, np.float32).reshape(-1, 2)
+    g = np.zeros(H4D_PROP_NW)
+    loss = ctypes.c_double()
+    _ck(lib().h4d_proposal_grad(_pd(w), f.shape[0], f.ctypes.data, t.ctypes.data, ctypes.byref(loss), _pd(g)),
+        "h4d_proposal_grad")
+    return loss.value, g

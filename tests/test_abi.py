@@ -49,6 +49,6 @@ def test_strerror_names_every_code():
 
 def test_structure_sizes_match_header_layout():
     import ctypes
-    # h4d_record: 8 int32 + 5 double
-    assert h4d.RECORD_DTYPE.itemsize == 72
+    # h4d_record: 10 int32 + 6 double
+    assert h4d.RECORD_DTYPE.itemsize == 88
     assert ctypes.sizeof(h4d.h4d_counts) == 8 * 18
