@@ -10,10 +10,13 @@ Tolerances (written here, derived in the design doc):
     |dg| <= 2^-6 g_abs + 1e-7 max g_abs elementwise, g_abs the backward pass on absolute
     values (the GPU rounds dL/dlogit, dz2 and dz1 to bfloat16: three roundings of 2^-9);
   * trials: the cells drawn are identical, ln q within 1e-4; beta dM within 1e-3 kT for
-    trials within 20 kT of the acceptance boundary with the median within 2e-5 kT (FP32
-    pair forces alone produce that spread, tests/test_oracle_tolerance.py), else within
-    1e-3 relative (insertions onto an overlap exchange up to 1e6 kT under forces of 1e20
-    that FP32 and FP64 integrate apart; their acceptance is zero on both sides);
+    trials within 20 kT of the acceptance boundary and at least half of them within
+    2e-5 kT (FP32 pair forces alone produce that spread, tests/test_oracle_tolerance.py:
+    a pair that lands within binary32 rounding of a cut-off is counted in a different
+    step; trials from one state replay the same bulk trajectory, so such an event can be
+    shared by several of them), else within 1e-3 relative (insertions onto an overlap
+    exchange up to 1e6 kT under forces of 1e20 that FP32 and FP64 integrate apart; their
+    acceptance is zero on both sides);
   * detailed balance: the ideal pair gas with a strongly state-dependent network keeps
     P(N) = lam^N / (N!)^2 / I0(2 sqrt(lam)) within 0.01 per N.
 """
@@ -176,7 +179,7 @@ def test_uniform_mode_records_match_oracle():
         if abs(ro["x_acc"]) < 20:
             near.append(abs(yg[-1] - yo))
     assert moves == {0, 1}
-    assert np.median(near) <= 2e-5, near
+    assert np.mean(np.array(near) <= 2e-5) >= 0.5, near
 
 
 # ---------------------------------------------------------------------------------------
@@ -221,7 +224,7 @@ def test_learned_trials_match_oracle():
         # n_f dt (dF dt / m) ~ 4e-5 sigma over the trajectory
         assert xg.shape == xo.shape and np.abs(d).max() < 1e-4
     assert moves == {0, 1}
-    assert np.median(near) <= 2e-5, near
+    assert np.mean(np.array(near) <= 2e-5) >= 0.5, near
     # the network is far from uniform: the factor moves the exponent by order one
     recs = ctx.h4d_get_work(0, 10)
     assert np.abs(recs["ln_q"]).max() > 0.5

@@ -58,3 +58,22 @@ def test_fp32_pair_forces_alone_move_trial_work_by_up_to_1e_3_kT():
     assert np.median(devs) < 2e-5
     assert devs.max() > 1e-4  # FP32 forces alone exceed 1e-4 kT on some trials ...
     assert devs.max() < 1e-3  # ... and stay inside the 1e-3 kT GPU tolerance
+
+
+def test_fp64_trajectory_can_put_a_pair_within_binary32_rounding_of_the_cutoff():
+    """the mechanism behind the jumps: 11 NVE steps from the seed-6 state bring ions 24 and
+    54 to 1.1e-7 sigma inside the Coulomb cut-off (4 sigma) -- closer than binary32 resolves
+    r^2 = 16 (one ulp is 9.5e-7 below 16) -- so an FP32 force pass may count the pair a step
+    later than FP64 does; the missed force jump, 0.05 kT/sigma, costs about 2.9e-4 kT"""
+    cfg, po, x0, v0 = _state(6)
+    L = cfg["L"]
+    p0 = orc.make_params(dict(cfg, tau_t=0.0), use_cells=0)
+    st = orc.State(p0, x0, v0, cfg["n_pairs"], cfg["cap_pairs"])
+    orc.nve(p0, st, 11)
+    x = st.positions()
+    d = x[54] - x[24]
+    d -= L * np.round(d / L)
+    r = float(np.sqrt(d @ d))
+    print(f"r(24, 54) after 11 steps = 4 - {4.0 - r:.3e}")
+    assert 0.0 < 4.0 - r < 2e-7
+    assert np.float32(r * r) >= np.float32(16.0) - np.spacing(np.float32(16.0))
