@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--n-eq", type=int, default=None, help="override equilibrium steps per cycle (profiling)")
     ap.add_argument("--n-f", type=int, default=None, help="override NEMD steps per trial (profiling)")
     ap.add_argument("--tune-iters", type=int, default=20, help="force passes per autotuner candidate")
+    # learned-proposal workload (nacl_learned): records, training and calibration before timing
+    ap.add_argument("--records", type=int, default=100000, help="training records to generate (nacl_learned)")
+    ap.add_argument("--record-nf", type=int, default=50, help="NEMD steps of the record-generating trials")
+    ap.add_argument("--cell-len", type=float, default=1.4, help="proposal grid cell edge (A)")
+    ap.add_argument("--train-steps", type=int, default=2000)
+    ap.add_argument("--calib-cycles", type=int, default=2, help="fixed-N production cycles per proposal")
     return ap.parse_args()
 
 
@@ -69,12 +75,12 @@ def workload(name, chains, rank):
         if ARGS.n_f is not None:
             cfg["n_f"] = ARGS.n_f
         return cfg, reps
-    cfg = dict(wl.CONFIGS[name])
+    cfg = dict(wl.CONFIGS["nacl_aq" if name == "nacl_learned" else name])
     if ARGS.n_eq is not None:
         cfg["n_eq"] = ARGS.n_eq
     if ARGS.n_f is not None:
         cfg["n_f"] = ARGS.n_f
-    if name == "nacl_aq":
+    if name in ("nacl_aq", "nacl_learned"):
         reps = []
         for c in range(chains):
             x = wl.aqueous_positions(cfg["n_water"], cfg["n_pairs"], cfg["L"], 2000 * (rank + 1) + c)
@@ -169,6 +175,9 @@ def run_gpu(args):
     n_eq, n_f = cfg["n_eq"], cfg["n_f"]
     # equilibrate the random starts (untimed), autotune the force pass, then warm up
     ctx.h4d_run_md(args.equil)
+    learned = None
+    if args.workload == "nacl_learned":
+        learned = learned_setup(ctx, cfg, args, stream)
     tune = ctx.h4d_autotune(args.tune_iters)
     tpa_hist = {}
     for r in range(ctx.R):
@@ -236,6 +245,9 @@ def run_gpu(args):
     sm_mhz = clk.get("sm_max_mhz") or 2070.0
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
+    if learned is not None:
+        learned["uniform_arm"] = uniform_arm(ctx, reps, args, n_eq, n_f, stream)
+        ctx.h4d_proposal(h4d.H4D_PROPOSAL_LEARNED, args.cell_len, 0.1, 0)
     seq = None
     if args.sequential and args.workload == "batched256":
         seq = sequential_baseline(reps, cfg, args.sequential, n_eq)
@@ -276,6 +288,8 @@ def run_gpu(args):
                          "pairs_in_cutoff": pairs, "flops_per_pair": FLOPS_PER_PAIR},
             "e2e": e2e,
         }
+        if learned is not None:
+            out["learned_proposal"] = learned
         if seq is not None:
             out["sequential_one_replica_at_a_time"] = seq
             out["batched_over_sequential"] = value / seq["value"]
@@ -288,6 +302,12 @@ def run_gpu(args):
 
 
 def workload_config(args, cfg, reps, n_f, n_eq, world):
+    if args.workload == "nacl_learned":
+        return {"workload": f"learned proposal on aqueous NaCl: {cfg['n_water']} rigid waters + {cfg['n_pairs']} NaCl, "
+                            f"L={cfg['L']} A, N_f={n_f}, N_eq={n_eq}, {len(reps)} chains/GPU, "
+                            f"{args.cell_len} A proposal cells", "chains_per_gpu": len(reps),
+                "n_f": n_f, "n_eq": n_eq, "parallelism": f"replicas x{world}",
+                "l2": "state > L2; no flush needed"}
     if args.workload == "nacl_aq":
         return {"workload": f"aqueous NaCl: {cfg['n_water']} rigid waters + {cfg['n_pairs']} NaCl, L={cfg['L']} A, "
                             f"N_f={n_f}, N_eq={n_eq}, {len(reps)} chains/GPU", "chains_per_gpu": len(reps),
@@ -303,6 +323,125 @@ def workload_config(args, cfg, reps, n_f, n_eq, world):
                         f"{args.chains} chains/GPU", "chains_per_gpu": args.chains, "ions": cfg["n_ions"],
             "n_f": n_f, "n_eq": n_eq, "parallelism": f"replicas x{world}",
             "l2": "state > L2 (about 1.3 GB per GPU); no flush needed"}
+
+
+# ---------------------------------------------------------------------------------------
+# learned insertion-site proposal on aqueous NaCl
+# ---------------------------------------------------------------------------------------
+def _balanced_mu(x_ins, x_del):
+    """beta mu at which insertions and deletions of a fixed-N sample (taken at beta mu = 0)
+    are accepted equally often: the equilibrium condition of Eqs. 3-8 at that N"""
+    f = lambda m: np.exp(np.minimum(x_ins + m, 0)).mean() - np.exp(np.minimum(x_del - m, 0)).mean()
+    lo, hi = -1000.0, 1000.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if f(mid) < 0 else (lo, mid)
+    return 0.5 * (lo + hi)
+
+
+def _initial_weights(seed):
+    """seeded Gaussian start of the 96-64-64-2 network (std 1/sqrt(fan-in), zero biases),
+    flat layout W1, b1, W2, b2, W3, b3"""
+    rng = np.random.default_rng(seed)
+    parts = [rng.normal(0, 96 ** -0.5, 96 * 64), np.zeros(64), rng.normal(0, 64 ** -0.5, 64 * 64), np.zeros(64),
+             rng.normal(0, 64 ** -0.5, 64 * 2), np.zeros(2)]
+    return np.concatenate(parts)
+
+
+def _fixed_n_sample(ctx, cycles):
+    recs = []
+    ctx.h4d_run_trials(cycles, 10)
+    for r in range(ctx.R):
+        w = ctx.h4d_get_work(r, cycles)
+        recs.append(w[w["status"] == 0])
+    rec = np.concatenate(recs)
+    ins = rec["move"] == 1
+    return rec["x_acc"][ins], rec["x_acc"][~ins]
+
+
+def learned_setup(ctx, cfg, args, stream):
+    """Untimed preparation of the learned proposal: fixed-N uniform trials with a short
+    protocol generate the training records, the network trains on the GPU, and a fixed-N
+    sample of production trials of each proposal gives the balancing beta mu and the
+    insertion and deletion exponents of both (taken at beta mu = 0)."""
+    import torch
+
+    from paper_2307_11447_gb300 import lib as h4d
+
+    R = ctx.R
+    n_f = cfg["n_f"]
+    per_rep = int(math.ceil(args.records / R))
+    ctx.h4d_set_no_accept(1)
+    ctx.h4d_set_mu(0.0)
+    ctx.h4d_set_protocol(args.record_nf, cfg["w_max"], cfg["dt"], cfg.get("kappa_sr", 0.0), 0)
+    ctx.h4d_proposal(h4d.H4D_PROPOSAL_UNIFORM, args.cell_len, 0.1, per_rep)
+    t0 = time.perf_counter()
+    done = 0
+    while done < per_rep:
+        k = min(50, per_rep - done)
+        ctx.h4d_run_trials(k, 10)
+        done += k
+    torch.cuda.synchronize()
+    t_rec = time.perf_counter() - t0
+    ys = np.concatenate([ctx.h4d_proposal_records(r)[1] for r in range(R)])
+    y0 = float(np.median(ys))
+    ctx.h4d_proposal_set_weights(_initial_weights(1))
+    t0 = time.perf_counter()
+    loss0 = ctx.h4d_train_proposal(1, 4096, 0.0, y0, seed=1)
+    loss = ctx.h4d_train_proposal(args.train_steps, 4096, 2e-3, y0, seed=2)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    # production protocol, fixed N: both proposals from the same ensemble
+    ctx.h4d_set_protocol(n_f, cfg["w_max"], cfg["dt"], cfg.get("kappa_sr", 0.0), 0)
+    ctx.h4d_proposal(h4d.H4D_PROPOSAL_UNIFORM, args.cell_len, 0.1, 0)
+    ui, ud = _fixed_n_sample(ctx, args.calib_cycles)
+    ctx.h4d_proposal(h4d.H4D_PROPOSAL_LEARNED, args.cell_len, 0.1, 0)
+    li, ld = _fixed_n_sample(ctx, args.calib_cycles)
+    mu = _balanced_mu(ui, ud)
+    acc = lambda xi, xd: 0.5 * (np.exp(np.minimum(xi + mu, 0)).mean() + np.exp(np.minimum(xd - mu, 0)).mean())
+    ctx.h4d_set_no_accept(0)
+    ctx.h4d_set_mu(mu)
+    return {
+        "records": int(len(ys)), "record_n_f": args.record_nf, "cell_len_A": args.cell_len,
+        "grid_cells_per_edge": int(max(3, min(32, math.floor(cfg["L"] / args.cell_len)))),
+        "record_generation_s": t_rec, "train_steps": args.train_steps, "train_batch": 4096, "train_s": t_train,
+        "train_loss_first_last": [loss0, loss], "target_shift_y0": y0,
+        "beta_mu_balanced": mu,
+        "fixed_n_production": {
+            "trials_per_proposal": int(len(ui) + len(ud)),
+            "uniform": {"median_x_ins": float(np.median(ui)), "median_x_del": float(np.median(ud)),
+                        "mean_acceptance_at_balanced_mu": float(acc(ui, ud))},
+            "learned": {"median_x_ins": float(np.median(li)), "median_x_del": float(np.median(ld)),
+                        "mean_acceptance_at_balanced_mu": float(acc(li, ld))},
+        },
+    }
+
+
+def uniform_arm(ctx, reps, args, n_eq, n_f, stream):
+    """The same grand-canonical cycles with uniform placement (the plain method), timed
+    like the learned ones."""
+    import torch
+
+    from paper_2307_11447_gb300 import lib as h4d
+
+    ctx.h4d_proposal(h4d.H4D_PROPOSAL_UNIFORM, args.cell_len, 0.1, 0)
+    c0 = [ctx.h4d_get_counts(r) for r in range(ctx.R)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        ctx.h4d_run_trials(1, n_eq)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    secs = ev[0].elapsed_time(ev[1]) / 1e3
+    c1 = [ctx.h4d_get_counts(r) for r in range(ctx.R)]
+    acc = sum((b["accepted_ins"] + b["accepted_del"]) - (a["accepted_ins"] + a["accepted_del"]) for a, b in zip(c0, c1))
+    units = 0.0
+    for r, (a, b) in enumerate(zip(c0, c1)):
+        mean_pairs = (b["sum_n"] - a["sum_n"]) / max(b["cycles"] - a["cycles"], 1)
+        units += (2.0 * mean_pairs + 3.0 * reps[r].get("n_water", 0)) * (n_eq + n_f) * args.steps
+    return {"atom_steps_per_s": units / secs, "accepted_exchanges_per_s": acc / secs, "accepted": int(acc),
+            "ms_per_step": 1e3 * secs / args.steps}
 
 
 def sequential_baseline(reps, cfg, count, n_eq):
@@ -383,15 +522,18 @@ def _oracle_chain(job):
     from oracle import oracle as orc
     from paper_2307_11447_gb300 import workloads as wl
 
-    cfg = dict(wl.CONFIGS[name])
+    cfg = dict(wl.CONFIGS["nacl_aq" if name == "nacl_learned" else name])
     p = orc.make_params(cfg, use_cells=1, seed=seed)
-    x = wl.lj_positions(cfg["n_pairs"], cfg["L"], seed)
+    if cfg.get("n_water", 0):
+        x = wl.aqueous_positions(cfg["n_water"], cfg["n_pairs"], cfg["L"], seed)
+    else:
+        x = wl.lj_positions(cfg["n_pairs"], cfg["L"], seed)
     st = orc.State(p, x, None, cfg["n_pairs"], cfg["cap_pairs"])
     orc.init_velocities(p, st)
     t0 = time.perf_counter()
     orc.md(p, st, n_steps)
     dt = time.perf_counter() - t0
-    return 2 * cfg["n_pairs"] * n_steps, dt
+    return (3 * cfg.get("n_water", 0) + 2 * cfg["n_pairs"]) * n_steps, dt
 
 
 def cpu_baseline(name, sample_steps=8, cores=None):
@@ -408,8 +550,9 @@ def cpu_baseline(name, sample_steps=8, cores=None):
     wall = time.perf_counter() - t0
     units = sum(r[0] for r in res)
     busy = max(r[1] for r in res)
+    system = "aqueous NaCl system" if name in ("nacl_aq", "nacl_learned") else "4000-ion system"
     return {"value": units / busy, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"{cores} chains x {sample_steps} MD steps of the 4000-ion system, cell list, FP64 "
+            "sample": f"{cores} chains x {sample_steps} MD steps of the {system}, cell list, FP64 "
                       f"(wall {wall:.1f} s incl. process start)"}
 
 
@@ -455,7 +598,7 @@ def main():
     global ARGS
     args = parse()
     if args.chains is None:
-        args.chains = 152 if args.workload == "nacl_aq" else 304
+        args.chains = 152 if args.workload in ("nacl_aq", "nacl_learned") else 304
     ARGS = args
     if args.impl == "reference":
         run_reference(args)
