@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--n-eq", type=int, default=None, help="override equilibrium steps per cycle (profiling)")
     ap.add_argument("--n-f", type=int, default=None, help="override NEMD steps per trial (profiling)")
     ap.add_argument("--tune-iters", type=int, default=20, help="force passes per autotuner candidate")
+    ap.add_argument("--skin", type=float, default=None, help="Verlet skin (default: the workload's)")
+    ap.add_argument("--skin-outer", type=float, default=None, help="outer-list skin (default: the workload's)")
     # learned-proposal workload (nacl_learned): records, training and calibration before timing
     ap.add_argument("--records", type=int, default=100000, help="training records to generate (nacl_learned)")
     ap.add_argument("--record-nf", type=int, default=50, help="NEMD steps of the record-generating trials")
@@ -76,6 +78,10 @@ def workload(name, chains, rank):
             cfg["n_f"] = ARGS.n_f
         return cfg, reps
     cfg = dict(wl.CONFIGS["nacl_aq" if name == "nacl_learned" else name])
+    if ARGS.skin is not None:
+        cfg["skin"] = ARGS.skin
+    if ARGS.skin_outer is not None:
+        cfg["skin_outer"] = ARGS.skin_outer
     if ARGS.n_eq is not None:
         cfg["n_eq"] = ARGS.n_eq
     if ARGS.n_f is not None:
@@ -370,7 +376,7 @@ def learned_setup(ctx, cfg, args, stream):
 
     R = ctx.R
     n_f = cfg["n_f"]
-    per_rep = int(math.ceil(args.records / R))
+    per_rep = int(math.ceil(args.records / R)) + 4  # a few trials end with non-finite work
     ctx.h4d_set_no_accept(1)
     ctx.h4d_set_mu(0.0)
     ctx.h4d_set_protocol(args.record_nf, cfg["w_max"], cfg["dt"], cfg.get("kappa_sr", 0.0), 0)
@@ -383,8 +389,16 @@ def learned_setup(ctx, cfg, args, stream):
         done += k
     torch.cuda.synchronize()
     t_rec = time.perf_counter() - t0
-    ys = np.concatenate([ctx.h4d_proposal_records(r)[1] for r in range(R)])
-    y0 = float(np.median(ys))
+    ys, sts = [], []
+    for r in range(R):
+        _, y, _, s = ctx.h4d_proposal_records(r)
+        ys.append(y)
+        sts.append(s)
+    ys, sts = np.concatenate(ys), np.concatenate(sts)
+    ok = (sts == 0) & np.isfinite(ys)  # training uses the same records
+    if not ok.any():
+        raise RuntimeError("no usable training records")
+    y0 = float(np.median(ys[ok]))
     ctx.h4d_proposal_set_weights(_initial_weights(1))
     t0 = time.perf_counter()
     loss0 = ctx.h4d_train_proposal(1, 4096, 0.0, y0, seed=1)
@@ -402,7 +416,7 @@ def learned_setup(ctx, cfg, args, stream):
     ctx.h4d_set_no_accept(0)
     ctx.h4d_set_mu(mu)
     return {
-        "records": int(len(ys)), "record_n_f": args.record_nf, "cell_len_A": args.cell_len,
+        "records": int(ok.sum()), "record_n_f": args.record_nf, "cell_len_A": args.cell_len,
         "grid_cells_per_edge": int(max(3, min(32, math.floor(cfg["L"] / args.cell_len)))),
         "record_generation_s": t_rec, "train_steps": args.train_steps, "train_batch": 4096, "train_s": t_train,
         "train_loss_first_last": [loss0, loss], "target_shift_y0": y0,
