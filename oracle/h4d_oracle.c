@@ -597,6 +597,46 @@ double orc_nemd_path(const orc_params* p, orc_state* s, const int32_t* flyers, i
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* Bimodal flyer-distance bias (Sec. II.B.3)                                             */
+/* ------------------------------------------------------------------------------------ */
+double orc_bias_density(double alpha, double xb, double L, double x) {
+  double sa = sqrt(alpha);
+  double num = exp(-alpha * (x - xb) * (x - xb)) + exp(-alpha * (x + xb) * (x + xb));
+  double den = erf(sa * (xb + 0.5 * L)) - erf(sa * (xb - 0.5 * L));
+  return sqrt(alpha / M_PI) * num / den;
+}
+
+/* inverse error function: Winitzki's closed-form approximation (a = 0.147) as the start,
+ * then Newton steps x <- x - (erf(x) - y) / (2/sqrt(pi) exp(-x^2)) */
+double orc_erfinv(double y) {
+  const double a = 0.147;
+  double w = log((1.0 - y) * (1.0 + y));
+  double t = 2.0 / (M_PI * a) + 0.5 * w;
+  double x = copysign(sqrt(sqrt(t * t - w / a) - t), y);
+  for (int k = 0; k < 6; ++k) {
+    double d = 2.0 / sqrt(M_PI) * exp(-x * x);
+    if (!(d > 0.0)) break;
+    x -= (erf(x) - y) / d;
+  }
+  return x;
+}
+
+double orc_bias_offset(double alpha, double xb, double L, uint64_t r_mode, uint64_t r_u) {
+  double c = (r_mode >> 63) ? xb : -xb;
+  double sa = sqrt(alpha);
+  double lo = erf(sa * (-0.5 * L - c)), hi = erf(sa * (0.5 * L - c));
+  double u = ((double)(r_u >> 11) + 0.5) * 0x1.0p-53; /* in (0, 1) */
+  return c + orc_erfinv(lo + u * (hi - lo)) / sa;
+}
+
+/* B^ins of the anion at xa relative to the cation at xc: V prod_i b(x_ac,i) (Eq. 14) */
+static double bias_B(const orc_params* p, const double* xa, const double* xc) {
+  double B = p->L * p->L * p->L;
+  for (int k = 0; k < 3; ++k) B *= orc_bias_density(p->bias_alpha, p->bias_xb, p->L, minimg(xa[k] - xc[k], p->L));
+  return B;
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* Learned insertion-site proposal (definitions in h4d_oracle.h)                         */
 /* ------------------------------------------------------------------------------------ */
 static int species_of(int type) { return type <= 2 ? type : -1; } /* water H is not counted */
@@ -744,6 +784,10 @@ static void flip_all(double* v, int n) {
  *   block 5: learned proposal only: [0], [1] choose the uniform component (u < eps) for
  *            the cation and the anion cell, [2], [3] draw the cation and the anion cell;
  *            the 32-bit draws of blocks 1-2 then place each ion inside its cell
+ *   block 6: bimodal bias only: [0..2] top bit picks the mode (+x_b or -x_b) of the
+ *            anion offset on x, y, z; the anion's position words of blocks 1-2 then
+ *            drive the inverse CDF of that truncated Gaussian.  Deletion with the bias
+ *            picks the anion by inverse CDF of B^ins with u01 of block 1 word 1.
  * Readings: insertion and deletion are proposed with probability 1/2 each; the cation
  * and the anion are chosen independently (Eq. 3 squares 1/(N+1)); the momentum
  * reversal flips every velocity with probability 1/2 before NEMD and again after the
@@ -756,13 +800,14 @@ static void flip_all(double* v, int n) {
 int orc_trial_prop(const orc_params* p, const orc_proposal* q, orc_state* s, orc_record* rec,
                    double* site_feat, double* site_y) {
   uint64_t t = s->trial_ctr++;
-  uint64_t b0[4], b1[4], b2[4], b3[4], b4[4], b5[4];
+  uint64_t b0[4], b1[4], b2[4], b3[4], b4[4], b5[4], b6[4];
   draw(p, t, 0, ORC_PUR_TRIAL, b0);
   draw(p, t, 1, ORC_PUR_TRIAL, b1);
   draw(p, t, 2, ORC_PUR_TRIAL, b2);
   draw(p, t, 3, ORC_PUR_TRIAL, b3);
   draw(p, t, 4, ORC_PUR_TRIAL, b4);
   draw(p, t, 5, ORC_PUR_TRIAL, b5);
+  draw(p, t, 6, ORC_PUR_TRIAL, b6);
   int insertion = (int)(b0[0] >> 63);
   int flip_start = (int)(b0[1] >> 63), flip_end = (int)(b0[2] >> 63);
   double ln_u = log(u01_open(b0[3]));
@@ -779,6 +824,7 @@ int orc_trial_prop(const orc_params* p, const orc_proposal* q, orc_state* s, orc
   rec->cell_c = rec->cell_a = -1;
   rec->ln_u = ln_u;
   int learned = q && q->mode == 1;
+  int biased = p->bias_alpha > 0.0 && !learned;
   int G = q ? q->G : 0, nc = G * G * G;
   double ln_q = 0.0;
 
@@ -821,6 +867,14 @@ int orc_trial_prop(const orc_params* p, const orc_proposal* q, orc_state* s, orc
       free(lg);
       free(e);
     }
+    if (biased) {
+      /* the anion at a biased offset from the cation, per axis, in 32-bit box units */
+      for (int d = 0; d < 3; ++d) {
+        double off = orc_bias_offset(p->bias_alpha, p->bias_xb, p->L, b6[d], d == 0 ? b1[3] : b2[d - 1]);
+        int64_t k = (int64_t)nearbyint(off / p->L * 4294967296.0);
+        X[3 + d] = (uint32_t)((uint64_t)((int64_t)X[d] + k) & 0xffffffffULL);
+      }
+    }
     for (int d = 0; d < 3; ++d) {
       s->x[3 * ci + d] = (double)X[d] * h;
       s->x[3 * ai + d] = (double)X[3 + d] * h;
@@ -852,8 +906,33 @@ int orc_trial_prop(const orc_params* p, const orc_proposal* q, orc_state* s, orc
     /* H_end: the N+1-pair system, everyone in 3D */
     Uend = orc_energy_forces(p, ntot, s->x, NULL, NULL, NULL);
     Kend = orc_kinetic(p, ntot, s->v, fly);
+    if (biased) {
+      /* B^ins / B^del of the reverse deletion, in the end state: the mean of B^ins over
+       * the N+1 anions relative to the inserted cation (Eq. 15) */
+      double sum = 0.0;
+      for (int k = 0; k <= N; ++k) sum += bias_B(p, &s->x[3 * (base + 2 * k + 1)], &s->x[3 * ci]);
+      ln_q = log(sum / (double)(N + 1));
+    }
   } else {
     int c = pick(b1[0], N), a = pick(b1[1], N);
+    if (biased) {
+      /* the anion with probability B^ins(r_a,n | r_c) / sum_n B^ins (Eq. 15); the factor
+       * B^ins / B^del is the mean of B^ins over the N anions of the start state */
+      double* Bn = (double*)malloc(sizeof(double) * (size_t)N);
+      double sum = 0.0;
+      for (int k = 0; k < N; ++k) {
+        Bn[k] = bias_B(p, &s->x[3 * (base + 2 * k + 1)], &s->x[3 * (base + 2 * c)]);
+        sum += Bn[k];
+      }
+      double target = u01(b1[1]) * sum, cum = 0.0;
+      a = N - 1;
+      for (int k = 0; k < N; ++k) {
+        cum += Bn[k];
+        if (cum > target) { a = k; break; }
+      }
+      ln_q = log(sum / (double)N);
+      free(Bn);
+    }
     rec->cation = c;
     rec->anion = a;
     ci = base + 2 * c;

@@ -56,6 +56,10 @@ typedef struct {
   double d_oh, d_hh;
   int32_t n_water, use_cells;
   uint64_t seed, replica;
+  /* bimodal flyer-distance bias (Sec. II.B.3, Eqs. 14-18): the anion is placed at an
+   * offset from the cation drawn per axis from b (Eq. 16) with sharpness bias_alpha and
+   * mean separation bias_xb; bias_alpha <= 0 switches it off */
+  double bias_alpha, bias_xb;
 } orc_params;
 
 typedef struct {
@@ -126,6 +130,15 @@ int orc_run_cycles(const orc_params* p, orc_state* s, int64_t n_cycles, int64_t 
 
 /* draw initial Maxwell-Boltzmann velocities for all atoms */
 void orc_init_velocities(const orc_params* p, orc_state* s);
+
+/* Bimodal bias.  Density of the anion-cation offset x on one axis, x in [-L/2, L/2)
+ * (Eq. 16, normalised on the box); the inverse error function used to draw from it
+ * (Winitzki's approximation refined by Newton steps on erf); one draw of the offset from
+ * two 64-bit random words (the top bit of r_mode picks the mode at +x_b or -x_b, which
+ * carry equal mass; r_u drives the inverse CDF of that truncated Gaussian). */
+double orc_bias_density(double alpha, double xb, double L, double x);
+double orc_erfinv(double y);
+double orc_bias_offset(double alpha, double xb, double L, uint64_t r_mode, uint64_t r_u);
 
 /* ------------------------------------------------------------------------------------ */
 /* Learned insertion-site proposal.  The box is cut into G^3 cells (cell index           */

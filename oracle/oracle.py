@@ -84,6 +84,8 @@ class Params(ctypes.Structure):
         ("use_cells", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
         ("replica", ctypes.c_uint64),
+        ("bias_alpha", ctypes.c_double),
+        ("bias_xb", ctypes.c_double),
     ]
 
 
@@ -182,6 +184,12 @@ def lib():
         _lib.orc_run_cycles.argtypes = [P, S, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
         _lib.orc_init_velocities.argtypes = [P, S]
         _lib.orc_atom_type.argtypes = [P, ctypes.c_int]
+        _lib.orc_bias_density.argtypes = [d, d, d, d]
+        _lib.orc_bias_density.restype = d
+        _lib.orc_erfinv.argtypes = [d]
+        _lib.orc_erfinv.restype = d
+        _lib.orc_bias_offset.argtypes = [d, d, d, ctypes.c_uint64, ctypes.c_uint64]
+        _lib.orc_bias_offset.restype = d
         Q = ctypes.POINTER(Proposal)
         _lib.orc_proposal_features.argtypes = [P, ctypes.c_int, ctypes.c_int, pd, ctypes.c_int, ctypes.c_int, pd]
         _lib.orc_proposal_logits.argtypes = [P, Q, ctypes.c_int, pd, ctypes.c_int, ctypes.c_int, pd]
@@ -228,6 +236,8 @@ def make_params(cfg: dict, **override) -> Params:
     p.use_cells = int(c.get("use_cells", 0))
     p.seed = int(c.get("seed", 0))
     p.replica = int(c.get("replica", 0))
+    p.bias_alpha = float(c.get("bias_alpha", 0.0))
+    p.bias_xb = float(c.get("bias_xb", 0.0))
     return p
 
 
@@ -379,3 +389,15 @@ def run_cycles_prop(p: Params, q: Proposal | None, st: State, n_cycles: int, n_e
     lib().orc_run_cycles_prop(ctypes.byref(p), None if q is None else ctypes.byref(q), ctypes.byref(st.s),
                               n_cycles, n_eq, recs.ctypes.data)
     return recs
+
+
+def bias_density(alpha, xb, L, x):
+    return lib().orc_bias_density(alpha, xb, L, x)
+
+
+def erfinv(y):
+    return lib().orc_erfinv(y)
+
+
+def bias_offset(alpha, xb, L, r_mode, r_u):
+    return lib().orc_bias_offset(alpha, xb, L, int(r_mode), int(r_u))
