@@ -156,6 +156,18 @@ const char* h4d_strerror(int code);
 int h4d_set_mu(h4d_ctx* ctx, double beta_mu);
 int h4d_set_protocol(h4d_ctx* ctx, int32_t n_f, double w_max, double dt, double kappa_sr,
                      int32_t schedule);
+/* Bimodal flyer-distance bias (Sec. II.B.3, Eqs. 14-18), off by default (alpha_b = 0).
+ * Insertion: the cation is placed uniformly, the anion at an offset drawn per axis from
+ * b(x) = sqrt(alpha_b/pi) [e^{-alpha_b (x - x_b)^2} + e^{-alpha_b (x + x_b)^2}] /
+ * [erf(sqrt(alpha_b)(x_b + L/2)) - erf(sqrt(alpha_b)(x_b - L/2))] on [-L/2, L/2) (Eq. 16;
+ * alpha_b in 1/length^2, x_b a length).  Deletion: the cation uniformly, the anion with
+ * probability B^ins(r_a | r_c) / sum_n B^ins, B^ins = V prod_axes b.  The exponent gains
+ * -ln q for an insertion (q over the end state) and +ln q for a deletion (start state),
+ * q = mean of B^ins over the anions with the pair present relative to its cation
+ * (Eqs. 17-18; record field ln_q).  Random draws: block 6 of the trial, words 0-2, pick
+ * the mode (top bit) on x, y, z; the anion's position words of blocks 1-2 drive the
+ * inverse CDF.  Cannot be combined with the learned proposal (H4D_EINVAL). */
+int h4d_set_bias(h4d_ctx* ctx, double alpha_b, double x_b);
 /* fixed-N work sampling (SI Sec. S1, Eq. 21): trials are run and recorded but never
  * accepted when on != 0 */
 int h4d_set_no_accept(h4d_ctx* ctx, int32_t on);
@@ -210,7 +222,8 @@ int h4d_count_pairs(h4d_ctx* ctx, int64_t* n_pairs_in_cutoff);
  * evaluated on the end state with the flyers removed (record field ln_q).
  * Random draws: block 5 of the trial (counter {trial, 5, 1, 0}): words 0 and 1 choose the
  * uniform component (u < eps) for the cation and the anion, words 2 and 3 the cell; the
- * 32-bit position draws of blocks 1-2 place the ion inside the cell.
+ * 32-bit position draws of blocks 1-2 place the ion inside the cell.  Cannot be combined
+ * with the bimodal bias (H4D_EINVAL).
  * Flat weight layout (row index = input unit, doubles on the host, FP32 masters on the
  * device): W1[96][64], b1[64], W2[64][64], b2[64], W3[64][2], b3[2]. */
 #define H4D_PROPOSAL_UNIFORM 0

@@ -738,8 +738,21 @@ int h4d_set_protocol(h4d_ctx* c, int32_t n_f, double w_max, double dt, double ka
   c->eng.proto.prop_mode = keep.prop_mode;
   c->eng.proto.prop_record = keep.prop_record;
   c->eng.proto.prop_eps = keep.prop_eps;
+  c->eng.proto.bias_on = keep.bias_on;
+  c->eng.proto.bias_alpha = keep.bias_alpha;
+  c->eng.proto.bias_xb = keep.bias_xb;
   invalidate_graphs(c);
   return push_plan(c);
+}
+
+int h4d_set_bias(h4d_ctx* c, double alpha_b, double x_b) {
+  if (!c || !std::isfinite(alpha_b) || !std::isfinite(x_b) || alpha_b < 0 || x_b < 0) return H4D_EINVAL;
+  if (alpha_b > 0 && c->eng.proto.prop_mode) return H4D_EINVAL;  // one placement rule at a time
+  c->eng.proto.bias_on = alpha_b > 0 ? 1 : 0;
+  c->eng.proto.bias_alpha = alpha_b;
+  c->eng.proto.bias_xb = x_b;
+  invalidate_graphs(c);
+  return H4D_OK;
 }
 
 int h4d_set_no_accept(h4d_ctx* c, int32_t on) {
@@ -1370,6 +1383,7 @@ int h4d_proposal(h4d_ctx* c, int32_t mode, double cell_len, double eps, int32_t 
   if (!c || (mode != H4D_PROPOSAL_UNIFORM && mode != H4D_PROPOSAL_LEARNED) || !(cell_len > 0) || !(eps > 0) ||
       !(eps <= 1) || records_per_replica < 0 || records_per_replica > (1 << 20))
     return H4D_EINVAL;
+  if (mode == H4D_PROPOSAL_LEARNED && c->eng.proto.bias_on) return H4D_EINVAL;  // one placement rule
   int rc = pull_reps(c);
   if (rc) return rc;
   CK(cudaStreamSynchronize(c->stream));

@@ -1468,6 +1468,71 @@ __device__ __noinline__ void prop_prepare(const Ctx& c, const PropView& pv, int 
   }
 }
 
+
+// ------------------------------------------------------------------------------------
+// Bimodal flyer-distance bias (Sec. II.B.3, Eqs. 14-18).  The anion of an insertion sits
+// at an offset from the (uniform) cation drawn per axis from b (Eq. 16): two Gaussians
+// at +-x_b of sharpness alpha, truncated to [-L/2, L/2) and normalised there.  A deletion
+// picks its anion with probability B^ins(r_a | r_c) / sum_n B^ins, B^ins = V prod_i b.
+// The Metropolis exponent gains -ln q (insertion) or +ln q (deletion) with
+// q = mean of B^ins over the anions of the state with the pair present.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ double bias_density(double alpha, double xb, double L, double x) {
+  const double sa = sqrt(alpha);
+  const double num = exp(-alpha * (x - xb) * (x - xb)) + exp(-alpha * (x + xb) * (x + xb));
+  const double den = erf(sa * (xb + 0.5 * L)) - erf(sa * (xb - 0.5 * L));
+  return sqrt(alpha / 3.141592653589793) * num / den;
+}
+
+// inverse error function: Winitzki's approximation (a = 0.147), then Newton steps on erf
+__device__ double bias_erfinv(double y) {
+  const double a = 0.147;
+  const double w = log((1.0 - y) * (1.0 + y));
+  const double t = 2.0 / (3.141592653589793 * a) + 0.5 * w;
+  double x = copysign(sqrt(sqrt(t * t - w / a) - t), y);
+  for (int k = 0; k < 6; ++k) {
+    const double d = 1.1283791670955126 * exp(-x * x);  // 2/sqrt(pi) e^{-x^2}
+    if (!(d > 0.0)) break;
+    x -= (erf(x) - y) / d;
+  }
+  return x;
+}
+
+// one offset from b: the top bit of r_mode picks the mode (equal masses), r_u drives the
+// inverse CDF of that truncated Gaussian
+__device__ __noinline__ double bias_offset(double alpha, double xb, double L, u64 r_mode, u64 r_u) {
+  const double c = (r_mode >> 63) ? xb : -xb;
+  const double sa = sqrt(alpha);
+  const double lo = erf(sa * (-0.5 * L - c)), hi = erf(sa * (0.5 * L - c));
+  const double u = ((double)(r_u >> 11) + 0.5) * 0x1.0p-53;
+  return c + bias_erfinv(lo + u * (hi - lo)) / sa;
+}
+
+// B^ins of the atom at pa relative to the one at pc (minimum-image offsets, exact)
+__device__ __noinline__ double bias_B(const Proto& pr, double L, const uint4& pa, const uint4& pc) {
+  const double s = L * 0x1.0p-32;
+  double B = L * L * L;
+  B *= bias_density(pr.bias_alpha, pr.bias_xb, L, (double)(int)(pa.x - pc.x) * s);
+  B *= bias_density(pr.bias_alpha, pr.bias_xb, L, (double)(int)(pa.y - pc.y) * s);
+  B *= bias_density(pr.bias_alpha, pr.bias_xb, L, (double)(int)(pa.z - pc.z) * s);
+  return B;
+}
+
+// sum of B^ins over the anions 0..n_anions-1 relative to the cation at pc; with
+// target >= 0 also the first anion whose running sum exceeds target (thread 0 only)
+__device__ __noinline__ double bias_sum(const Proto& pr, double L, const uint4* pos, int nw3, int n_anions,
+                                        const uint4 pc, double target, int* pick) {
+  double sum = 0.0;
+  int a = n_anions - 1;
+  bool found = target < 0.0;
+  for (int k = 0; k < n_anions; ++k) {
+    sum += bias_B(pr, L, pos[nw3 + 2 * k + 1], pc);
+    if (!found && sum > target) { a = k; found = true; }
+  }
+  if (pick) *pick = a;
+  return sum;
+}
+
 template <int SYS>
 __device__ void trial_phase(const Ctx& c) {
   const Eng& e = *c.e;
@@ -1500,6 +1565,18 @@ __device__ void trial_phase(const Ctx& c) {
       S->xfly[0] = (unsigned)(b1[0] >> 32); S->xfly[1] = (unsigned)(b1[1] >> 32);
       S->xfly[2] = (unsigned)(b1[2] >> 32); S->xfly[3] = (unsigned)(b1[3] >> 32);
       S->xfly[4] = (unsigned)(b2[0] >> 32); S->xfly[5] = (unsigned)(b2[1] >> 32);
+      if (e.proto.bias_on) {
+        // draw block 6: [0..2] the mode of the anion offset on x, y, z; the anion's
+        // position words of blocks 1-2 drive the inverse CDF
+        u64 b6[4];
+        draw4(e.seed, rep_id, t, 6, kPurTrial, b6);
+        const u64 ru[3] = {b1[3], b2[0], b2[1]};
+        for (int d = 0; d < 3; ++d) {
+          const double off = bias_offset(e.proto.bias_alpha, e.proto.bias_xb, R.L, b6[d], ru[d]);
+          const long long k = __double2ll_rn(off / R.L * 4294967296.0);
+          S->xfly[3 + d] = S->xfly[d] + (unsigned)(unsigned long long)k;
+        }
+      }
       const double sdc = sqrt(1.0 / (e.proto.beta * e.pot.dm[0]));
       const double sda = sqrt(1.0 / (e.proto.beta * e.pot.dm[1]));
       S->vfly[0] = sdc * gauss_c(b3[0], b3[1]);
@@ -1511,6 +1588,16 @@ __device__ void trial_phase(const Ctx& c) {
     } else if (N > 0) {
       S->cat = pick_index(b1[0], N);
       S->ani = pick_index(b1[1], N);
+      if (e.proto.bias_on) {
+        // the anion with probability B^ins(r_a,n | r_c) / sum_n B^ins (Eq. 15), in index
+        // order; the factor B^ins / B^del is the mean of B^ins over the N anions
+        const uint4 pc = c.v.pos[R.nw3 + 2 * S->cat];
+        const double sum = bias_sum(e.proto, R.L, c.v.pos, R.nw3, N, pc, -1.0, nullptr);
+        int a = N - 1;
+        bias_sum(e.proto, R.L, c.v.pos, R.nw3, N, pc, u01(b1[1]) * sum, &a);
+        S->ani = a;
+        S->lnq = log(sum / (double)N);
+      }
     }
   }
   c.sync();
@@ -1673,6 +1760,12 @@ __device__ void trial_phase(const Ctx& c) {
       xacc = bdm - e.proto.beta_mu;
     }
     const double x_phys = xacc;
+    if (ins && e.proto.bias_on) {
+      // B^ins / B^del of the reverse deletion, in the end state: the mean of B^ins over the
+      // N+1 anions relative to the inserted cation
+      const double sum = bias_sum(e.proto, R.L, c.v.pos, R.nw3, N + 1, c.v.pos[f0], -1.0, nullptr);
+      S->lnq = log(sum / (double)(N + 1));
+    }
     xacc += ins ? -S->lnq : S->lnq;  // proposal density relative to uniform placement
     int status = (isfinite(dH) && !S->flag_nan && !S->flag_overflow) ? 0 : 3;
     S->flag_nan = 0;

@@ -42,8 +42,9 @@ struct Proto {
   int no_accept;
   int prop_mode;    // 0 uniform placement, 1 learned proposal density
   int prop_record;  // write a training record for every trial
-  int pad;
+  int bias_on;      // bimodal flyer-distance bias (Sec. II.B.3)
   double prop_eps;  // weight of the uniform component of the learned proposal
+  double bias_alpha, bias_xb;  // sharpness and mean separation of the bias (Eq. 16)
 };
 
 struct Rep {
