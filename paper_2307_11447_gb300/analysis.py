@@ -18,26 +18,32 @@ import numpy as np
 from scipy import special
 
 
-def bar_mu(bdm_ins: np.ndarray, bdm_del: np.ndarray, iters: int = 100) -> float:
+def bar_mu(bdm_ins: np.ndarray, bdm_del: np.ndarray, iters: int = 200) -> float:
     """beta*mu solving sum_i f(beta(C + dM_i) - beta mu) = sum_j f(-(beta(C + dM_j) - beta mu))
-    with f(x) = 1/(1+e^x) and C = ln(N_ins/N_del)/beta; inputs are beta*Delta M."""
+    with f(x) = 1/(1+e^x) and C = ln(N_ins/N_del)/beta; inputs are beta*Delta M.  Both sides
+    are taken as log-sums (ln f(x) = -softplus(x)), so the root stays defined when the two
+    work distributions barely overlap; the left side grows and the right side falls with
+    beta mu, so bisection finds the unique root."""
     a = np.asarray(bdm_ins, np.float64)
     b = np.asarray(bdm_del, np.float64)
     c = math.log(a.size / b.size)
-    mu = 0.5 * (np.median(a) + np.median(b))
+
+    def g(mu):
+        left = special.logsumexp(-np.logaddexp(0.0, c + a - mu))
+        right = special.logsumexp(-np.logaddexp(0.0, -(c + b - mu)))
+        return left - right
+
+    lo = min(a.min(), b.min()) - 50.0
+    hi = max(a.max(), b.max()) + 50.0
     for _ in range(iters):
-        xa = c + a - mu
-        xb = c + b - mu
-        fa = special.expit(-xa)  # 1/(1+e^{xa})
-        fb = special.expit(xb)   # 1/(1+e^{-xb})
-        g = fa.sum() - fb.sum()
-        # d/dmu of each side
-        dg = (fa * (1 - fa)).sum() + (fb * (1 - fb)).sum()
-        step = -g / dg
-        mu += step
-        if abs(step) < 1e-12:
+        mid = 0.5 * (lo + hi)
+        if g(mid) < 0.0:
+            lo = mid
+        else:
+            hi = mid
+        if hi - lo < 1e-12:
             break
-    return float(mu)
+    return float(0.5 * (lo + hi))
 
 
 def p_acc(bdm: np.ndarray, beta_mu: float, insertion: bool) -> float:

@@ -182,3 +182,58 @@ def test_gpu_checkpoint_resume_is_bit_identical(tmp_path):
         ca, cb = a.h4d_get_counts(r), b.h4d_get_counts(r)
         for k in ("n_pairs", "cycles", "accepted_ins", "accepted_del", "md_steps"):
             assert ca[k] == cb[k]
+
+
+def _fixed_n_bdm(cfg, n_pairs, move, R, seed0):
+    reps = [dict(L=cfg["L"], n_pairs=n_pairs, cap_pairs=cfg["cap_pairs"], x=wl.lj_positions(n_pairs, cfg["L"], seed0 + r))
+            for r in range(R)]
+    ctx = h4d.Context(h4d.make_params(cfg), reps, seed=seed0)
+    ctx.h4d_run_md(300)
+    ctx.h4d_set_no_accept(1)
+    ctx.h4d_run_trials(300, 20)
+    out = []
+    for r in range(R):
+        rec = ctx.h4d_get_work(r, 300)
+        ok = (rec["status"] == 0) & (rec["move"] == move)
+        out.append(rec["beta_dM"][ok])
+    return out
+
+
+def test_bar_mu_from_fixed_n_work_balances_grand_canonical_occupation():
+    """SI Sec. S1: the BAR estimate of beta mu from fixed-N insertion work at N and
+    deletion work at N+1 (Crooks, Eq. S1) is the beta mu at which grand-canonical chains
+    occupy N and N+1 equally: P(N+1)/P(N) = 1 within the errors of both (the BAR error
+    from a bootstrap over replicas, the occupation ratio from replica means)"""
+    # a dense liquid state point (200 ions at rho 0.3), where P(N) is narrow and unimodal
+    # (the dilute electrolyte of the other chain tests sits near liquid-vapour coexistence,
+    # where grand-canonical chains wander far from any one N)
+    cfg = dict(wl.lj_config(200, 0.3, 300, cap_pairs=140, beta_mu=0.0))
+    N, R = 100, 64
+    ins = _fixed_n_bdm(cfg, N, 1, R, 700)
+    dele = _fixed_n_bdm(cfg, N + 1, 0, R, 900)
+    mu = an.bar_mu(np.concatenate(ins), np.concatenate(dele))
+    rng = np.random.default_rng(0)
+    boots = []
+    for _ in range(40):
+        a = rng.integers(0, R, R)
+        b = rng.integers(0, R, R)
+        boots.append(an.bar_mu(np.concatenate([ins[i] for i in a]), np.concatenate([dele[j] for j in b])))
+    s_mu = float(np.std(boots, ddof=1))
+    RG = 128
+    reps = [dict(L=cfg["L"], n_pairs=N, cap_pairs=cfg["cap_pairs"], x=wl.lj_positions(N, cfg["L"], 1100 + r))
+            for r in range(RG)]
+    ctx = h4d.Context(h4d.make_params(cfg, beta_mu=mu), reps, seed=77)
+    ctx.h4d_run_md(300)
+    ctx._n_eq = 20
+    n = _n_series(ctx, RG, 1500)[:, 300:]
+    c_n = (n == N).sum(1).astype(float)
+    c_n1 = (n == N + 1).sum(1).astype(float)
+    ratio = c_n1.sum() / c_n.sum()
+    # delta method on the replica totals
+    m1, m0 = c_n1.mean(), c_n.mean()
+    cov = np.cov(c_n1, c_n)
+    var_ln = (cov[0, 0] / m1**2 + cov[1, 1] / m0**2 - 2 * cov[0, 1] / (m1 * m0)) / RG
+    tol = 3.0 * math.sqrt(var_ln + s_mu**2)
+    print(f"BAR beta mu {mu:.3f} +- {s_mu:.3f} from {sum(map(len, ins))} + {sum(map(len, dele))} trials; "
+          f"GC at that mu: P(N+1)/P(N) = {ratio:.3f} (ln {math.log(ratio):+.3f}, tolerance {tol:.3f}), <N> {n.mean():.2f}")
+    assert abs(math.log(ratio)) < tol
