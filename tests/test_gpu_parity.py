@@ -182,3 +182,37 @@ def test_energy_getter_matches_oracle():
     Ko = orc.kinetic(po, v0)
     assert U == pytest.approx(Uo, rel=1e-10)
     assert K == pytest.approx(Ko, rel=1e-7)
+
+
+@pytest.mark.parametrize("sched,n", [("wv", 2.0), ("wx", 3.0)])
+def test_single_trials_with_nonlinear_schedules_match_oracle(sched, n):
+    """SI Eqs. S6-S7 (deletion the time reverse of insertion): single trials with the
+    w_v and w_x altitude schedules against the oracle; work within 1e-3 kT near the
+    acceptance boundary with at least half of those trials within 2e-5 kT (the FP32-force
+    spread derived in tests/test_oracle_tolerance.py), 1e-3 relative beyond it"""
+    cfg, x0, v0 = _equilibrated_c0(seed=3)
+    L = cfg["L"]
+    x0 = quantize(x0, L)
+    n_pairs = cfg["n_pairs"]
+    cfg.update(beta_mu=-8.0, schedule=sched, sched_n=n, n_f=60)
+    po = orc.make_params(cfg, use_cells=0)
+    ctx = h4d.Context(h4d.make_params(cfg), [dict(L=L, n_pairs=n_pairs, cap_pairs=cfg["cap_pairs"], x=x0, v=v0)],
+                      seed=cfg["seed"])
+    moves, near = set(), []
+    for k in range(8):
+        ctx.h4d_set_state(0, n_pairs, x0, v0)
+        ctx.h4d_run_trials(1, 0)
+        rg = ctx.h4d_get_work(0, 1)[0]
+        st = orc.State(po, x0, v0, n_pairs, cfg["cap_pairs"])
+        st.s.trial_ctr = k
+        ro = orc.trial(po, st)
+        moves.add(int(ro["move"]))
+        assert rg["move"] == ro["move"] and rg["status"] == ro["status"] == 0
+        err = abs(rg["beta_dM"] - ro["beta_dM"])
+        bound = 1e-3 if abs(ro["x_acc"]) < 20 else 1e-3 + 1e-3 * abs(ro["beta_dM"])
+        assert err <= bound, (k, rg["beta_dM"], ro["beta_dM"])
+        assert abs(rg["w_prot"] - ro["w_prot"]) <= bound
+        if abs(ro["x_acc"]) < 20:
+            near.append(err)
+    assert moves == {0, 1}
+    assert np.mean(np.array(near) <= 2e-5) >= 0.5, near
