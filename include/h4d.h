@@ -168,6 +168,13 @@ int h4d_set_protocol(h4d_ctx* ctx, int32_t n_f, double w_max, double dt, double 
  * the mode (top bit) on x, y, z; the anion's position words of blocks 1-2 drive the
  * inverse CDF.  Cannot be combined with the learned proposal (H4D_EINVAL). */
 int h4d_set_bias(h4d_ctx* ctx, double alpha_b, double x_b);
+/* Different w_max for the two ion species (SI, "Different w_max for different ion
+ * species"): the anion flies at w_max + 0.5 (sig_c + sig_a) f_w (sigmas of types 0 and 1)
+ * and moves proportionally faster, so both flyers reach (insertion) or leave (deletion)
+ * w = 0 together; the flyers' mutual pair then changes with the step and enters the
+ * protocol work, and the screening of Eq. 11 uses the mean flyer altitude.  The
+ * acceptance rule is unchanged.  f_w = 0 (default): one w_max for both. */
+int h4d_set_species_wmax(h4d_ctx* ctx, double f_w);
 /* fixed-N work sampling (SI Sec. S1, Eq. 21): trials are run and recorded but never
  * accepted when on != 0 */
 int h4d_set_no_accept(h4d_ctx* ctx, int32_t on);

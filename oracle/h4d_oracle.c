@@ -261,10 +261,17 @@ double orc_energy_forces(const orc_params* p, int n, const double* x, const doub
 }
 
 /* energy of the pairs that involve at least one flyer, the flyers at altitude wf */
+/* altitude of flyer i when the cation's altitude is w: the anion's is scaled by
+ * r_w = w_max,a / w_max,c (1 with one w_max for both species) */
+static double species_w(const orc_params* p, int i, double w) {
+  if (p->fw <= 0.0 || orc_atom_type(p, i) != 1) return w;
+  return w * (1.0 + 0.5 * (p->sig[0] + p->sig[1]) * p->fw / p->w_max);
+}
+
 static double flyer_energy(const orc_params* p, int n, const double* x, const uint8_t* fly, double wf,
                            double* wbuf) {
-  for (int i = 0; i < n; ++i) wbuf[i] = (fly[i] == 1) ? wf : 0.0;
-  double wbar = wf;
+  for (int i = 0; i < n; ++i) wbuf[i] = (fly[i] == 1) ? species_w(p, i, wf) : 0.0;
+  double wbar = mean_flyer_w(n, wbuf, fly);
   double U = 0.0;
   for (int i = 0; i < n; ++i) {
     if (fly[i] != 1) continue;
@@ -554,7 +561,7 @@ static double nemd(const orc_params* p, int n, double* x, double* v, const uint8
   double* wbuf = (double*)calloc((size_t)n, sizeof(double));
   double* xold = (double*)calloc(3 * (size_t)n, sizeof(double));
   double w0 = orc_altitude(p, insertion, 0);
-  for (int i = 0; i < n; ++i) w[i] = (fly[i] == 1) ? w0 : 0.0;
+  for (int i = 0; i < n; ++i) w[i] = (fly[i] == 1) ? species_w(p, i, w0) : 0.0;
   orc_energy_forces(p, n, x, w, fly, F);
   double wprot = 0.0;
   for (int k = 0; k < p->n_f; ++k) {
@@ -567,7 +574,7 @@ static double nemd(const orc_params* p, int n, double* x, double* v, const uint8
     drift(p, n, x, v, fly, h);
     if (p->n_water) shake(p, x, v, xold, h);
     wprot += flyer_energy(p, n, x, fly, wk1, wbuf) - flyer_energy(p, n, x, fly, wk, wbuf);
-    for (int i = 0; i < n; ++i) w[i] = (fly[i] == 1) ? wk1 : 0.0;
+    for (int i = 0; i < n; ++i) w[i] = (fly[i] == 1) ? species_w(p, i, wk1) : 0.0;
     orc_energy_forces(p, n, x, w, fly, F);
     kick(p, n, v, F, fly, 0.5 * h);
     if (p->n_water) rattle_v(p, x, v);
@@ -588,7 +595,7 @@ double orc_nemd_path(const orc_params* p, orc_state* s, const int32_t* flyers, i
   if (U_end) {
     double* w = (double*)calloc((size_t)n, sizeof(double));
     double wf = orc_altitude(p, insertion, p->n_f);
-    for (int i = 0; i < n; ++i) w[i] = fly[i] ? wf : 0.0;
+    for (int i = 0; i < n; ++i) w[i] = fly[i] ? species_w(p, i, wf) : 0.0;
     *U_end = orc_energy_forces(p, n, s->x, w, fly, NULL);
     free(w);
   }

@@ -60,6 +60,10 @@ typedef struct {
    * offset from the cation drawn per axis from b (Eq. 16) with sharpness bias_alpha and
    * mean separation bias_xb; bias_alpha <= 0 switches it off */
   double bias_alpha, bias_xb;
+  /* different w_max per species (SI, "Different w_max for different ion species"): the
+   * anion starts (insertion) or ends (deletion) at w_max + 0.5 (sig_c + sig_a) fw and
+   * moves proportionally faster, so both flyers reach w = 0 together; fw = 0: one w_max */
+  double fw;
 } orc_params;
 
 typedef struct {

@@ -86,6 +86,7 @@ class Params(ctypes.Structure):
         ("replica", ctypes.c_uint64),
         ("bias_alpha", ctypes.c_double),
         ("bias_xb", ctypes.c_double),
+        ("fw", ctypes.c_double),
     ]
 
 
@@ -238,6 +239,7 @@ def make_params(cfg: dict, **override) -> Params:
     p.replica = int(c.get("replica", 0))
     p.bias_alpha = float(c.get("bias_alpha", 0.0))
     p.bias_xb = float(c.get("bias_xb", 0.0))
+    p.fw = float(c.get("fw", 0.0))
     return p
 
 

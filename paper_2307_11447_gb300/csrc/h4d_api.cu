@@ -218,6 +218,12 @@ static int check_params(const h4d_params* p) {
   return H4D_OK;
 }
 
+// ratio of the anion's w_max to the cation's: (w_max + 0.5 (sig_c + sig_a) f_w) / w_max
+static double species_rw(const h4d_params& p, double f_w) {
+  if (!(f_w > 0) || !(p.w_max > 0)) return 1.0;
+  return 1.0 + 0.5 * (p.sig[0] + p.sig[1]) * f_w / p.w_max;
+}
+
 static void fill_pot(const h4d_params& p, Pot& P, Proto& pr) {
   std::memset(&P, 0, sizeof(P));
   P.sys = p.system;
@@ -276,6 +282,7 @@ static void fill_pot(const h4d_params& p, Pot& P, Proto& pr) {
   pr.tau_t = p.tau_t;
   pr.beta = p.beta;
   pr.beta_mu = p.beta_mu;
+  pr.rw = 1.0;
 }
 
 // neighbour-row capacity from the densest plausible packing (about one particle per sigma^3
@@ -741,8 +748,18 @@ int h4d_set_protocol(h4d_ctx* c, int32_t n_f, double w_max, double dt, double ka
   c->eng.proto.bias_on = keep.bias_on;
   c->eng.proto.bias_alpha = keep.bias_alpha;
   c->eng.proto.bias_xb = keep.bias_xb;
+  c->eng.proto.fw = keep.fw;
+  c->eng.proto.rw = species_rw(c->prm, keep.fw);
   invalidate_graphs(c);
   return push_plan(c);
+}
+
+int h4d_set_species_wmax(h4d_ctx* c, double f_w) {
+  if (!c || !std::isfinite(f_w) || f_w < 0 || (f_w > 0 && !(c->prm.w_max > 0))) return H4D_EINVAL;
+  c->eng.proto.fw = f_w;
+  c->eng.proto.rw = species_rw(c->prm, f_w);
+  invalidate_graphs(c);
+  return H4D_OK;
 }
 
 int h4d_set_bias(h4d_ctx* c, double alpha_b, double x_b) {

@@ -698,7 +698,10 @@ __device__ void force_pass_impl(const Ctx& c, int mode, float w_prev, double* ki
       }
       if (NEMD && (mode & 4) && iflyer) {
         // protocol work of a flying row: U(w_now) - U(w_prev) against every non-flyer
-        const float go = __expf(-P.kappa_sr * w_prev);
+        // the anion flies rw times higher; screening uses the mean flyer altitude
+        const float rw = (float)e.proto.rw;
+        const float wp_i = (i == fly1) ? rw * w_prev : w_prev;
+        const float go = __expf(-P.kappa_sr * (0.5f * (1.0f + rw) * w_prev));
         for (int s2 = lin; s2 < cnt; s2 += tpa) {
           const int j = e.nbr[nbr_index(e, R, i, s2, ltpa)];
           if (j == fly0 || j == fly1) continue;
@@ -708,7 +711,7 @@ __device__ void force_pass_impl(const Ctx& c, int mode, float w_prev, double* ki
           const float dz = (float)(int)(pj.z - pi.z) * scale;
           const float r3 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
           const float r2n = fmaf(wi, wi, r3);
-          const float r2o = fmaf(w_prev, w_prev, r3);
+          const float r2o = fmaf(wp_i, wp_i, r3);
           const PairCoef<SYS> cf = coef<SYS>(P, ti, type_t<SYS>(j, R.nw3));
           const float un = (r2n < P.rc2_max) ? pair_u32<SYS>(P, cf, r2n, gscr) : 0.0f;
           const float uo = (r2o < P.rc2_max) ? pair_u32<SYS>(P, cf, r2o, go) : 0.0f;
@@ -1662,11 +1665,12 @@ __device__ void trial_phase(const Ctx& c) {
   }
   c.sync();
   const float w0 = (float)altitude(e.proto, ins, 0);
+  const float w0a = (float)(e.proto.rw * altitude(e.proto, ins, 0));  // the anion's altitude
   if (c.tid == 0) {
     if (ins) {
       const int ci = n, ai = n + 1;
       c.v.pos[ci] = make_uint4(S->xfly[0], S->xfly[1], S->xfly[2], __float_as_uint(w0));
-      c.v.pos[ai] = make_uint4(S->xfly[3], S->xfly[4], S->xfly[5], __float_as_uint(w0));
+      c.v.pos[ai] = make_uint4(S->xfly[3], S->xfly[4], S->xfly[5], __float_as_uint(w0a));
       e.vhi[R.atom_off + ci] = make_float4((float)S->vfly[0], (float)S->vfly[1], (float)S->vfly[2], 0.f);
       e.vlo[R.atom_off + ci] = make_float4((float)(S->vfly[0] - (double)(float)S->vfly[0]),
                                            (float)(S->vfly[1] - (double)(float)S->vfly[1]),
@@ -1684,7 +1688,7 @@ __device__ void trial_phase(const Ctx& c) {
       S->n_tot = n;
     }
     S->w_cur = w0;
-    S->g_scr = expf(-e.pot.kappa_sr * w0);
+    S->g_scr = expf(-e.pot.kappa_sr * (0.5f * (w0 + w0a)));
     S->wprot = 0.0;
     S->wprot_c = 0.0;
     S->dW[0] = S->dW[1] = 0.0;
@@ -1705,14 +1709,15 @@ __device__ void trial_phase(const Ctx& c) {
     maybe_rebuild(c);
     const float w_prev = S->w_cur;
     const float w_next = (float)altitude(e.proto, ins, k + 1);
+    const float w_next_a = (float)(e.proto.rw * altitude(e.proto, ins, k + 1));
     if (c.tid == 0) {
       uint4 p0 = c.v.pos[f0], p1 = c.v.pos[f1];
       p0.w = __float_as_uint(w_next);
-      p1.w = __float_as_uint(w_next);
+      p1.w = __float_as_uint(w_next_a);
       c.v.pos[f0] = p0;
       c.v.pos[f1] = p1;
       S->w_cur = w_next;
-      S->g_scr = expf(-e.pot.kappa_sr * w_next);
+      S->g_scr = expf(-e.pot.kappa_sr * (0.5f * (w_next + w_next_a)));
     }
     c.sync();
     force_pass<SYS>(c, 1 | 4, w_prev, nullptr);
@@ -1722,7 +1727,20 @@ __device__ void trial_phase(const Ctx& c) {
       c.sync();
     }
     if (c.tid == 0) {
-      const double y = (S->dW[0] + S->dW[1]) - S->wprot_c;
+      double dff = 0.0;
+      if (e.proto.rw != 1.0) {
+        // the flyers' own pair: unscreened, its altitude gap changes with the step
+        const uint4 a = c.v.pos[f0], b = c.v.pos[f1];
+        const double s = R.L * 0x1.0p-32;
+        const double dx = (double)(int)(b.x - a.x) * s, dy = (double)(int)(b.y - a.y) * s,
+                     dz = (double)(int)(b.z - a.z) * s;
+        const double r3 = dx * dx + dy * dy + dz * dz;
+        const double dn = (double)w_next - (double)w_next_a;
+        const double dp = (double)w_prev - (double)(float)(e.proto.rw * altitude(e.proto, ins, k));
+        const int ta = type_of(f0, c.r.nw3), tb = type_of(f1, c.r.nw3);
+        dff = pair_u64(e.pot, ta, tb, r3 + dn * dn, 1.0) - pair_u64(e.pot, ta, tb, r3 + dp * dp, 1.0);
+      }
+      const double y = (S->dW[0] + S->dW[1] + dff) - S->wprot_c;
       const double t = S->wprot + y;
       S->wprot_c = (t - S->wprot) - y;
       S->wprot = t;

@@ -45,6 +45,8 @@ struct Proto {
   int bias_on;      // bimodal flyer-distance bias (Sec. II.B.3)
   double prop_eps;  // weight of the uniform component of the learned proposal
   double bias_alpha, bias_xb;  // sharpness and mean separation of the bias (Eq. 16)
+  double fw;  // species w_max: the anion's w_max is w_max + 0.5 (sig_c + sig_a) fw
+  double rw;  // its ratio to the cation's (1 = one w_max); the anion's altitude is rw w
 };
 
 struct Rep {

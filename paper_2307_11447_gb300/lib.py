@@ -151,6 +151,7 @@ def lib():
             "h4d_set_protocol": ([vp, i32, d, d, d, i32], i32),
             "h4d_set_no_accept": ([vp, i32], i32),
             "h4d_set_bias": ([vp, d, d], i32),
+            "h4d_set_species_wmax": ([vp, d], i32),
             "h4d_run_md": ([vp, i64], i32),
             "h4d_run_trials": ([vp, i64, i32], i32),
             "h4d_get_counts": ([vp, i32, ctypes.POINTER(h4d_counts)], i32),
@@ -274,6 +275,9 @@ class Context:
 
     def h4d_set_protocol(self, n_f, w_max, dt, kappa_sr, schedule=0):
         _ck(lib().h4d_set_protocol(self.h, n_f, w_max, dt, kappa_sr, schedule), "h4d_set_protocol")
+
+    def h4d_set_species_wmax(self, f_w):
+        _ck(lib().h4d_set_species_wmax(self.h, f_w), "h4d_set_species_wmax")
 
     def h4d_set_bias(self, alpha_b, x_b):
         _ck(lib().h4d_set_bias(self.h, alpha_b, x_b), "h4d_set_bias")

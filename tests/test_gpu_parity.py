@@ -216,3 +216,38 @@ def test_single_trials_with_nonlinear_schedules_match_oracle(sched, n):
             near.append(err)
     assert moves == {0, 1}
     assert np.mean(np.array(near) <= 2e-5) >= 0.5, near
+
+
+def test_single_trials_with_species_wmax_match_oracle():
+    """SI, different w_max per species (f_w = 1: the anion flies 1 sigma higher and faster):
+    single trials against the oracle -- beta dM and the protocol work, which now includes
+    the flyers' own pair, within the trial-work tolerance above"""
+    cfg, x0, v0 = _equilibrated_c0(seed=4)
+    L = cfg["L"]
+    x0 = quantize(x0, L)
+    n_pairs = cfg["n_pairs"]
+    cfg.update(beta_mu=-8.0, n_f=60, fw=1.0, kappa_sr=0.5)
+    po = orc.make_params(cfg, use_cells=0)
+    ctx = h4d.Context(h4d.make_params(cfg), [dict(L=L, n_pairs=n_pairs, cap_pairs=cfg["cap_pairs"], x=x0, v=v0)],
+                      seed=cfg["seed"])
+    ctx.h4d_set_species_wmax(1.0)
+    moves, near = set(), []
+    for k in range(8):
+        ctx.h4d_set_state(0, n_pairs, x0, v0)
+        ctx.h4d_run_trials(1, 0)
+        rg = ctx.h4d_get_work(0, 1)[0]
+        st = orc.State(po, x0, v0, n_pairs, cfg["cap_pairs"])
+        st.s.trial_ctr = k
+        ro = orc.trial(po, st)
+        moves.add(int(ro["move"]))
+        print(f"trial {k}: move {ro['move']} dM diff {rg['beta_dM'] - ro['beta_dM']:+.2e} "
+              f"w_prot gpu {rg['w_prot']:.6f} oracle {ro['w_prot']:.6f}")
+        assert rg["move"] == ro["move"] and rg["status"] == ro["status"] == 0
+        err = abs(rg["beta_dM"] - ro["beta_dM"])
+        bound = 1e-3 if abs(ro["x_acc"]) < 20 else 1e-3 + 1e-3 * abs(ro["beta_dM"])
+        assert err <= bound, (k, rg["beta_dM"], ro["beta_dM"])
+        assert abs(rg["w_prot"] - ro["w_prot"]) <= bound + 1e-4 * abs(ro["w_prot"])
+        if abs(ro["x_acc"]) < 20:
+            near.append(err)
+    assert moves == {0, 1}
+    assert np.mean(np.array(near) <= 2e-5) >= 0.5, near

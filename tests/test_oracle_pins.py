@@ -248,9 +248,11 @@ def test_nve_energy_drift_scales_as_dt_squared():
     assert 3.0 < ratio < 5.3, ratio
 
 
-def test_nemd_is_time_reversible():
-    """Insertion schedule forward, negate momenta, deletion schedule: back to the start."""
-    p, st = _lj_state(12, 6.0, 4, dt=0.003, n_f=60, tau_t=0.1, kappa_sr=0.5)
+@pytest.mark.parametrize("fw", [0.0, 1.0])
+def test_nemd_is_time_reversible(fw):
+    """Insertion schedule forward, negate momenta, deletion schedule: back to the start
+    (also with a different w_max for the anion, fw > 0)."""
+    p, st = _lj_state(12, 6.0, 4, dt=0.003, n_f=60, tau_t=0.1, kappa_sr=0.5, fw=fw)
     orc.md(p, st, 200)
     x0, v0 = st.positions(), st.velocities()
     fly = [4, 7]
@@ -305,3 +307,23 @@ def test_rattle_keeps_water_rigid():
         assert dist(o, h1) == pytest.approx(1.0, abs=1e-7)
         assert dist(o, h2) == pytest.approx(1.0, abs=1e-7)
         assert dist(h1, h2) == pytest.approx(cfg["d_hh"], abs=1e-7)
+
+
+@pytest.mark.parametrize("fw", [0.0, 0.5, 1.0])
+def test_species_wmax_two_flyer_protocol_work_closed_form(fw):
+    """SI, different w_max per species: the anion starts at w_max + 0.5 (sig_c + sig_a) fw
+    and both flyers reach w = 0 together.  With only the two (frozen) flyers in the box the
+    protocol work telescopes to u(r, 0) - u(r, dw0), dw0 = 0.5 (sig_c + sig_a) fw: the
+    flyer-flyer term is the only one, unscreened (both fly), and its altitude gap closes
+    linearly."""
+    cfg = dict(wl.LJ_PHYSICS)
+    cfg.update(L=12.0, n_f=40, fw=fw, kappa_sr=0.7)
+    p = orc.make_params(cfg)
+    x = np.array([[3.0, 3.0, 3.0], [4.4, 3.3, 2.8]])
+    st = orc.State(p, x, None, 1, 1)
+    w, _ = orc.nemd_path(p, st, [0, 1], True)
+    r = float(np.linalg.norm(x[1] - x[0]))
+    dw0 = 0.5 * (cfg["sig"][0] + cfg["sig"][1]) * fw
+    u0, _ = orc.pair(p, 0, 1, r)
+    u1, _ = orc.pair(p, 0, 1, math.sqrt(r * r + dw0 * dw0))
+    assert w == pytest.approx(u0 - u1, abs=1e-12)
