@@ -550,7 +550,7 @@ def _oracle_chain(job):
     return (3 * cfg.get("n_water", 0) + 2 * cfg["n_pairs"]) * n_steps, dt
 
 
-def cpu_baseline(name, sample_steps=8, cores=None):
+def cpu_baseline(name, sample_steps=8, cores=None, one_core=True):
     """The oracle as it stands, one chain per host process (spawned), each running
     sample_steps MD steps of the 4000-ion system (every MD step costs one 4D force
     evaluation like a NEMD step)."""
@@ -565,9 +565,14 @@ def cpu_baseline(name, sample_steps=8, cores=None):
     units = sum(r[0] for r in res)
     busy = max(r[1] for r in res)
     system = "aqueous NaCl system" if name in ("nacl_aq", "nacl_learned") else "4000-ion system"
-    return {"value": units / busy, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"{cores} chains x {sample_steps} MD steps of the {system}, cell list, FP64 "
-                      f"(wall {wall:.1f} s incl. process start)"}
+    out = {"value": units / busy, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
+           "sample": f"{cores} chains x {sample_steps} MD steps of the {system}, cell list, FP64 "
+                     f"(wall {wall:.1f} s incl. process start)"}
+    if one_core and cores > 1:
+        with ctx.Pool(1) as pool:
+            u1, t1 = pool.map(_oracle_chain, [(name, 77, sample_steps)])[0]
+        out["one_core"] = {"value": u1 / t1, "unit": "atom-steps/s", "seconds": t1}
+    return out
 
 
 def run_reference(args):
@@ -576,11 +581,11 @@ def run_reference(args):
         return
     cores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        cpu_baseline(args.workload, sample_steps=1, cores=cores)
+        cpu_baseline(args.workload, sample_steps=1, cores=cores, one_core=False)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(args.workload, sample_steps=2, cores=cores))
+        vals.append(cpu_baseline(args.workload, sample_steps=2, cores=cores, one_core=False))
     secs = time.perf_counter() - t0
     value = float(np.mean([v["value"] for v in vals]))
     out = {
