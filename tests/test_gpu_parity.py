@@ -209,7 +209,8 @@ def test_single_trials_with_nonlinear_schedules_match_oracle(sched, n):
         moves.add(int(ro["move"]))
         assert rg["move"] == ro["move"] and rg["status"] == ro["status"] == 0
         err = abs(rg["beta_dM"] - ro["beta_dM"])
-        assert err <= 0.1, (k, rg["beta_dM"], ro["beta_dM"])
+        bound = 1e-3 if abs(ro["x_acc"]) < 20 else 1e-3 + 1e-3 * abs(ro["beta_dM"])
+        assert err <= bound, (k, rg["beta_dM"], ro["beta_dM"])
         assert abs(rg["w_prot"] - ro["w_prot"]) <= bound
         if abs(ro["x_acc"]) < 20:
             near.append(err)
@@ -243,7 +244,8 @@ def test_single_trials_with_species_wmax_match_oracle():
               f"w_prot gpu {rg['w_prot']:.6f} oracle {ro['w_prot']:.6f}")
         assert rg["move"] == ro["move"] and rg["status"] == ro["status"] == 0
         err = abs(rg["beta_dM"] - ro["beta_dM"])
-        assert err <= 0.1, (k, rg["beta_dM"], ro["beta_dM"])
+        bound = 1e-3 if abs(ro["x_acc"]) < 20 else 1e-3 + 1e-3 * abs(ro["beta_dM"])
+        assert err <= bound, (k, rg["beta_dM"], ro["beta_dM"])
         assert abs(rg["w_prot"] - ro["w_prot"]) <= bound + 1e-4 * abs(ro["w_prot"])
         if abs(ro["x_acc"]) < 20:
             near.append(err)
