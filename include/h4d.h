@@ -120,6 +120,8 @@ typedef struct h4d_counts {
   double t_force_ns;        /* of which: FP32 force passes */
   double t_energy_ns;       /* of which: FP64 end-point energies */
   int64_t threads_per_atom; /* lanes that share one neighbour row in the force pass */
+  int64_t nbr_refreshes;    /* Verlet-row refreshes filtered from the outer rows (between builds) */
+  double t_filter_ns;       /* part of t_build_ns spent filtering Verlet rows from outer rows */
 } h4d_counts;
 
 /* One trial record; Delta M follows the insertion direction (Eqs. 6, 8). */

@@ -9,7 +9,7 @@
  * code, header, table or constant generator with the CUDA library, and the CUDA
  * library never calls it.
  *
- * Conventions (all readings of the paper are listed in the design doc as well):
+ * Conventions (each reading of the paper is stated where it is used):
  *   - atoms [0, 3*n_water) are rigid waters stored O,H,H; ions follow, stored as
  *     interleaved pairs: ion 2k is cation k (type 0), ion 2k+1 is anion k (type 1);
  *     water O is type 2 and H is type 3.

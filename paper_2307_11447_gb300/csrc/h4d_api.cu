@@ -897,6 +897,8 @@ int h4d_get_counts(h4d_ctx* c, int32_t r, h4d_counts* out) {
   out->t_force_ns = R.t_force_ns;
   out->t_energy_ns = R.t_energy_ns;
   out->threads_per_atom = R.tpa;
+  out->nbr_refreshes = R.refreshes;
+  out->t_filter_ns = R.t_filter_ns;
   return H4D_OK;
 }
 
@@ -986,7 +988,7 @@ int h4d_count_pairs(h4d_ctx* c, int64_t* n) {
 }
 
 // ---- checkpoint: a flat binary image of the replica table and per-atom state ----
-static const uint64_t kMagic = 0x3230303044344848ULL;  // "HH4D0002"
+static const uint64_t kMagic = 0x3330303044344848ULL;  // "HH4D0003"
 
 int h4d_save(h4d_ctx* c, const char* path) {
   if (!c || !path) return H4D_EINVAL;

@@ -357,14 +357,24 @@ __device__ void filter_list_impl(const Ctx& c);
 __device__ void build_list(const Ctx& c) {
   const u64 t0 = (c.tid == 0) ? gtimer() : 0;
   build_list_impl(c);
+  const u64 t1 = (c.tid == 0) ? gtimer() : 0;
   filter_list_impl(c);
-  if (c.tid == 0) c.R->t_build_ns += (double)(gtimer() - t0);
+  if (c.tid == 0) {
+    const u64 t2 = gtimer();
+    c.R->t_build_ns += (double)(t2 - t0);
+    c.R->t_filter_ns += (double)(t2 - t1);
+  }
 }
 // Verlet rows only, filtered from the outer rows (valid while the outer list is)
 __device__ void refresh_list(const Ctx& c) {
   const u64 t0 = (c.tid == 0) ? gtimer() : 0;
   filter_list_impl(c);
-  if (c.tid == 0) c.R->t_build_ns += (double)(gtimer() - t0);
+  if (c.tid == 0) {
+    const double dt = (double)(gtimer() - t0);
+    c.R->t_build_ns += dt;
+    c.R->t_filter_ns += dt;
+    c.R->refreshes++;
+  }
 }
 __device__ void build_list_impl(const Ctx& c) {
   const Eng& e = *c.e;

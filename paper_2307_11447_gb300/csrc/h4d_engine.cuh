@@ -75,6 +75,8 @@ struct Rep {
   double sum_n, sum_n2;
   double t_nemd_ns, t_md_ns;
   double t_build_ns, t_force_ns, t_energy_ns;  // phase timers (thread 0 of the group)
+  long long refreshes;  // Verlet-row refreshes from the outer rows (outside full builds)
+  double t_filter_ns;   // part of t_build_ns spent filtering Verlet rows from outer rows
   int dirty;      // state changed on the host: rebuild list and forces
   int prop_G;     // proposal grid cells per edge (0 = no grid)
   int prop_off;   // first cell of this replica in the grid arrays (a multiple of 32)

@@ -94,6 +94,8 @@ class h4d_counts(ctypes.Structure):
         ("t_force_ns", ctypes.c_double),
         ("t_energy_ns", ctypes.c_double),
         ("threads_per_atom", ctypes.c_int64),
+        ("nbr_refreshes", ctypes.c_int64),
+        ("t_filter_ns", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -1,6 +1,6 @@
 """GPU (libh4d, sm_103a) against the FP64 oracle on the same seeded inputs.
 
-Tolerances (written here, derived in the design doc):
+Tolerances (each derived from the arithmetic of the two sides):
   * forces: |F_gpu - F_orc|_i <= 1e-5 (|F_orc|_i + F_rms) per atom (FP32 pair math);
   * potential energy: FP64 on both sides on identical fixed-point positions, rel 1e-10;
   * neighbour sets: bit-exact (integer criterion);

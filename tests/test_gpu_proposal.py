@@ -1,6 +1,6 @@
 """The learned insertion-site proposal on the GPU against the oracle.
 
-Tolerances (written here, derived in the design doc):
+Tolerances (each derived from the arithmetic of the two sides):
   * features: counts bit-exact; field |dE| <= 2e-5 (FP32 contributions summed in fixed
     point on the GPU, FP64 in the oracle);
   * logits against the oracle evaluated in the kernel's precision (bf16 operands, binary32
