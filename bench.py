@@ -235,6 +235,10 @@ def run_gpu(args):
              for k in ("build", "filter", "force", "energy")}
     phase["verlet_filter"] = phase.pop("filter")
     refreshes = sum(b["nbr_refreshes"] - a["nbr_refreshes"] for a, b in zip(c0, c1))
+    # each chain's own device time (its thread 0's timers) against the launch time: the
+    # launch ends with its slowest chain
+    chain_ms = np.array([(b["t_nemd_ns"] - a["t_nemd_ns"] + b["t_md_ns"] - a["t_md_ns"]) / 1e6
+                         for a, b in zip(c0, c1)])
     tmax = t_ms
     tot = np.array([atom_steps, nemd_atom_steps, accepted], np.float64)
     if world > 1:
@@ -287,6 +291,9 @@ def run_gpu(args):
             "md_steps_per_verlet_refresh": (n_eq + n_f) * args.steps * len(c0) / max(builds + refreshes, 1),
             "nemd_time_fraction": nemd_frac,
             "phase_time_fraction": phase,
+            "chain_time_ms": {"min": float(chain_ms.min()), "mean": float(chain_ms.mean()),
+                              "max": float(chain_ms.max()), "cv": float(chain_ms.std() / chain_ms.mean()),
+                              "launch_over_mean_chain": float(t_ms / chain_ms.mean())},
             "autotuned_threads_per_atom": {str(k): v for k, v in sorted(tpa_hist.items())},
             "autotune_us_per_force_pass_and_build": {str(k): [round(a / 1e3, 1), round(b / 1e3, 1)] for k, (a, b) in tune.items()},
             "trials": int(args.chains * world * args.steps),
