@@ -67,6 +67,21 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_over_ranks(t, units, dist=None, device="cuda"):
+    """Whole-job figures of a timed region: the MAX of the ranks' times and the SUM of
+    their units (rank-local values when there is one rank)."""
+    units = np.asarray(units, np.float64)
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(t), units
+    import torch
+
+    tt = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    tv = torch.tensor(units, dtype=torch.float64, device=device)
+    dist.all_reduce(tv)
+    return float(tt.item()), tv.cpu().numpy()
+
+
 def workload(name, chains, rank):
     from paper_2307_11447_gb300 import workloads as wl
 
@@ -239,15 +254,7 @@ def run_gpu(args):
     # launch ends with its slowest chain
     chain_ms = np.array([(b["t_nemd_ns"] - a["t_nemd_ns"] + b["t_md_ns"] - a["t_md_ns"]) / 1e6
                          for a, b in zip(c0, c1)])
-    tmax = t_ms
-    tot = np.array([atom_steps, nemd_atom_steps, accepted], np.float64)
-    if world > 1:
-        tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tmax = float(tt.item())
-        tv = torch.tensor(tot, device="cuda")
-        dist.all_reduce(tv)
-        tot = tv.cpu().numpy()
+    tmax, tot = reduce_over_ranks(t_ms, [atom_steps, nemd_atom_steps, accepted], dist if world > 1 else None)
     secs = tmax / 1e3
     value = tot[0] / secs
     # roofline of the engine kernel: algorithmic FP32 work of the pair term
@@ -502,7 +509,11 @@ def run_e2e(ctx, reps, args, n_eq, n_f, stream, world, dist):
     """Same metric through the public API with host buffers: every step uploads each
     chain's positions and velocities from pinned host memory, runs one cycle and reads the
     counters and trial records back."""
+    import ctypes
+
     import torch
+
+    from paper_2307_11447_gb300.lib import h4d_counts as h4d_counts_t
 
     xs, vs = [], []
     for r in range(ctx.R):
@@ -524,17 +535,12 @@ def run_e2e(ctx, reps, args, n_eq, n_f, stream, world, dist):
         for r in range(ctx.R):
             c = ctx.h4d_get_counts(r)
             rec = ctx.h4d_get_work(r, 1)
-            d2h += 8 * 14 + rec.nbytes
+            d2h += ctypes.sizeof(h4d_counts_t) + rec.nbytes
             atom_steps += (2.0 * c["n_pairs"] + 3.0 * reps[r].get("n_water", 0)) * (n_eq + n_f)
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([secs], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        secs = float(t.item())
-        a = torch.tensor([atom_steps], dtype=torch.float64, device="cuda")
-        dist.all_reduce(a)
-        atom_steps = float(a.item())
+    secs, tot = reduce_over_ranks(secs, [atom_steps], dist)
+    atom_steps = float(tot[0])
     return {"value": atom_steps / secs, "unit": "atom-steps/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h)}
 
@@ -587,6 +593,16 @@ def cpu_baseline(name, sample_steps=8, cores=None, one_core=True):
     return out
 
 
+def reference_config(args, world):
+    """The GPU arm's `config` for the same flags (positions are not needed for it)."""
+    if args.workload == "batched256":
+        cfg, reps = workload(args.workload, args.chains, 0)
+    else:
+        cfg, _ = workload(args.workload, 0, 0)
+        reps = [{}] * args.chains
+    return workload_config(args, cfg, reps, cfg["n_f"], cfg["n_eq"], world)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -614,7 +630,7 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "LJ electrolyte 4000 ions rho=0.3, FP64 CPU oracle, bounded sample per step"},
+        "config": reference_config(args, world),
         "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
                          "sample": vals[-1]["sample"]},
         "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
