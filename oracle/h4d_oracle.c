@@ -294,6 +294,27 @@ static uint32_t fixpt(double x, double L) {
   return (uint32_t)((uint64_t)s & 0xffffffffULL);
 }
 
+/* early rejection: the anion (fixed point Xa) lies in the cube of volume v_ex centred on
+ * the cation (Xc), per axis on the minimum-image fixed-point offset */
+static int in_excluded_volume(const orc_params* p, const uint32_t Xc[3], const uint32_t Xa[3]) {
+  if (!(p->v_ex > 0.0)) return 0;
+  double half = nearbyint(0.5 * cbrt(p->v_ex) / p->L * 4294967296.0);
+  for (int d = 0; d < 3; ++d) {
+    double off = fabs((double)(int32_t)(Xa[d] - Xc[d]));
+    if (!(off <= half)) return 0;
+  }
+  return 1;
+}
+
+int orc_in_excluded_volume(const orc_params* p, const double* xc, const double* xa) {
+  uint32_t Xc[3], Xa[3];
+  for (int d = 0; d < 3; ++d) {
+    Xc[d] = fixpt(xc[d], p->L);
+    Xa[d] = fixpt(xa[d], p->L);
+  }
+  return in_excluded_volume(p, Xc, Xa);
+}
+
 int64_t orc_neighbor_pairs(int n, const double* x, double L, double r_list, int32_t* out_i,
                            int32_t* out_j, int64_t cap) {
   double s = r_list / L * 4294967296.0;
@@ -909,7 +930,9 @@ int orc_trial_prop(const orc_params* p, const orc_proposal* q, orc_state* s, orc
     /* H_start: the N-pair system, flyers absent */
     Ustart = orc_energy_forces(p, n, s->x, NULL, NULL, NULL);
     Kstart = orc_kinetic(p, ntot, s->v, fly);
-    rec->w_prot = nemd(p, ntot, s->x, s->v, fly, 1);
+    /* early rejection: an anion inside the excluded cube is inserted instantaneously */
+    rec->instant = in_excluded_volume(p, X, X + 3);
+    rec->w_prot = rec->instant ? 0.0 : nemd(p, ntot, s->x, s->v, fly, 1);
     /* H_end: the N+1-pair system, everyone in 3D */
     Uend = orc_energy_forces(p, ntot, s->x, NULL, NULL, NULL);
     Kend = orc_kinetic(p, ntot, s->v, fly);
@@ -947,7 +970,14 @@ int orc_trial_prop(const orc_params* p, const orc_proposal* q, orc_state* s, orc
     fly[ci] = fly[ai] = 1;
     Ustart = orc_energy_forces(p, n, s->x, NULL, NULL, NULL);
     Kstart = orc_kinetic(p, n, s->v, fly);
-    rec->w_prot = nemd(p, n, s->x, s->v, fly, 0);
+    /* early rejection: the same cube classifies the pair to delete */
+    uint32_t Xc[3], Xa[3];
+    for (int d = 0; d < 3; ++d) {
+      Xc[d] = fixpt(s->x[3 * ci + d], p->L);
+      Xa[d] = fixpt(s->x[3 * ai + d], p->L);
+    }
+    rec->instant = in_excluded_volume(p, Xc, Xa);
+    rec->w_prot = rec->instant ? 0.0 : nemd(p, n, s->x, s->v, fly, 0);
     /* H_end: the N-1-pair system, flyers absent */
     uint8_t* gone = (uint8_t*)calloc((size_t)n, 1);
     gone[ci] = gone[ai] = 2;

@@ -64,6 +64,14 @@ typedef struct {
    * anion starts (insertion) or ends (deletion) at w_max + 0.5 (sig_c + sig_a) fw and
    * moves proportionally faster, so both flyers reach w = 0 together; fw = 0: one w_max */
   double fw;
+  /* early rejection (SI, "Simple, early rejection scheme"): a cube of volume v_ex
+   * centred on the flying cation.  A pair whose anion lies inside it -- every axis of
+   * the anion's minimum-image fixed-point offset from the cation within
+   * round(0.5 cbrt(v_ex) / L 2^32) -- is exchanged by an instantaneous MC move (no NEMD:
+   * Delta H = Delta U at unchanged velocities); any other pair by NEMD.  The same rule
+   * classifies insertions and deletions, so each pair geometry has one kind of move in
+   * both directions.  v_ex = 0 switches it off. */
+  double v_ex;
 } orc_params;
 
 typedef struct {
@@ -80,7 +88,7 @@ typedef struct {
   int32_t status;     /* 0 ok, 1 deletion from empty system, 2 capacity, 3 non-finite energy */
   int32_t cation, anion;  /* chosen pair (deletion) or -1 */
   int32_t cell_c, cell_a; /* proposal-grid cells of the exchanged cation and anion, or -1 */
-  int32_t pad;
+  int32_t instant;    /* 1: instantaneous move of the early-rejection scheme (no NEMD) */
   double dH;          /* H_end - H_start in energy units */
   double beta_dM;     /* beta * Delta M, insertion-direction convention (Eqs. 6, 8) */
   double w_prot;      /* protocol work sum_k [U(w_{k+1}) - U(w_k)] at fixed positions */
@@ -127,6 +135,10 @@ double orc_nemd_path(const orc_params* p, orc_state* s, const int32_t* flyers, i
 
 /* one H4D pair-exchange trial (Sec. II.A) */
 int orc_trial(const orc_params* p, orc_state* s, orc_record* rec);
+
+/* early rejection: 1 if the anion at xa lies in the excluded cube (volume p->v_ex) centred
+ * on the cation at xc, judged on fixed-point coordinates as in a trial; 0 otherwise */
+int orc_in_excluded_volume(const orc_params* p, const double* xc, const double* xa);
 
 /* n_cycles GCMD cycles: n_eq equilibrium MD steps then one trial (Fig. 1) */
 int orc_run_cycles(const orc_params* p, orc_state* s, int64_t n_cycles, int64_t n_eq,

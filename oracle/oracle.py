@@ -17,6 +17,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "h4d_oracle.c")
+_HDR = os.path.join(_HERE, "h4d_oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 MAXT = 4
@@ -30,7 +31,8 @@ def build(force: bool = False, fp32_forces: bool = False) -> str:
     """Compile the oracle with the host C compiler (no GPU, no CUDA).  fp32_forces builds
     the tolerance-derivation variant whose dynamics use binary32 pair forces."""
     out = _LIB32 if fp32_forces else _LIB
-    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(out) or os.path.getmtime(out) < newest:
         tmp = out + f".tmp{os.getpid()}"
         defs = ["-DORC_FP32_FORCES"] if fp32_forces else []
         subprocess.check_call(
@@ -87,6 +89,7 @@ class Params(ctypes.Structure):
         ("bias_alpha", ctypes.c_double),
         ("bias_xb", ctypes.c_double),
         ("fw", ctypes.c_double),
+        ("v_ex", ctypes.c_double),
     ]
 
 
@@ -112,7 +115,7 @@ RECORD_DTYPE = np.dtype(
         ("anion", np.int32),
         ("cell_c", np.int32),
         ("cell_a", np.int32),
-        ("pad", np.int32),
+        ("instant", np.int32),
         ("dH", np.float64),
         ("beta_dM", np.float64),
         ("w_prot", np.float64),
@@ -195,6 +198,8 @@ def lib():
         _lib.orc_proposal_features.argtypes = [P, ctypes.c_int, ctypes.c_int, pd, ctypes.c_int, ctypes.c_int, pd]
         _lib.orc_proposal_logits.argtypes = [P, Q, ctypes.c_int, pd, ctypes.c_int, ctypes.c_int, pd]
         _lib.orc_trial_prop.argtypes = [P, Q, S, ctypes.c_void_p, pd, pd]
+        _lib.orc_in_excluded_volume.argtypes = [P, pd, pd]
+        _lib.orc_in_excluded_volume.restype = ctypes.c_int
         _lib.orc_run_cycles_prop.argtypes = [P, Q, S, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
     return _lib
 
@@ -240,6 +245,7 @@ def make_params(cfg: dict, **override) -> Params:
     p.bias_alpha = float(c.get("bias_alpha", 0.0))
     p.bias_xb = float(c.get("bias_xb", 0.0))
     p.fw = float(c.get("fw", 0.0))
+    p.v_ex = float(c.get("v_ex", 0.0))
     return p
 
 
@@ -311,6 +317,13 @@ def neighbor_pairs(x: np.ndarray, L: float, r_list: float):
     oj = np.zeros(max(m, 1), np.int32)
     lib().orc_neighbor_pairs(n, _ptr(x), L, r_list, _ptr(oi, ctypes.c_int32), _ptr(oj, ctypes.c_int32), m)
     return oi[:m], oj[:m]
+
+
+def in_excluded_volume(p: Params, xc, xa) -> bool:
+    """early rejection: whether the anion at xa lies in the excluded cube on the cation at xc"""
+    xc = np.ascontiguousarray(xc, np.float64)
+    xa = np.ascontiguousarray(xa, np.float64)
+    return bool(lib().orc_in_excluded_volume(ctypes.byref(p), _ptr(xc), _ptr(xa)))
 
 
 def altitude(p: Params, insertion: bool, k: int) -> float:
