@@ -666,17 +666,17 @@ int h4d_create(const h4d_params* params, const h4d_system* sys, uint64_t seed, v
     std::memset(&R, 0, sizeof(Rep));
     int nw = sys->n_water ? sys->n_water[r] : 0;
     if (nw < 0 || sys->n_pairs[r] < 0 || sys->cap_pairs[r] < sys->n_pairs[r] || !(sys->L[r] > 0)) {
-      delete c;
+      h4d_destroy(c);
       return H4D_EINVAL;
     }
-    if (nw > 0 && params->system != H4D_SYS_AQ) { delete c; return H4D_EINVAL; }
+    if (nw > 0 && params->system != H4D_SYS_AQ) { h4d_destroy(c); return H4D_EINVAL; }
     R.n_water = nw;
     R.nw3 = 3 * nw;
     R.n_pairs = sys->n_pairs[r];
     R.cap_pairs = sys->cap_pairs[r];
     R.cap_atoms = R.nw3 + 2 * R.cap_pairs;
-    if (R.cap_atoms > 65535 || R.cap_atoms < 1) { delete c; return H4D_ECAPACITY; }
-    if (2.0 * (rmax_of(*params) + params->skin) >= sys->L[r]) { delete c; return H4D_EINVAL; }
+    if (R.cap_atoms > 65535 || R.cap_atoms < 1) { h4d_destroy(c); return H4D_ECAPACITY; }
+    if (2.0 * (rmax_of(*params) + params->skin) >= sys->L[r]) { h4d_destroy(c); return H4D_EINVAL; }
     R.atom_off = off;
     off += R.cap_atoms;
     set_rep_geometry(*params, R, sys->L[r]);
@@ -689,7 +689,7 @@ int h4d_create(const h4d_params* params, const h4d_system* sys, uint64_t seed, v
   c->max_nbr = ((c->max_nbr + 127) / 128) * 128;
   c->max_out = std::max(c->max_nbr, derive_max_rows(*params, rmax_of(*params) + outer_skin(*params)));
   rc = make_plan(c);
-  if (rc) { delete c; return rc; }
+  if (rc) { h4d_destroy(c); return rc; }
   rc = alloc_all(c);
   if (rc) { h4d_destroy(c); return rc; }
   fill_eng(c);
