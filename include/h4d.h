@@ -133,7 +133,7 @@ typedef struct h4d_record {
   int32_t cation, anion; /* chosen pair index (deletion), else -1 */
   int32_t cell_c, cell_a; /* proposal-grid cells of the exchanged cation and anion, or -1
                              when no proposal grid is enabled */
-  int32_t pad;
+  int32_t instant;    /* 1: instantaneous move of the early-rejection scheme (no NEMD) */
   double dH;          /* H_end - H_start (energy units, FP64) */
   double beta_dM;     /* beta Delta M */
   double w_prot;      /* protocol work sum_k [U(w_{k+1}) - U(w_k)] (FP32 pairs, FP64 sum) */
@@ -170,6 +170,15 @@ int h4d_set_protocol(h4d_ctx* ctx, int32_t n_f, double w_max, double dt, double 
  * the mode (top bit) on x, y, z; the anion's position words of blocks 1-2 drive the
  * inverse CDF.  Cannot be combined with the learned proposal (H4D_EINVAL). */
 int h4d_set_bias(h4d_ctx* ctx, double alpha_b, double x_b);
+/* Early rejection (SI, "Simple, early rejection scheme"), off by default (v_ex = 0).  A
+ * cube of volume v_ex (length^3) centred on the flying cation: a pair whose anion lies in
+ * it -- every axis of the minimum-image fixed-point offset within
+ * rint(0.5 cbrt(v_ex) / L 2^32) -- is exchanged by an instantaneous MC move (no NEMD
+ * steps: Delta H = Delta U at unchanged velocities, protocol work 0, record field
+ * instant = 1); any other pair by NEMD.  The pair's geometry decides the move type for
+ * insertions (after placement, biased or learned) and deletions alike, so the
+ * acceptance rule is unchanged.  H4D_EINVAL for a negative or non-finite v_ex. */
+int h4d_set_early_rejection(h4d_ctx* ctx, double v_ex);
 /* Different w_max for the two ion species (SI, "Different w_max for different ion
  * species"): the anion flies at w_max + 0.5 (sig_c + sig_a) f_w (sigmas of types 0 and 1)
  * and moves proportionally faster, so both flyers reach (insertion) or leave (deletion)
@@ -277,7 +286,15 @@ int h4d_train_proposal(h4d_ctx* ctx, int64_t steps, int32_t batch, double lr, do
 int h4d_proposal_grad(const double* host_w, int64_t n_rec, const float* host_feat, const float* host_t,
                       double* loss, double* host_grad);
 
-/* ---- checkpoint ---- */
+/* ---- checkpoint ----
+ * h4d_save writes a flat binary image (magic "HH4D0003", seed, replica table, positions,
+ * velocities, trial records) of a context; it synchronises.  h4d_load restores it into a
+ * context created with the same system (replica count, atom capacities, waters, box edges
+ * and ion capacities must match, else H4D_EINVAL and nothing is changed): each chain's
+ * ion count, counters, random-number counters, statistics and records come from the file,
+ * the context keeps its own geometry, thresholds, launch plan, proposal grid and record
+ * rings.  Out-of-range fields (ion count above capacity, negative record count, an
+ * unknown lane count) are rejected.  A resumed chain continues bit-identically. */
 int h4d_save(h4d_ctx* ctx, const char* path);
 int h4d_load(h4d_ctx* ctx, const char* path);
 

@@ -750,6 +750,7 @@ int h4d_set_protocol(h4d_ctx* c, int32_t n_f, double w_max, double dt, double ka
   c->eng.proto.bias_xb = keep.bias_xb;
   c->eng.proto.fw = keep.fw;
   c->eng.proto.rw = species_rw(c->prm, keep.fw);
+  c->eng.proto.vex_edge = keep.vex_edge;
   invalidate_graphs(c);
   return push_plan(c);
 }
@@ -768,6 +769,13 @@ int h4d_set_bias(h4d_ctx* c, double alpha_b, double x_b) {
   c->eng.proto.bias_on = alpha_b > 0 ? 1 : 0;
   c->eng.proto.bias_alpha = alpha_b;
   c->eng.proto.bias_xb = x_b;
+  invalidate_graphs(c);
+  return H4D_OK;
+}
+
+int h4d_set_early_rejection(h4d_ctx* c, double v_ex) {
+  if (!c || !std::isfinite(v_ex) || v_ex < 0) return H4D_EINVAL;
+  c->eng.proto.vex_edge = v_ex > 0 ? std::cbrt(v_ex) : 0.0;
   invalidate_graphs(c);
   return H4D_OK;
 }
@@ -1038,13 +1046,42 @@ int h4d_load(h4d_ctx* c, const char* path) {
   std::fclose(f);
   if (!ok) return H4D_EINVAL;
   for (int r = 0; r < c->R; ++r) {
-    if (reps[r].atom_off != c->rep_h[r].atom_off || reps[r].cap_atoms != c->rep_h[r].cap_atoms) return H4D_EINVAL;
-    // the proposal grid and record rings belong to this context, not to the checkpoint
-    reps[r].prop_G = c->rep_h[r].prop_G;
-    reps[r].prop_off = c->rep_h[r].prop_off;
-    reps[r].prec_off = c->rep_h[r].prec_off;
-    reps[r].prec_cap = c->rep_h[r].prec_cap;
-    reps[r].prec_count = c->rep_h[r].prec_count;
+    const Rep& cur = c->rep_h[r];
+    const Rep& f = reps[r];
+    // a checkpoint of the same system: its layout must be this context's, and the fields
+    // the kernels index with must be in range
+    if (f.atom_off != cur.atom_off || f.cap_atoms != cur.cap_atoms || f.cap_pairs != cur.cap_pairs ||
+        f.n_water != cur.n_water || f.L != cur.L)
+      return H4D_EINVAL;
+    if (f.n_pairs < 0 || f.n_pairs > cur.cap_pairs || f.rec_count < 0) return H4D_EINVAL;
+    if (f.tpa != 1 && f.tpa != 2 && f.tpa != 4 && f.tpa != 8 && f.tpa != 16) return H4D_EINVAL;
+    // only the chain's state and statistics come from the file; geometry, thresholds,
+    // offsets, the proposal grid and the record rings stay this context's
+    Rep m = cur;
+    m.n_pairs = f.n_pairs;
+    m.tpa = f.tpa;
+    m.rec_count = f.rec_count;
+    m.trial_ctr = f.trial_ctr;
+    m.step_ctr = f.step_ctr;
+    m.cycles = f.cycles;
+    m.trials_ins = f.trials_ins;
+    m.trials_del = f.trials_del;
+    m.acc_ins = f.acc_ins;
+    m.acc_del = f.acc_del;
+    m.rej_status = f.rej_status;
+    m.md_steps = f.md_steps;
+    m.builds = f.builds;
+    m.refreshes = f.refreshes;
+    m.err = f.err;
+    m.sum_n = f.sum_n;
+    m.sum_n2 = f.sum_n2;
+    m.t_nemd_ns = f.t_nemd_ns;
+    m.t_md_ns = f.t_md_ns;
+    m.t_build_ns = f.t_build_ns;
+    m.t_force_ns = f.t_force_ns;
+    m.t_energy_ns = f.t_energy_ns;
+    m.t_filter_ns = f.t_filter_ns;
+    reps[r] = m;
   }
   c->seed = hdr[3];
   c->eng.seed = hdr[3];

@@ -171,7 +171,7 @@ struct GScal {
   int flag_rebuild, flag_overflow, flag_nan, n_tot;
   int fly0, fly1, ins, status;
   int flip_s, flip_e, cat, ani;
-  int n_before, accept, pad0, pad1;
+  int n_before, accept, inst, pad1;  // inst: instantaneous move (early rejection)
   float w_cur, g_scr, pad2, pad3;
   double alpha_th, dW[2], wprot, wprot_c, red_out;
   double ln_u, ustart, kstart, uend, kend;
@@ -1624,7 +1624,7 @@ __device__ void trial_phase(const Ctx& c) {
     if (c.tid == 0) {
       h4d_record rr;
       rr.move = ins; rr.accepted = 0; rr.n_before = N; rr.n_after = N; rr.status = S->status;
-      rr.cation = -1; rr.anion = -1; rr.cell_c = -1; rr.cell_a = -1; rr.pad = 0;
+      rr.cation = -1; rr.anion = -1; rr.cell_c = -1; rr.cell_a = -1; rr.instant = 0;
       rr.dH = 0.0; rr.beta_dM = 0.0; rr.w_prot = 0.0; rr.ln_u = S->ln_u; rr.x_acc = 0.0; rr.ln_q = 0.0;
       e.rec[R.rec_off + (int)(R.rec_count % R.rec_cap)] = rr;
       R.rec_count++;
@@ -1666,6 +1666,28 @@ __device__ void trial_phase(const Ctx& c) {
     c.sync();
     if (S->prec_slot >= 0) prop_record_features(c, pv, S->prec_slot, S->cell_c, S->cell_a);
   }
+  // early rejection (SI): a pair whose anion lies in the cube of edge vex_edge around the
+  // cation, per axis on the minimum-image fixed-point offset, is exchanged by an
+  // instantaneous move (no NEMD steps); the same rule classifies both directions
+  if (c.tid == 0) {
+    int inst = 0;
+    if (e.proto.vex_edge > 0.0) {
+      uint4 pc, pa;
+      if (ins) {
+        pc = make_uint4(S->xfly[0], S->xfly[1], S->xfly[2], 0u);
+        pa = make_uint4(S->xfly[3], S->xfly[4], S->xfly[5], 0u);
+      } else {
+        pc = c.v.pos[R.nw3 + 2 * S->cat];
+        pa = c.v.pos[R.nw3 + 2 * S->ani + 1];
+      }
+      const double half = rint(0.5 * e.proto.vex_edge / R.L * 4294967296.0);
+      inst = fabs((double)(int)(pa.x - pc.x)) <= half && fabs((double)(int)(pa.y - pc.y)) <= half &&
+             fabs((double)(int)(pa.z - pc.z)) <= half;
+    }
+    S->inst = inst;
+  }
+  c.sync();
+  const bool inst = S->inst != 0;
   // save the state for a rejection (positions from shared memory, velocities)
   for (int a = c.tid; a < n; a += c.T) {
     const int ga = R.atom_off + a;
@@ -1674,8 +1696,9 @@ __device__ void trial_phase(const Ctx& c) {
     e.vlo_save[ga] = e.vlo[ga];
   }
   c.sync();
-  const float w0 = (float)altitude(e.proto, ins, 0);
-  const float w0a = (float)(e.proto.rw * altitude(e.proto, ins, 0));  // the anion's altitude
+  // an instantaneous move keeps the flyers in 3D throughout
+  const float w0 = inst ? 0.f : (float)altitude(e.proto, ins, 0);
+  const float w0a = inst ? 0.f : (float)(e.proto.rw * altitude(e.proto, ins, 0));  // the anion's altitude
   if (c.tid == 0) {
     if (ins) {
       const int ci = n, ai = n + 1;
@@ -1711,9 +1734,12 @@ __device__ void trial_phase(const Ctx& c) {
   // H_start: insertion leaves the flyers out, deletion has everyone in 3D
   const double Us = ins ? energy64(c, f0, f1) : energy64(c, -1, -1);
   const double Ks = kinetic64(c);
-  force_pass<SYS>(c, 0, 0.f, nullptr);
-  c.sync();
-  for (int k = 0; k < e.proto.n_f; ++k) {
+  const int n_steps = inst ? 0 : e.proto.n_f;
+  if (n_steps > 0) {
+    force_pass<SYS>(c, 0, 0.f, nullptr);
+    c.sync();
+  }
+  for (int k = 0; k < n_steps; ++k) {
     kick_drift<SYS>(c, 1.0f);
     c.sync();
     maybe_rebuild(c);
@@ -1805,7 +1831,7 @@ __device__ void trial_phase(const Ctx& c) {
     rr.n_after = N + (acc ? (ins ? 1 : -1) : 0);
     rr.status = status;
     rr.cation = ins ? -1 : S->cat; rr.anion = ins ? -1 : S->ani;
-    rr.cell_c = S->cell_c; rr.cell_a = S->cell_a; rr.pad = 0;
+    rr.cell_c = S->cell_c; rr.cell_a = S->cell_a; rr.instant = S->inst;
     rr.dH = dH; rr.beta_dM = bdm; rr.w_prot = S->wprot; rr.ln_u = S->ln_u; rr.x_acc = xacc; rr.ln_q = S->lnq;
     if (S->prec_slot >= 0) {
       const int gi = R.prec_off + S->prec_slot;

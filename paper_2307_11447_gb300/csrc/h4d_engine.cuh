@@ -47,6 +47,7 @@ struct Proto {
   double bias_alpha, bias_xb;  // sharpness and mean separation of the bias (Eq. 16)
   double fw;  // species w_max: the anion's w_max is w_max + 0.5 (sig_c + sig_a) fw
   double rw;  // its ratio to the cation's (1 = one w_max); the anion's altitude is rw w
+  double vex_edge;  // early rejection: edge of the excluded cube around the flying cation (0 = off)
 };
 
 struct Rep {

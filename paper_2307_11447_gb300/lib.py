@@ -113,7 +113,7 @@ RECORD_DTYPE = np.dtype(
         ("anion", np.int32),
         ("cell_c", np.int32),
         ("cell_a", np.int32),
-        ("pad", np.int32),
+        ("instant", np.int32),
         ("dH", np.float64),
         ("beta_dM", np.float64),
         ("w_prot", np.float64),
@@ -153,6 +153,7 @@ def lib():
             "h4d_set_protocol": ([vp, i32, d, d, d, i32], i32),
             "h4d_set_no_accept": ([vp, i32], i32),
             "h4d_set_bias": ([vp, d, d], i32),
+            "h4d_set_early_rejection": ([vp, d], i32),
             "h4d_set_species_wmax": ([vp, d], i32),
             "h4d_run_md": ([vp, i64], i32),
             "h4d_run_trials": ([vp, i64, i32], i32),
@@ -283,6 +284,9 @@ class Context:
 
     def h4d_set_bias(self, alpha_b, x_b):
         _ck(lib().h4d_set_bias(self.h, alpha_b, x_b), "h4d_set_bias")
+
+    def h4d_set_early_rejection(self, v_ex):
+        _ck(lib().h4d_set_early_rejection(self.h, v_ex), "h4d_set_early_rejection")
 
     def h4d_set_no_accept(self, on):
         _ck(lib().h4d_set_no_accept(self.h, int(on)), "h4d_set_no_accept")
