@@ -25,9 +25,11 @@
  *   - Pointers named host_* are host memory; the library copies from or into them and
  *     never keeps them.  Pointers named dev_* are device memory owned by the caller.
  *     All other device memory is owned by the context and freed by h4d_destroy().
- *   - Each context issues its work on the CUDA stream given at creation (NULL = the
- *     legacy default stream).  Launching entry points return when the work is queued;
- *     getters synchronise the stream before they return.
+ *   - Each context issues its work on the CUDA stream given at creation; with NULL the
+ *     context creates a non-blocking stream of its own (CUDA-graph capture cannot use
+ *     the legacy default stream) and destroys it in h4d_destroy().  Launching entry
+ *     points return when the work is queued; getters synchronise the stream before they
+ *     return.
  *   - Atom layout inside a replica: atoms [0, 3*n_water) are rigid waters stored as
  *     O,H,H; ions follow as interleaved pairs, ion 2k = cation k (type 0) and ion 2k+1 =
  *     anion k (type 1).  Water O is type 2 and H is type 3.  Positions are Cartesian in
@@ -88,7 +90,7 @@ typedef struct h4d_params {
                              a Verlet refresh rebuilds both lists once the two largest
                              displacements since the outer build exceed skin_outer - skin */
   int32_t max_nbr;        /* neighbour-row capacity per atom; 0 = derived from density */
-  int32_t threads_per_atom; /* 1,2,4,8,16 or 32; 0 = autotune per replica size */
+  int32_t threads_per_atom; /* 1,2,4,8,16 or 32; 0 = chosen per replica size (h4d_autotune measures) */
 } h4d_params;
 
 /* Initial replicas.  Replica r holds 3*n_water[r] + 2*n_pairs[r] atoms; host_x (and
@@ -147,8 +149,10 @@ typedef struct h4d_record {
 /* ---- context lifetime ---- */
 
 /* Create a context: copies params and the initial replicas to the device, sizes every
- * buffer for cap_pairs, autotunes the launch shape when threads_per_atom == 0.
- * seed keys the random stream.  cuda_stream is a cudaStream_t (NULL = default). */
+ * buffer for cap_pairs, picks the lanes per neighbour row by replica size when
+ * threads_per_atom == 0 (h4d_autotune then measures and keeps the fastest).
+ * seed keys the random stream.  cuda_stream is a cudaStream_t (NULL = a stream the context
+ * creates and owns). */
 int h4d_create(const h4d_params* params, const h4d_system* sys, uint64_t seed, void* cuda_stream,
                h4d_ctx** out);
 void h4d_destroy(h4d_ctx* ctx);
@@ -294,7 +298,7 @@ int h4d_proposal_grad(const double* host_w, int64_t n_rec, const float* host_fea
  * ion count, counters, random-number counters, statistics and records come from the file,
  * the context keeps its own geometry, thresholds, launch plan, proposal grid and record
  * rings.  Out-of-range fields (ion count above capacity, negative record count, an
- * unknown lane count) are rejected.  A resumed chain continues bit-identically. */
+ * lane count that is not a power of two up to 32) are rejected.  A resumed chain continues bit-identically. */
 int h4d_save(h4d_ctx* ctx, const char* path);
 int h4d_load(h4d_ctx* ctx, const char* path);
 

@@ -1054,7 +1054,7 @@ int h4d_load(h4d_ctx* c, const char* path) {
         f.n_water != cur.n_water || f.L != cur.L)
       return H4D_EINVAL;
     if (f.n_pairs < 0 || f.n_pairs > cur.cap_pairs || f.rec_count < 0) return H4D_EINVAL;
-    if (f.tpa != 1 && f.tpa != 2 && f.tpa != 4 && f.tpa != 8 && f.tpa != 16) return H4D_EINVAL;
+    if (f.tpa < 1 || f.tpa > 32 || (f.tpa & (f.tpa - 1))) return H4D_EINVAL;  // lanes per row: 1..32, a power of two
     // only the chain's state and statistics come from the file; geometry, thresholds,
     // offsets, the proposal grid and the record rings stay this context's
     Rep m = cur;
