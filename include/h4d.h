@@ -158,8 +158,14 @@ int h4d_create(const h4d_params* params, const h4d_system* sys, uint64_t seed, v
 void h4d_destroy(h4d_ctx* ctx);
 const char* h4d_strerror(int code);
 
-/* ---- settings ---- */
+/* ---- settings (each applies from the next launch) ---- */
+/* beta mu of the ion pair in the acceptance exponents of Eqs. 6 and 8 (Lambda_s = 1);
+ * H4D_EINVAL when not finite. */
 int h4d_set_mu(h4d_ctx* ctx, double beta_mu);
+/* NEMD protocol (Sec. II.A): n_f >= 1 steps of length dt > 0 between w_max >= 0 and 0 on
+ * the schedule H4D_SCHED_* (Eq. 2, Eqs. S6-S7), screening kappa_sr >= 0 (Eq. 11);
+ * H4D_EINVAL otherwise.  The bias, proposal, species w_max, early-rejection and no-accept
+ * settings are kept; synchronises the stream. */
 int h4d_set_protocol(h4d_ctx* ctx, int32_t n_f, double w_max, double dt, double kappa_sr,
                      int32_t schedule);
 /* Bimodal flyer-distance bias (Sec. II.B.3, Eqs. 14-18), off by default (alpha_b = 0).
@@ -221,7 +227,10 @@ int h4d_get_work(h4d_ctx* ctx, int32_t replica, h4d_record* host_rec, int64_t ca
  * fails with H4D_ECAPACITY when cap_atoms is too small */
 int h4d_get_state(h4d_ctx* ctx, int32_t replica, double* host_x, double* host_v,
                   int64_t cap_atoms, int64_t* n_atoms);
-/* overwrite a replica's state (n_pairs ion pairs, positions and velocities) */
+/* overwrite a replica's state: n_pairs ion pairs, host_x [3*n_water + 2*n_pairs][3]
+ * (wrapped into [0, L)), host_v of the same shape or NULL (Maxwell-Boltzmann draw);
+ * H4D_EINVAL for a bad replica or NULL host_x, H4D_ECAPACITY when n_pairs is negative or
+ * above the replica's cap_pairs.  Neighbour rows are rebuilt at the next launch. */
 int h4d_set_state(h4d_ctx* ctx, int32_t replica, int32_t n_pairs, const double* host_x,
                   const double* host_v);
 int32_t h4d_num_replicas(h4d_ctx* ctx);
