@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--sequential", type=int, default=0,
                     help="batched workload: also time this many replicas run one at a time (alone on the GPU)")
     ap.add_argument("--workload", default="lj4000")
+    ap.add_argument("--cpu-cores", type=int, default=None,
+                    help="host processes for the oracle legs (default: every host core)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--equil", type=int, default=1000)
     ap.add_argument("--n-eq", type=int, default=None, help="override equilibrium steps per cycle (profiling)")
@@ -319,7 +321,7 @@ def run_gpu(args):
             out["sequential_one_replica_at_a_time"] = seq
             out["batched_over_sequential"] = value / seq["value"]
         if rank == 0 and os.environ.get("H4D_BENCH_CPU", "1") == "1":
-            out["cpu_baseline"] = cpu_baseline(args.workload, sample_steps=60)
+            out["cpu_baseline"] = cpu_baseline(args.workload, sample_steps=60, cores=args.cpu_cores)
         print(json.dumps(out), flush=True)
     ctx.close()
     if world > 1:
@@ -607,7 +609,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    cores = os.cpu_count() or 1
+    cores = args.cpu_cores or os.cpu_count() or 1
     for _ in range(args.warmup):
         cpu_baseline(args.workload, sample_steps=1, cores=cores, one_core=False)
     vals = []
