@@ -1,5 +1,6 @@
-"""The CSVR thermostat of the oracle's equilibrium MD (Bussi, Donadio and Parrinello 2007;
-the paper leaves the NVT thermostat open, the reading taken is CSVR).
+"""Thermal velocities in the oracle: the CSVR thermostat of equilibrium MD (Bussi, Donadio
+and Parrinello 2007; the paper leaves the NVT thermostat open, the reading taken is CSVR)
+and the Maxwell-Boltzmann draws of the initial velocities and of inserted ions (Sec. II.A).
 
 Pin: without forces the thermostat alone must sample the canonical kinetic energy, K ~
 Gamma(dof/2, k_B T) with dof = 3 n (no constraints): mean dof/2 kT, variance dof/2 (kT)^2,
@@ -50,3 +51,46 @@ def test_csvr_samples_the_canonical_kinetic_energy():
     orc.init_velocities(p, st2)
     orc.md(p, st2, 200 + K.size)
     assert math.isclose(orc.kinetic(p, st2.velocities()), K[-1], rel_tol=1e-12)
+
+
+def test_initial_velocities_are_maxwell_boltzmann_per_species():
+    """orc_init_velocities (Sec. II.A): every Cartesian component of an atom of mass m is
+    N(0, kT/m); checked per species with unequal masses"""
+    n_pairs = 2000
+    cfg = dict(wl.LJ_PHYSICS)
+    cfg.update(L=60.0, n_f=1, mass=[1.0, 3.5], beta=0.8, seed=12, replica=1)
+    p = orc.make_params(cfg)
+    x = np.random.default_rng(1).random((2 * n_pairs, 3)) * cfg["L"]
+    st = orc.State(p, x, None, n_pairs, n_pairs)
+    orc.init_velocities(p, st)
+    v = st.velocities()
+    for t, m in enumerate(cfg["mass"]):
+        z = (v[t::2] * math.sqrt(m * cfg["beta"])).ravel()
+        ks = stats.kstest(z, stats.norm.cdf)
+        assert ks.pvalue > 1e-3, (t, ks)
+        assert abs(z.mean()) < 4 / math.sqrt(z.size)
+
+
+def test_inserted_ions_carry_maxwell_boltzmann_velocities():
+    """the flyers' velocities drawn at an insertion (trial blocks 3-4) and kept on
+    acceptance: per species N(0, kT/m) over many accepted insertions of an ideal pair gas"""
+    cfg = dict(wl.LJ_PHYSICS)
+    cfg.update(L=10.0, n_f=1, q=[0.0, 0.0], eps=[0.0, 0.0], mass=[2.0, 0.5], beta=1.0,
+               beta_mu=math.log(1e4 / 1e6), seed=6, replica=2)
+    p = orc.make_params(cfg)
+    cap = 400
+    st = orc.State(p, np.random.default_rng(2).random((2 * cap, 3)) * cfg["L"], None, 0, cap)
+    orc.init_velocities(p, st)
+    vc, va = [], []
+    for _ in range(3000):
+        n0 = st.n_pairs
+        r = orc.trial(p, st)
+        if r["move"] == 1 and r["accepted"]:
+            v = st.velocities()
+            vc.append(v[2 * n0].copy())
+            va.append(v[2 * n0 + 1].copy())
+    assert len(vc) > 300
+    for vs, m in ((vc, cfg["mass"][0]), (va, cfg["mass"][1])):
+        z = (np.array(vs) * math.sqrt(m * cfg["beta"])).ravel()
+        ks = stats.kstest(z, stats.norm.cdf)
+        assert ks.pvalue > 1e-3, (m, ks)
