@@ -94,3 +94,38 @@ def test_inserted_ions_carry_maxwell_boltzmann_velocities():
         z = (np.array(vs) * math.sqrt(m * cfg["beta"])).ravel()
         ks = stats.kstest(z, stats.norm.cdf)
         assert ks.pvalue > 1e-3, (m, ks)
+
+
+def test_rigid_water_velocities_are_equipartitioned():
+    """orc_init_velocities on rigid waters: Maxwell-Boltzmann draws with the bond-parallel
+    components removed (the RATTLE projection, mass-weighted) leave each molecule with
+    3/2 kT of translational and 3/2 kT of rotational kinetic energy on average, and the
+    constraints satisfied"""
+    cfg = dict(wl.AQ_PHYSICS)
+    nw, L = 400, 30.0
+    x = wl.aqueous_positions(nw, 0, L, 5)
+    kT = 1.0 / cfg["beta"]
+    m = np.array(cfg["mass"])[[2, 3, 3]]
+    kt, kr = [], []
+    for seed in range(20):
+        c = dict(cfg)
+        c.update(L=L, n_water=nw, n_f=1, seed=seed, replica=0)
+        p = orc.make_params(c)
+        st = orc.State(p, x, None, 0, 1)
+        orc.init_velocities(p, st)
+        v = st.velocities().reshape(nw, 3, 3)
+        M = m.sum()
+        V = (v * m[None, :, None]).sum(1) / M
+        k_t = 0.5 * M * (V**2).sum(1) * cfg["mvv2e"]
+        k = 0.5 * (m[None, :, None] * v**2).sum((1, 2)) * cfg["mvv2e"]
+        kt.append(k_t)
+        kr.append(k - k_t)
+        # rigid: every bond's relative velocity is perpendicular to the bond
+        xm = x.reshape(nw, 3, 3)
+        for a, b in ((0, 1), (0, 2), (1, 2)):
+            d = xm[:, b] - xm[:, a]
+            dv = v[:, b] - v[:, a]
+            assert np.abs((d * dv).sum(1)).max() < 1e-9 * np.abs(dv).max()
+    kt, kr = np.concatenate(kt) / kT, np.concatenate(kr) / kT
+    for k in (kt, kr):
+        assert abs(k.mean() - 1.5) < 4 * math.sqrt(1.5 / k.size), (kt.mean(), kr.mean())
