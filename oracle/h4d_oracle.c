@@ -78,6 +78,7 @@ static double gauss_sin(uint64_t ra, uint64_t rb) {
 int orc_atom_type(const orc_params* p, int a) {
   int nsolv = 3 * p->n_water;
   if (a < nsolv) return (a % 3 == 0) ? 2 : 3;
+  if (p->single) return 0; /* single-particle exchange: one species */
   return (a - nsolv) & 1;
 }
 
@@ -473,7 +474,8 @@ static void vv_step(const orc_params* p, int n, double* x, double* v, double* F,
   if (p->n_water) rattle_v(p, x, v);
 }
 
-static int n_atoms(const orc_params* p, int n_pairs) { return 3 * p->n_water + 2 * n_pairs; }
+/* atoms of a state with n_pairs exchange units: ion pairs, or particles in single mode */
+static int n_atoms(const orc_params* p, int n_pairs) { return 3 * p->n_water + (p->single ? 1 : 2) * n_pairs; }
 
 double orc_nve(const orc_params* p, orc_state* s, int64_t n_steps, double* e_trace) {
   int n = n_atoms(p, s->n_pairs);
@@ -825,8 +827,11 @@ static void flip_all(double* v, int n) {
  * flyers' kinetic energy is left out: insertion draws it from Maxwell-Boltzmann and a
  * deletion discards it, so it cancels against the e^{-beta K}/N_k factors of Eqs. 3-4.
  */
+static int trial_single(const orc_params* p, orc_state* s, orc_record* rec);
+
 int orc_trial_prop(const orc_params* p, const orc_proposal* q, orc_state* s, orc_record* rec,
                    double* site_feat, double* site_y) {
+  if (p->single) return trial_single(p, s, rec); /* no proposal, bias or early rejection */
   uint64_t t = s->trial_ctr++;
   uint64_t b0[4], b1[4], b2[4], b3[4], b4[4], b5[4], b6[4];
   draw(p, t, 0, ORC_PUR_TRIAL, b0);
@@ -1024,7 +1029,7 @@ int orc_trial_prop(const orc_params* p, const orc_proposal* q, orc_state* s, orc
   x_acc += insertion ? -ln_q : ln_q;
   rec->ln_q = ln_q;
   rec->x_acc = x_acc;
-  int accept = isfinite(dH) && (ln_u < x_acc);
+  int accept = isfinite(dH) && (ln_u < x_acc) && !p->no_accept;
   if (!isfinite(dH)) rec->status = 3;
   if (accept) {
     if (insertion) {
@@ -1051,6 +1056,118 @@ int orc_trial_prop(const orc_params* p, const orc_proposal* q, orc_state* s, orc
   free(vs);
   free(fly);
   free(w0);
+  return 0;
+}
+
+/* Single-particle exchange (Sec. II.A: the Metropolis rule of Eqs. 3-8 translated to one
+ * flying particle; the flyer keeps its 3D position, Sec. II.B.1).  Draw table (counter
+ * {t, block, TRIAL, 0}):
+ *   block 0: as for pairs ([0] insertion, [1] and [2] the two reversals, [3] the uniform)
+ *   block 1: insertion: [0..2] x, y, z as 32-bit box fractions; deletion: [0] the particle
+ *   block 3: Maxwell-Boltzmann velocity of the inserted particle ([0],[1] cos and sin, [2],[3] cos)
+ * With one flyer the phase-space factor of Eqs. 3-4 appears once: insertion
+ * beta dM = beta dH - ln(V/(N+1)), accepted iff ln u < -beta dM + beta mu; deletion
+ * beta dM = -beta dH - ln(V/N), accepted iff ln u < beta dM - beta mu (Lambda = 1).
+ * Delta H and the momentum reversals follow the readings of the pair trial. */
+static int trial_single(const orc_params* p, orc_state* s, orc_record* rec) {
+  uint64_t t = s->trial_ctr++;
+  uint64_t b0[4], b1[4], b3[4];
+  draw(p, t, 0, ORC_PUR_TRIAL, b0);
+  draw(p, t, 1, ORC_PUR_TRIAL, b1);
+  draw(p, t, 3, ORC_PUR_TRIAL, b3);
+  int insertion = (int)(b0[0] >> 63);
+  int flip_start = (int)(b0[1] >> 63), flip_end = (int)(b0[2] >> 63);
+  double ln_u = log(u01_open(b0[3]));
+  int N = s->n_pairs;
+  int base = 3 * p->n_water;
+  int n = n_atoms(p, N);
+  double V = p->L * p->L * p->L;
+
+  memset(rec, 0, sizeof(*rec));
+  rec->move = insertion;
+  rec->n_before = N;
+  rec->n_after = N;
+  rec->cation = rec->anion = -1;
+  rec->cell_c = rec->cell_a = -1;
+  rec->ln_u = ln_u;
+  if (flip_start) flip_all(s->v, n);
+  if ((!insertion && N == 0) || (insertion && N >= s->cap_pairs)) {
+    rec->status = insertion ? 2 : 1;
+    if (flip_end) flip_all(s->v, n);
+    return 0;
+  }
+  int ntot = insertion ? n + 1 : n;
+  double* xs = (double*)malloc(sizeof(double) * 3 * (size_t)ntot);
+  double* vs = (double*)malloc(sizeof(double) * 3 * (size_t)ntot);
+  memcpy(xs, s->x, sizeof(double) * 3 * (size_t)n);
+  memcpy(vs, s->v, sizeof(double) * 3 * (size_t)n);
+  uint8_t* fly = (uint8_t*)calloc((size_t)ntot, 1);
+  double Ustart, Uend, Kstart, Kend;
+  int fi;
+  if (insertion) {
+    fi = n;
+    double h = p->L / 4294967296.0;
+    for (int d = 0; d < 3; ++d) s->x[3 * fi + d] = (double)(uint32_t)(b1[d] >> 32) * h;
+    double sd = sqrt(1.0 / (p->beta * p->mass[0] * p->mvv2e));
+    s->v[3 * fi + 0] = sd * gauss_cos(b3[0], b3[1]);
+    s->v[3 * fi + 1] = sd * gauss_sin(b3[0], b3[1]);
+    s->v[3 * fi + 2] = sd * gauss_cos(b3[2], b3[3]);
+    fly[fi] = 1;
+    /* H_start: the N-particle system, flyer absent; H_end: N + 1 particles in 3D */
+    Ustart = orc_energy_forces(p, n, s->x, NULL, NULL, NULL);
+    Kstart = orc_kinetic(p, ntot, s->v, fly);
+    rec->w_prot = nemd(p, ntot, s->x, s->v, fly, 1);
+    Uend = orc_energy_forces(p, ntot, s->x, NULL, NULL, NULL);
+    Kend = orc_kinetic(p, ntot, s->v, fly);
+  } else {
+    int k = pick(b1[0], N);
+    fi = base + k;
+    rec->cation = k;
+    fly[fi] = 1;
+    Ustart = orc_energy_forces(p, n, s->x, NULL, NULL, NULL);
+    Kstart = orc_kinetic(p, n, s->v, fly);
+    rec->w_prot = nemd(p, n, s->x, s->v, fly, 0);
+    /* H_end: the N - 1-particle system, flyer absent */
+    uint8_t* gone = (uint8_t*)calloc((size_t)n, 1);
+    gone[fi] = 2;
+    Uend = orc_energy_forces(p, n, s->x, NULL, gone, NULL);
+    Kend = orc_kinetic(p, n, s->v, fly);
+    free(gone);
+  }
+  double dH = (Uend + Kend) - (Ustart + Kstart);
+  rec->dH = dH;
+  double x_acc;
+  if (insertion) {
+    rec->beta_dM = p->beta * dH - log(V / (double)(N + 1));
+    x_acc = -rec->beta_dM + p->beta_mu;
+  } else {
+    rec->beta_dM = -p->beta * dH - log(V / (double)N);
+    x_acc = rec->beta_dM - p->beta_mu;
+  }
+  rec->x_acc = x_acc;
+  int accept = isfinite(dH) && (ln_u < x_acc) && !p->no_accept;
+  if (!isfinite(dH)) rec->status = 3;
+  if (accept) {
+    if (insertion) {
+      s->n_pairs = N + 1;
+    } else {
+      int last = base + N - 1; /* swap-with-last removal */
+      for (int d = 0; d < 3; ++d) {
+        s->x[3 * fi + d] = s->x[3 * last + d];
+        s->v[3 * fi + d] = s->v[3 * last + d];
+      }
+      s->n_pairs = N - 1;
+    }
+  } else {
+    memcpy(s->x, xs, sizeof(double) * 3 * (size_t)n);
+    memcpy(s->v, vs, sizeof(double) * 3 * (size_t)n);
+  }
+  rec->accepted = accept;
+  rec->n_after = s->n_pairs;
+  if (flip_end) flip_all(s->v, n_atoms(p, s->n_pairs));
+  free(xs);
+  free(vs);
+  free(fly);
   return 0;
 }
 

@@ -72,6 +72,13 @@ typedef struct {
    * classifies insertions and deletions, so each pair geometry has one kind of move in
    * both directions.  v_ex = 0 switches it off. */
   double v_ex;
+  /* fixed-N work sampling (Sec. II.E, SI Sec. S1): trials run and are recorded but none
+   * is accepted, so the work distributions are sampled at fixed particle numbers */
+  int32_t no_accept;
+  /* single-particle exchange (Sec. II.A: the pair rule translated to one flying
+   * particle): every atom after the waters is one species of type 0, and a trial inserts
+   * or deletes one of them; n_pairs and cap_pairs of the state count particles */
+  int32_t single;
 } orc_params;
 
 typedef struct {

@@ -90,6 +90,8 @@ class Params(ctypes.Structure):
         ("bias_xb", ctypes.c_double),
         ("fw", ctypes.c_double),
         ("v_ex", ctypes.c_double),
+        ("no_accept", ctypes.c_int32),
+        ("single", ctypes.c_int32),
     ]
 
 
@@ -246,17 +248,21 @@ def make_params(cfg: dict, **override) -> Params:
     p.bias_xb = float(c.get("bias_xb", 0.0))
     p.fw = float(c.get("fw", 0.0))
     p.v_ex = float(c.get("v_ex", 0.0))
+    p.no_accept = int(bool(c.get("no_accept", 0)))
+    p.single = int(c.get("exchange", "pair") == "single")
     return p
 
 
 class State:
-    """A chain's state: positions and velocities of 3*n_water + 2*cap_pairs atoms."""
+    """A chain's state: positions and velocities of 3*n_water + 2*cap_pairs atoms (one atom
+    per unit instead of two with single-particle exchange)."""
 
     def __init__(self, p: Params, x: np.ndarray, v: np.ndarray | None, n_pairs: int, cap_pairs: int):
-        n_cap = 3 * p.n_water + 2 * cap_pairs
+        self.unit = 1 if p.single else 2
+        n_cap = 3 * p.n_water + self.unit * cap_pairs
         self.x = np.zeros((n_cap, 3), np.float64)
         self.v = np.zeros((n_cap, 3), np.float64)
-        n = 3 * p.n_water + 2 * n_pairs
+        n = 3 * p.n_water + self.unit * n_pairs
         self.x[:n] = np.asarray(x, np.float64).reshape(-1, 3)[:n]
         if v is not None:
             self.v[:n] = np.asarray(v, np.float64).reshape(-1, 3)[:n]
@@ -275,7 +281,7 @@ class State:
 
     @property
     def n_atoms(self) -> int:
-        return 3 * self.n_water + 2 * self.s.n_pairs
+        return 3 * self.n_water + self.unit * self.s.n_pairs
 
     def positions(self) -> np.ndarray:
         return self.x[: self.n_atoms].copy()
