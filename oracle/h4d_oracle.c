@@ -1187,3 +1187,62 @@ int orc_run_cycles_prop(const orc_params* p, const orc_proposal* q, orc_state* s
 int orc_run_cycles(const orc_params* p, orc_state* s, int64_t n_cycles, int64_t n_eq, orc_record* recs) {
   return orc_run_cycles_prop(p, NULL, s, n_cycles, n_eq, recs);
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* Ewald sum (Sec. II.B.2, Eqs. 9-10)                                                    */
+/* ------------------------------------------------------------------------------------ */
+double orc_ewald(const orc_params* p, int n, const double* x, double alpha, int kmax, double rcut,
+                 double* U_real, double* U_recip, double* U_self, double* U_excl, double* F_recip) {
+  const double L = p->L, V = L * L * L, K = p->kcoul;
+  double ur = 0.0, uk = 0.0, us = 0.0, ue = 0.0;
+  double* q = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  for (int i = 0; i < n; ++i) {
+    q[i] = p->q[orc_atom_type(p, i)];
+    us -= K * alpha / sqrt(M_PI) * q[i] * q[i];
+  }
+  /* real space and the intramolecular corrections */
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      double r2 = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        double d = minimg(x[3 * j + c] - x[3 * i + c], L);
+        r2 += d * d;
+      }
+      double r = sqrt(r2);
+      if (excluded(p, i, j)) ue -= K * q[i] * q[j] * erf(alpha * r) / r;
+      else if (r < rcut) ur += K * q[i] * q[j] * erfc(alpha * r) / r;
+    }
+  /* reciprocal space: every k = 2 pi n / L with 0 < max |n_d| <= kmax */
+  if (F_recip) memset(F_recip, 0, sizeof(double) * 3 * (size_t)n);
+  double* cs = (double*)malloc(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
+  for (int nx = -kmax; nx <= kmax; ++nx)
+    for (int ny = -kmax; ny <= kmax; ++ny)
+      for (int nz = -kmax; nz <= kmax; ++nz) {
+        if (nx == 0 && ny == 0 && nz == 0) continue;
+        double k[3] = {2.0 * M_PI * nx / L, 2.0 * M_PI * ny / L, 2.0 * M_PI * nz / L};
+        double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        double a = exp(-k2 / (4.0 * alpha * alpha)) / k2;
+        double re = 0.0, im = 0.0;
+        for (int j = 0; j < n; ++j) {
+          double th = k[0] * x[3 * j] + k[1] * x[3 * j + 1] + k[2] * x[3 * j + 2];
+          cs[2 * j] = cos(th);
+          cs[2 * j + 1] = sin(th);
+          re += q[j] * cs[2 * j];
+          im += q[j] * cs[2 * j + 1];
+        }
+        uk += 2.0 * M_PI * K / V * a * (re * re + im * im);
+        if (F_recip)
+          for (int j = 0; j < n; ++j) {
+            /* -d/dr_j of (2 pi K / V) a |S|^2 = (4 pi K q_j / V) a k (re sin - im cos) */
+            double f = 4.0 * M_PI * K * q[j] / V * a * (re * cs[2 * j + 1] - im * cs[2 * j]);
+            for (int c = 0; c < 3; ++c) F_recip[3 * j + c] += f * k[c];
+          }
+      }
+  free(cs);
+  free(q);
+  if (U_real) *U_real = ur;
+  if (U_recip) *U_recip = uk;
+  if (U_self) *U_self = us;
+  if (U_excl) *U_excl = ue;
+  return ur + uk + us + ue;
+}

@@ -106,6 +106,19 @@ typedef struct {
 
 void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
 
+/* Ewald sum of the Coulomb energy of the periodic system (Sec. II.B.2, Eqs. 9-10: the
+ * Coulomb energy split into a screened real-space part and a long-range part; the
+ * long-range part U_lr = U_recip + U_self is what g^lr(w) = exp(-kappa_lr w) scales).
+ * Charges p->q[type], prefactor p->kcoul, box p->L.  U_real: erfc(alpha r)/r over pairs
+ * closer than rcut (minimum image, unshifted, intramolecular water pairs left out);
+ * U_recip = (2 pi K / V) sum_{k != 0, |n_d| <= kmax} exp(-k^2 / 4 alpha^2) / k^2 |S(k)|^2 with
+ * S(k) = sum_j q_j exp(i k.r_j), k = 2 pi n / L; U_self = -K alpha/sqrt(pi) sum q_j^2;
+ * U_excl = -K sum over intramolecular water pairs q_i q_j erf(alpha r)/r (the reciprocal
+ * sum includes them).  F_recip (may be NULL) receives -dU_recip/dx per atom.  Returns
+ * U_real + U_recip + U_self + U_excl. */
+double orc_ewald(const orc_params* p, int n, const double* x, double alpha, int kmax, double rcut,
+                 double* U_real, double* U_recip, double* U_self, double* U_excl, double* F_recip);
+
 /* pair energy and derivative at 4D distance r4 between types ti, tj with
  * short-range screening factor g (Eq. 11) applied to the Coulomb part */
 void orc_pair(const orc_params* p, int ti, int tj, double r4, double g, double* u, double* dudr);

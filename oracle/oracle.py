@@ -203,6 +203,8 @@ def lib():
         _lib.orc_in_excluded_volume.argtypes = [P, pd, pd]
         _lib.orc_in_excluded_volume.restype = ctypes.c_int
         _lib.orc_run_cycles_prop.argtypes = [P, Q, S, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
+        _lib.orc_ewald.argtypes = [P, ctypes.c_int, pd, d, ctypes.c_int, d, pd, pd, pd, pd, pd]
+        _lib.orc_ewald.restype = d
     return _lib
 
 
@@ -422,3 +424,17 @@ def erfinv(y):
 
 def bias_offset(alpha, xb, L, r_mode, r_u):
     return lib().orc_bias_offset(alpha, xb, L, int(r_mode), int(r_u))
+
+
+def ewald(p: Params, x: np.ndarray, alpha: float, kmax: int, rcut: float, forces: bool = False):
+    """Ewald sum of the periodic Coulomb energy: dict with U (total), real, recip, self,
+    excl and, when asked, the reciprocal-space forces [n, 3]"""
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    n = x.shape[0]
+    parts = [ctypes.c_double() for _ in range(4)]
+    F = np.zeros((n, 3)) if forces else None
+    U = lib().orc_ewald(ctypes.byref(p), n, _ptr(x), alpha, int(kmax), rcut, *[ctypes.byref(v) for v in parts], _ptr(F))
+    out = {"U": U, "real": parts[0].value, "recip": parts[1].value, "self": parts[2].value, "excl": parts[3].value}
+    if forces:
+        out["F_recip"] = F
+    return out
