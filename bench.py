@@ -30,7 +30,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "accepted salt-pair exchanges/s & 4D atom-steps/s, plain vs batched/learned"
 FLOPS_PER_PAIR = 55  # FP32 operations per unordered pair inside the cut-off (FMA = 2, MUFU = 1)
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
 
@@ -184,6 +183,7 @@ def run_gpu(args):
     import torch
     import torch.distributed as dist
 
+    from paper_2307_11447_gb300 import analysis as an
     from paper_2307_11447_gb300 import lib as h4d
 
     rank, world, local = dist_env()
@@ -196,6 +196,8 @@ def run_gpu(args):
     with torch.cuda.stream(stream):
         ctx = h4d.Context(params, reps, seed=12345 + rank, stream=stream.cuda_stream)
     n_eq, n_f = cfg["n_eq"], cfg["n_f"]
+    sm_count, _, _ = h4d.h4d_device_info()
+    fp32_probe_tflops, _ = h4d.h4d_measure_fp32_peak()
     # equilibrate the random starts (untimed), autotune the force pass, then warm up
     ctx.h4d_run_md(args.equil)
     learned = None
@@ -266,7 +268,21 @@ def run_gpu(args):
     avg_launch_s = (t_ms / args.steps) / 1e3
     achieved = flops_per_launch / avg_launch_s / 1e12
     sm_mhz = clk.get("sm_max_mhz") or 2070.0
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    nominal = sm_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    # the roofline denominator is the FP32 throughput measured on this GPU (FMA chains on
+    # every SM, timed with CUDA events); the nominal lanes x clock figure is kept beside it
+    peak = fp32_probe_tflops
+    # grand-canonical statistics of the timed cycles (jackknife over chains) and trials
+    # that ended with non-finite work or an overflowing neighbour row (status 3)
+    status3 = 0
+    sums = []
+    for r in range(ctx.R):
+        rec = ctx.h4d_get_work(r, args.steps)
+        status3 += int((rec["status"] == 3).sum())
+        sums.append(an.chain_sums(rec["move"], rec["accepted"], rec["status"], rec["n_after"], rec["beta_dM"],
+                                  cfg["beta_mu"]))
+    gc = an.pooled_n_stats(sums)
+    eq21 = an.eq21_acceptance(sums)
 
     if learned is not None:
         learned["uniform_arm"] = uniform_arm(ctx, reps, args, n_eq, n_f, stream)
@@ -311,8 +327,16 @@ def run_gpu(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic_from_profile(),
                          "kernel": "cycles_kernel (persistent: list build, 4D pair forces, VV, FP64 work, Metropolis)",
-                         "peak_basis": f"FP32 {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz",
+                         "peak_basis": f"measured FP32 FMA-chain throughput on this GPU ({sm_count} SMs); "
+                                       f"nominal {sm_count} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz = "
+                                       f"{nominal:.1f} TFLOP/s",
+                         "frac_of_nominal": achieved / nominal,
                          "pairs_in_cutoff": pairs, "flops_per_pair": FLOPS_PER_PAIR},
+            "grand_canonical": {
+                "beta_mu": cfg["beta_mu"], "trials": int(sum(x["trials"] for x in sums)),
+                "mean_n": gc["mean_n"], "chi_osmotic": gc["chi"], "acceptance": gc["acc"],
+                "acceptance_eq21": eq21, "se_method": "jackknife over chains ([value, se])",
+                "status3_trials": status3},
             "e2e": e2e,
         }
         if learned is not None:
@@ -610,12 +634,14 @@ def run_reference(args):
     if rank != 0:
         return
     cores = args.cpu_cores or os.cpu_count() or 1
+    # the same sample size as the GPU line's cpu_baseline (60 MD steps per chain), so the
+    # process start-up does not weigh on the rate
     for _ in range(args.warmup):
-        cpu_baseline(args.workload, sample_steps=1, cores=cores, one_core=False)
+        cpu_baseline(args.workload, sample_steps=2, cores=cores, one_core=False)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(args.workload, sample_steps=2, cores=cores, one_core=False))
+        vals.append(cpu_baseline(args.workload, sample_steps=60, cores=cores, one_core=False))
     secs = time.perf_counter() - t0
     value = float(np.mean([v["value"] for v in vals]))
     out = {

@@ -34,7 +34,7 @@
  *     O,H,H; ions follow as interleaved pairs, ion 2k = cation k (type 0) and ion 2k+1 =
  *     anion k (type 1).  Water O is type 2 and H is type 3.  Positions are Cartesian in
  *     [0, L)^3 per replica (other values are wrapped); arrays are row-major [atom][xyz].
- *   - Random numbers: Philox4x64-10 keyed by (seed, replica); draw addresses are fixed
+ *   - Random numbers: Philox4x64-10 keyed by (seed, replica key); draw addresses are fixed
  *     (trial counter, block, purpose) so results do not depend on thread scheduling.
  */
 #ifndef H4D_H
@@ -64,6 +64,9 @@ typedef struct h4d_ctx h4d_ctx;
 #define H4D_SCHED_LINEAR 0 /* Eq. 2 */
 #define H4D_SCHED_WV 1     /* Eq. S6 insertion form; deletion is its time reverse */
 #define H4D_SCHED_WX 2     /* Eq. S7 insertion form; deletion is its time reverse */
+#define H4D_EXCHANGE_PAIR 0   /* cation-anion pairs (Eqs. 3-8) */
+#define H4D_EXCHANGE_SINGLE 1 /* single particles of one neutral species (Sec. II.A: the
+                                 pair rule with one flyer, V/(N+1) to the first power) */
 
 /* Physics, protocol and engine settings common to all replicas of a context. */
 typedef struct h4d_params {
@@ -91,11 +94,21 @@ typedef struct h4d_params {
                              displacements since the outer build exceed skin_outer - skin */
   int32_t max_nbr;        /* neighbour-row capacity per atom; 0 = derived from density */
   int32_t threads_per_atom; /* 1,2,4,8,16 or 32; 0 = chosen per replica size (h4d_autotune measures) */
+  int32_t exchange;       /* H4D_EXCHANGE_PAIR, or H4D_EXCHANGE_SINGLE: LJ system only, charges 0,
+                             every ion-block atom is one species with the parameters of
+                             type 0, and the "pair" counts of h4d_system, h4d_counts and the
+                             records count particles; bias, learned proposal, species w_max
+                             and early rejection are pair moves (H4D_EINVAL) */
+  int32_t pad_exchange;
 } h4d_params;
 
 /* Initial replicas.  Replica r holds 3*n_water[r] + 2*n_pairs[r] atoms; host_x (and
  * host_v when not NULL) concatenate the replicas in order, 3 doubles per atom.  With
- * host_v == NULL velocities are drawn from Maxwell-Boltzmann at 1/beta. */
+ * host_v == NULL velocities are drawn from Maxwell-Boltzmann at 1/beta.
+ * replica_key (may be NULL = the replica index r) gives each replica the second word of
+ * its Philox key (seed, key): a replica keeps its key, and with it every random draw and
+ * -- for the same threads_per_atom -- every result bit, whether it runs alone or packed
+ * with other replicas, since all of the engine's sums are independent of the launch plan. */
 typedef struct h4d_system {
   int32_t n_replicas;
   const double* L;          /* [R] cubic box edges */
@@ -104,6 +117,7 @@ typedef struct h4d_system {
   const int32_t* cap_pairs; /* [R] maximum ion pairs the replica may reach */
   const double* host_x;
   const double* host_v;
+  const uint64_t* replica_key; /* [R] or NULL */
 } h4d_system;
 
 /* Per-replica counters. */
@@ -124,6 +138,11 @@ typedef struct h4d_counts {
   int64_t threads_per_atom; /* lanes that share one neighbour row in the force pass */
   int64_t nbr_refreshes;    /* Verlet-row refreshes filtered from the outer rows (between builds) */
   double t_filter_ns;       /* part of t_build_ns spent filtering Verlet rows from outer rows */
+  int64_t last_smid;        /* SM that ran this replica's warps in the most recent launch */
+  double t_last_begin_ns;   /* device global timer when this replica's warps started and */
+  double t_last_end_ns;     /* finished the most recent launch (ns; compare across replicas) */
+  int64_t plan_warps;       /* warps of this replica's group in the launch plan */
+  int64_t plan_cta_groups;  /* replicas (groups) sharing its CTA, itself included */
 } h4d_counts;
 
 /* One trial record; Delta M follows the insertion direction (Eqs. 6, 8). */
@@ -234,6 +253,17 @@ int h4d_get_state(h4d_ctx* ctx, int32_t replica, double* host_x, double* host_v,
 int h4d_set_state(h4d_ctx* ctx, int32_t replica, int32_t n_pairs, const double* host_x,
                   const double* host_v);
 int32_t h4d_num_replicas(h4d_ctx* ctx);
+
+/* ---- device facts (no paper counterpart; measurement support) ---- */
+/* SM count of the current device, and the compute capability (major*10 + minor, 103 for
+ * sm_103a) and PTX version the engine kernel of this build was compiled for, from the
+ * CUDA runtime's kernel attributes.  H4D_ENODEV without a suitable device. */
+int h4d_device_info(int32_t* sm_count, int32_t* binary_version, int32_t* ptx_version);
+/* Measured FP32 throughput of the current device: a kernel of independent FMA chains on
+ * every SM (8 CTAs of 256 threads per SM, no memory traffic), timed with CUDA events on
+ * the legacy default stream; *tflops = 2 x FMAs / time (and *seconds the time when not
+ * NULL).  Allocates a small device buffer; synchronises. */
+int h4d_measure_fp32_peak(double* tflops, double* seconds);
 /* total pairs inside the larger cut-off over all replicas at the current state (each
  * unordered pair once); the algorithmic work unit of the pair kernel */
 int h4d_count_pairs(h4d_ctx* ctx, int64_t* n_pairs_in_cutoff);
@@ -300,11 +330,11 @@ int h4d_proposal_grad(const double* host_w, int64_t n_rec, const float* host_fea
                       double* loss, double* host_grad);
 
 /* ---- checkpoint ----
- * h4d_save writes a flat binary image (magic "HH4D0003", seed, replica table, positions,
+ * h4d_save writes a flat binary image (magic "HH4D0004", seed, replica table, positions,
  * velocities, trial records) of a context; it synchronises.  h4d_load restores it into a
  * context created with the same system (replica count, atom capacities, waters, box edges
  * and ion capacities must match, else H4D_EINVAL and nothing is changed): each chain's
- * ion count, counters, random-number counters, statistics and records come from the file,
+ * ion count, counters, random-number keys and counters, statistics and records come from the file,
  * the context keeps its own geometry, thresholds, launch plan, proposal grid and record
  * rings.  Out-of-range fields (ion count above capacity, negative record count, an
  * lane count that is not a power of two up to 32) are rejected.  A resumed chain continues bit-identically. */
@@ -325,7 +355,8 @@ int h4d_eval_forces(const h4d_params* params, double L, int32_t n_water, int32_t
  * (for example a host that forbids cudaMalloc inside its own callbacks, or code that
  * runs under a device-memory budget it does not control).  The paper has no counterpart;
  * this entry point exists for such embedders only.
- * Same arguments, units and results as h4d_eval_forces (host buffers in and out).  It
+ * Same arguments, units and results as h4d_eval_forces (host buffers in and out; n = 0
+ * gives *U = 0 and touches no device memory).  It
  * calls no cudaMalloc, cudaFree or other allocating routine: every device buffer lives in
  * one file-scope array of 16 MiB that each GPU loading the library holds until the
  * process exits.  The first call on a device looks up that array's device address
@@ -337,6 +368,23 @@ int h4d_eval_forces(const h4d_params* params, double L, int32_t n_water, int32_t
  * caller.  Works on the legacy default stream and returns after synchronising it. */
 int h4d_eval_forces_static(const h4d_params* params, double L, int32_t n_water, int32_t n,
                            const double* host_x, const double* host_w, double* host_F, double* U);
+
+/* Long-range Coulomb term of one configuration (Sec. II.B.2, Eqs. 9-10): the paper splits
+ * the 4D Coulomb energy into the screened short-range part (the pair term of
+ * h4d_eval_forces) and the 3D long-range part U_lr = U_recip + U_self, which NEMD scales
+ * by g^lr(wbar) = exp(-kappa_lr wbar) (wbar = mean altitude of the flying particles).
+ *   U_recip = g (2 pi K / V) sum_{k != 0} exp(-k^2 / 4 alpha^2) / k^2 |S(k)|^2,
+ *   S(k) = sum_j q_j exp(i k.r_j), k = 2 pi n / L over 0 < max_d |n_d| <= kmax;
+ *   U_self = -g K alpha / sqrt(pi) sum_j q_j^2;
+ *   host_F (may be NULL) [n][3] = -dU_recip/dx (FP32 sums of k-vector tiles, FP64 totals).
+ * Charges follow the atom layout of h4d_eval_forces (params->q by type, K = params->kcoul);
+ * host_x [n][3] in [0, L) (wrapped otherwise).  Intramolecular exclusion corrections of
+ * rigid waters are not included (they do not depend on the positions of other molecules).
+ * H4D_EINVAL for alpha <= 0, kmax outside 1..64, negative wbar or kappa_lr.  Allocates
+ * device scratch per call; runs on the legacy default stream and synchronises it. */
+int h4d_ewald_lr(const h4d_params* params, double L, int32_t n_water, int32_t n, const double* host_x,
+                 double alpha, int32_t kmax, double wbar, double kappa_lr, double* U_recip,
+                 double* U_self, double* host_F);
 
 /* Neighbour pairs (i < j) under the fixed-point criterion: X = round(x/L 2^32) mod 2^32
  * per coordinate, pair iff sum ((int32)(X_i - X_j))^2 <= floor((r_list/L 2^32)^2).

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libh4d.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["h4d_engine.cu", "h4d_api.cu", "h4d_train.cu"]
+SOURCES = ["h4d_engine.cu", "h4d_api.cu", "h4d_train.cu", "h4d_ewald.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 # extra preprocessor defines (e.g. engine launch bounds), space separated

@@ -169,6 +169,7 @@ struct h4d_ctx {
   uint16_t* d_nbr_out = nullptr;
   int* d_ncnt_out = nullptr;
   uint4* d_ref_out = nullptr;
+  double* d_red = nullptr;
   h4d_record* d_rec = nullptr;
   double* d_scratch = nullptr;
   unsigned long long* d_count = nullptr;
@@ -215,8 +216,15 @@ static int check_params(const h4d_params* p) {
     // the LJ specialisation assumes equal sizes/energies and charges +q/-q
     if (p->sig[0] != p->sig[1] || p->eps[0] != p->eps[1] || p->q[0] != -p->q[1]) return H4D_EINVAL;
   }
+  if (p->exchange != H4D_EXCHANGE_PAIR && p->exchange != H4D_EXCHANGE_SINGLE) return H4D_EINVAL;
+  // single particles: one neutral species (a lone charge would leave the box charged)
+  if (p->exchange == H4D_EXCHANGE_SINGLE && (p->system != H4D_SYS_LJ || p->q[0] != 0.0 || p->q[1] != 0.0))
+    return H4D_EINVAL;
   return H4D_OK;
 }
+
+// atoms per exchange unit
+static int unit_of(const h4d_params& p) { return p.exchange == H4D_EXCHANGE_SINGLE ? 1 : 2; }
 
 // ratio of the anion's w_max to the cation's: (w_max + 0.5 (sig_c + sig_a) f_w) / w_max
 static double species_rw(const h4d_params& p, double f_w) {
@@ -264,7 +272,9 @@ static void fill_pot(const h4d_params& p, Pot& P, Proto& pr) {
   P.dshift_c = std::erfc(p.alpha * p.rc_coul) / p.rc_coul;
   P.dkappa_sr = p.kappa_sr;
   for (int t = 0; t < 4; ++t) {
-    double m = (t < p.ntypes) ? p.mass[t] * p.mvv2e : 1.0;
+    // single-particle exchange: both parities of the ion block are the one species
+    const int tt = (p.exchange == H4D_EXCHANGE_SINGLE && t == 1) ? 0 : t;
+    double m = (t < p.ntypes) ? p.mass[tt] * p.mvv2e : 1.0;
     P.dm[t] = m;
     P.inv_m[t] = (float)(1.0 / m);
     P.m_f[t] = (float)m;
@@ -283,6 +293,8 @@ static void fill_pot(const h4d_params& p, Pot& P, Proto& pr) {
   pr.beta = p.beta;
   pr.beta_mu = p.beta_mu;
   pr.rw = 1.0;
+  pr.single = p.exchange == H4D_EXCHANGE_SINGLE;
+  pr.unit = unit_of(p);
 }
 
 // neighbour-row capacity from the densest plausible packing (about one particle per sigma^3
@@ -359,6 +371,7 @@ static int alloc_all(h4d_ctx* c) {
   CK(cudaMalloc(&c->d_nbr_out, na * (size_t)c->max_out * sizeof(uint16_t)));
   CK(cudaMalloc(&c->d_ncnt_out, na * sizeof(int)));
   CK(cudaMalloc(&c->d_ref_out, na * sizeof(uint4)));
+  CK(cudaMalloc(&c->d_red, na * sizeof(double)));
   CK(cudaMemset(c->d_ncnt_out, 0, na * sizeof(int)));
   CK(cudaMemset(c->d_pos, 0, na * sizeof(uint4)));
   CK(cudaMemset(c->d_vhi, 0, na * sizeof(float4)));
@@ -397,6 +410,7 @@ static void fill_eng(h4d_ctx* c) {
   e.ncnt_out = c->d_ncnt_out;
   e.ref_out = c->d_ref_out;
   e.rec = c->d_rec;
+  e.red = c->d_red;
   e.max_nbr = c->max_nbr;
   e.max_out = c->max_out;
   e.seed = c->seed;
@@ -437,7 +451,9 @@ static void philox_host(uint64_t c[4], uint64_t k0, uint64_t k1) {
 static double h_u01(uint64_t r) { return (double)(r >> 11) * 0x1.0p-53; }
 static double h_u01o(uint64_t r) { return (double)((r >> 11) + 1) * 0x1.0p-53; }
 
-static int atom_type_host(int a, int nw3) { return a < nw3 ? ((a % 3 == 0) ? 2 : 3) : ((a - nw3) & 1); }
+static int atom_type_host(int a, int nw3, int unit) {
+  return a < nw3 ? ((a % 3 == 0) ? 2 : 3) : (unit == 1 ? 0 : ((a - nw3) & 1));
+}
 
 static void split_ff(double v, float& hi, float& lo) {
   hi = (float)v;
@@ -477,7 +493,8 @@ static int upload_replica(h4d_ctx* c, int r, int n_pairs, const double* x, const
   Rep& R = c->rep_h[r];
   if (n_pairs < 0 || n_pairs > R.cap_pairs) return H4D_ECAPACITY;
   R.n_pairs = n_pairs;
-  int n = R.nw3 + 2 * n_pairs;
+  R.err = 0;  // the error flags describe the state they were raised on
+  int n = R.nw3 + unit_of(c->prm) * n_pairs;
   std::vector<uint4> pos(n);
   std::vector<float4> vh(n), vl(n);
   std::vector<double> vdraw(v ? 0 : 3 * (size_t)n);
@@ -488,8 +505,8 @@ static int upload_replica(h4d_ctx* c, int r, int n_pairs, const double* x, const
       vv[0] = v[3 * a]; vv[1] = v[3 * a + 1]; vv[2] = v[3 * a + 2];
     } else {
       uint64_t q[4] = {(uint64_t)a, 0, 4, 0};
-      philox_host(q, c->seed, (uint64_t)r);
-      int t = atom_type_host(a, R.nw3);
+      philox_host(q, c->seed, R.key);
+      int t = atom_type_host(a, R.nw3, unit_of(c->prm));
       double sd = std::sqrt(1.0 / (c->prm.beta * c->prm.mass[t] * c->prm.mvv2e));
       double rad0 = std::sqrt(-2.0 * std::log(h_u01o(q[0])));
       double rad1 = std::sqrt(-2.0 * std::log(h_u01o(q[2])));
@@ -540,8 +557,12 @@ static int check_device() {
 // A group's warp count follows the replica's weight (expected work, or the work the
 // autotuner measured), out of the warps the GPU holds at two CTAs per SM, so that
 // uneven replicas finish together.  A group spanning a whole CTA uses __syncthreads.
-static const int kCtaWarps = 16;
-static const size_t kCtaSmem = 113 * 1024;
+#ifndef H4D_CTA_WARPS
+#define H4D_CTA_WARPS 16
+#endif
+static const int kCtaWarps = H4D_CTA_WARPS;
+static const int kWarpsPerSm = 32;  // resident warps per SM at the engine's 64 registers
+static const size_t kCtaSmem = (size_t)(kWarpsPerSm / kCtaWarps > 1 ? 113 : 227) * 1024;
 
 static double default_weight(const Rep& r) {
   // pair count ~ atoms x density
@@ -563,7 +584,7 @@ static int make_plan(h4d_ctx* c, const std::vector<double>* weight = nullptr) {
     w[r] = (weight && (*weight)[r] > 0) ? (*weight)[r] : default_weight(c->rep_h[r]);
     W += w[r];
   }
-  const double budget = (double)c->sm_count * 2.0 * kCtaWarps;
+  const double budget = (double)c->sm_count * kWarpsPerSm;
   struct Item { int rep, nw; size_t smem; };
   std::vector<Item> items(R);
   for (int r = 0; r < R; ++r) {
@@ -674,11 +695,12 @@ int h4d_create(const h4d_params* params, const h4d_system* sys, uint64_t seed, v
     R.nw3 = 3 * nw;
     R.n_pairs = sys->n_pairs[r];
     R.cap_pairs = sys->cap_pairs[r];
-    R.cap_atoms = R.nw3 + 2 * R.cap_pairs;
+    R.cap_atoms = R.nw3 + unit_of(*params) * R.cap_pairs;
     if (R.cap_atoms > 65535 || R.cap_atoms < 1) { h4d_destroy(c); return H4D_ECAPACITY; }
     if (2.0 * (rmax_of(*params) + params->skin) >= sys->L[r]) { h4d_destroy(c); return H4D_EINVAL; }
     R.atom_off = off;
     off += R.cap_atoms;
+    R.key = sys->replica_key ? sys->replica_key[r] : (uint64_t)r;
     set_rep_geometry(*params, R, sys->L[r]);
     R.tpa = choose_tpa(*params, R.cap_atoms);
     R.rec_cap = 1024;
@@ -698,7 +720,7 @@ int h4d_create(const h4d_params* params, const h4d_system* sys, uint64_t seed, v
     Rep& R = c->rep_h[r];
     rc = upload_replica(c, r, R.n_pairs, sys->host_x + xo, sys->host_v ? sys->host_v + xo : nullptr);
     if (rc) { h4d_destroy(c); return rc; }
-    xo += 3 * (size_t)(R.nw3 + 2 * R.n_pairs);
+    xo += 3 * (size_t)(R.nw3 + unit_of(*params) * R.n_pairs);
   }
   rc = push_plan(c);
   if (rc) { h4d_destroy(c); return rc; }
@@ -711,7 +733,7 @@ void h4d_destroy(h4d_ctx* c) {
   if (!c) return;
   void* ptrs[] = {c->d_rep, c->d_groups, c->d_cta_groups, c->d_pos, c->d_vhi, c->d_vlo, c->d_force,
                   c->d_pos_save, c->d_vhi_save, c->d_vlo_save, c->d_ref, c->d_nbr, c->d_ncnt, c->d_rec,
-                  c->d_scratch, c->d_count, c->d_nbr_out, c->d_ncnt_out, c->d_ref_out};
+                  c->d_scratch, c->d_count, c->d_nbr_out, c->d_ncnt_out, c->d_ref_out, c->d_red};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   prop_free(c->prop);
@@ -756,6 +778,7 @@ int h4d_set_protocol(h4d_ctx* c, int32_t n_f, double w_max, double dt, double ka
 }
 
 int h4d_set_species_wmax(h4d_ctx* c, double f_w) {
+  if (c && c->eng.proto.single && f_w != 0.0) return H4D_EINVAL;  // a pair move
   if (!c || !std::isfinite(f_w) || f_w < 0 || (f_w > 0 && !(c->prm.w_max > 0))) return H4D_EINVAL;
   c->eng.proto.fw = f_w;
   c->eng.proto.rw = species_rw(c->prm, f_w);
@@ -764,6 +787,7 @@ int h4d_set_species_wmax(h4d_ctx* c, double f_w) {
 }
 
 int h4d_set_bias(h4d_ctx* c, double alpha_b, double x_b) {
+  if (c && c->eng.proto.single && alpha_b != 0.0) return H4D_EINVAL;  // a pair move
   if (!c || !std::isfinite(alpha_b) || !std::isfinite(x_b) || alpha_b < 0 || x_b < 0) return H4D_EINVAL;
   if (alpha_b > 0 && c->eng.proto.prop_mode) return H4D_EINVAL;  // one placement rule at a time
   c->eng.proto.bias_on = alpha_b > 0 ? 1 : 0;
@@ -774,6 +798,7 @@ int h4d_set_bias(h4d_ctx* c, double alpha_b, double x_b) {
 }
 
 int h4d_set_early_rejection(h4d_ctx* c, double v_ex) {
+  if (c && c->eng.proto.single && v_ex != 0.0) return H4D_EINVAL;  // a pair move
   if (!c || !std::isfinite(v_ex) || v_ex < 0) return H4D_EINVAL;
   c->eng.proto.vex_edge = v_ex > 0 ? std::cbrt(v_ex) : 0.0;
   invalidate_graphs(c);
@@ -792,6 +817,7 @@ static int check_errors(h4d_ctx* c) {
   if (rc) return rc;
   for (auto& r : c->rep_h) {
     if (r.err & 1) return H4D_ECAPACITY;
+    if (r.err & 4) return H4D_ETIMEOUT;  // the cause when a constraint solver gave up first
     if (r.err & 2) return H4D_ENAN;
   }
   return H4D_OK;
@@ -907,6 +933,17 @@ int h4d_get_counts(h4d_ctx* c, int32_t r, h4d_counts* out) {
   out->threads_per_atom = R.tpa;
   out->nbr_refreshes = R.refreshes;
   out->t_filter_ns = R.t_filter_ns;
+  out->last_smid = R.smid;
+  out->t_last_begin_ns = (double)R.t_begin;
+  out->t_last_end_ns = (double)R.t_end;
+  out->plan_warps = 0;
+  out->plan_cta_groups = 0;
+  for (size_t k = 0; k + 1 < c->cta_groups_h.size(); ++k)
+    for (int g = c->cta_groups_h[k]; g < c->cta_groups_h[k + 1]; ++g)
+      if (c->groups_h[g].rep == r) {
+        out->plan_warps = c->groups_h[g].nwarps;
+        out->plan_cta_groups = c->cta_groups_h[k + 1] - c->cta_groups_h[k];
+      }
   return H4D_OK;
 }
 
@@ -947,7 +984,7 @@ int h4d_get_state(h4d_ctx* c, int32_t r, double* x, double* v, int64_t cap_atoms
   int rc = pull_reps(c);
   if (rc) return rc;
   const Rep& R = c->rep_h[r];
-  int n = R.nw3 + 2 * R.n_pairs;
+  int n = R.nw3 + unit_of(c->prm) * R.n_pairs;
   if (n_atoms) *n_atoms = n;
   if (n > cap_atoms) return H4D_ECAPACITY;
   std::vector<uint4> pos(n);
@@ -995,8 +1032,73 @@ int h4d_count_pairs(h4d_ctx* c, int64_t* n) {
   return check_errors(c);
 }
 
+int h4d_device_info(int32_t* sm_count, int32_t* binary_version, int32_t* ptx_version) {
+  if (!sm_count || !binary_version || !ptx_version) return H4D_EINVAL;
+  int rc = check_device();
+  if (rc) return rc;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(sm_count, cudaDevAttrMultiProcessorCount, dev));
+  int b = 0, p = 0;
+  rc = h4d::engine_binary_version(&b, &p);
+  if (rc) return rc;
+  *binary_version = b;
+  *ptx_version = p;
+  return H4D_OK;
+}
+
+// FP32 throughput probe: every thread runs 8 independent FMA chains (no memory traffic in
+// the loop); the result is stored only when it equals a value it cannot reach, so the
+// chains are kept but nothing is written
+static __global__ void __launch_bounds__(256) fma_chain_kernel(int iters, float seed, float* sink) {
+  float a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = seed + 0.001f * (float)(threadIdx.x + k);
+  const float m = 0.9999999f, d = 1e-7f;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] = fmaf(a[k], m, d);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  if (s == -1.0f) sink[blockIdx.x] = s;
+}
+
+int h4d_measure_fp32_peak(double* tflops, double* seconds) {
+  if (!tflops) return H4D_EINVAL;
+  int rc = check_device();
+  if (rc) return rc;
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  float* sink = nullptr;
+  CK(cudaMalloc(&sink, sizeof(float) * (size_t)sms * 8));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int blocks = sms * 8, iters = 4096;  // 8 resident CTAs of 256 threads per SM
+  fma_chain_kernel<<<blocks, 256>>>(16, 1.0f, sink);  // warm-up
+  cudaEventRecord(e0);
+  fma_chain_kernel<<<blocks, 256>>>(iters, 1.0f, sink);
+  cudaEventRecord(e1);
+  cudaError_t err = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (err != cudaSuccess || !(ms > 0.f)) return H4D_ECUDA;
+  const double flops = 2.0 * 8.0 * 16.0 * (double)iters * 256.0 * (double)blocks;
+  *tflops = flops / (ms * 1e-3) / 1e12;
+  if (seconds) *seconds = ms * 1e-3;
+  return H4D_OK;
+}
+
 // ---- checkpoint: a flat binary image of the replica table and per-atom state ----
-static const uint64_t kMagic = 0x3330303044344848ULL;  // "HH4D0003"
+static const uint64_t kMagic = 0x3430303044344848ULL;  // "HH4D0004"
 
 int h4d_save(h4d_ctx* c, const char* path) {
   if (!c || !path) return H4D_EINVAL;
@@ -1063,6 +1165,7 @@ int h4d_load(h4d_ctx* c, const char* path) {
     m.rec_count = f.rec_count;
     m.trial_ctr = f.trial_ctr;
     m.step_ctr = f.step_ctr;
+    m.key = f.key;
     m.cycles = f.cycles;
     m.trials_ins = f.trials_ins;
     m.trials_del = f.trials_del;
@@ -1102,7 +1205,7 @@ int h4d_eval_forces(const h4d_params* params, double L, int32_t n_water, int32_t
   int rc = check_params(params);
   if (rc) return rc;
   if (!x || !F || n < 0 || n_water < 0 || 3 * n_water > n || !(L > 0)) return H4D_EINVAL;
-  if (((n - 3 * n_water) & 1) != 0) return H4D_EINVAL;
+  if (unit_of(*params) == 2 && ((n - 3 * n_water) & 1) != 0) return H4D_EINVAL;
   if (2.0 * (rmax_of(*params) + params->skin) >= L) return H4D_EINVAL;
   if (n > 65535) return H4D_ECAPACITY;
   rc = check_device();
@@ -1121,7 +1224,7 @@ int h4d_eval_forces(const h4d_params* params, double L, int32_t n_water, int32_t
   std::memset(&R, 0, sizeof(Rep));
   R.n_water = n_water;
   R.nw3 = 3 * n_water;
-  R.n_pairs = (n - 3 * n_water) / 2;
+  R.n_pairs = (n - 3 * n_water) / unit_of(*params);
   R.cap_pairs = R.n_pairs;
   R.cap_atoms = std::max(n, 1);
   R.atom_off = 0;
@@ -1302,11 +1405,15 @@ extern "C" int h4d_eval_forces_static(const h4d_params* params, double L, int32_
                                       const double* x, const double* w, double* F, double* U) {
   int rc = check_params(params);
   if (rc) return rc;
-  if (!x || !F || n < 1 || n_water < 0 || 3 * n_water > n || !(L > 0)) return H4D_EINVAL;
-  if (((n - 3 * n_water) & 1) != 0) return H4D_EINVAL;
+  if (!x || !F || n < 0 || n_water < 0 || 3 * n_water > n || !(L > 0)) return H4D_EINVAL;
+  if (unit_of(*params) == 2 && ((n - 3 * n_water) & 1) != 0) return H4D_EINVAL;
   if (2.0 * (rmax_of(*params) + params->skin) >= L) return H4D_EINVAL;
   rc = check_device();
   if (rc) return rc;
+  if (n == 0) {  // no atoms: zero energy, nothing to write (as h4d_eval_forces)
+    if (U) *U = 0.0;
+    return H4D_OK;
+  }
   void* base = nullptr;
   rc = static_scratch_address(&base);
   if (rc) return rc;
@@ -1324,7 +1431,7 @@ extern "C" int h4d_eval_forces_static(const h4d_params* params, double L, int32_
   std::memset(&R, 0, sizeof(Rep));
   R.n_water = n_water;
   R.nw3 = 3 * n_water;
-  R.n_pairs = (n - 3 * n_water) / 2;
+  R.n_pairs = (n - 3 * n_water) / unit_of(*params);
   R.cap_pairs = R.n_pairs;
   R.cap_atoms = n;
   set_rep_geometry(*params, R, L);
@@ -1356,6 +1463,7 @@ extern "C" int h4d_eval_forces_static(const h4d_params* params, double L, int32_
   const size_t o_nbo = carve_bytes(off, na * (size_t)c.max_out * sizeof(uint16_t));
   const size_t o_cno = carve_bytes(off, na * sizeof(int));
   const size_t o_rfo = carve_bytes(off, na * sizeof(uint4));
+  const size_t o_red = carve_bytes(off, na * sizeof(double));
   if (off > kStaticScratchBytes) return H4D_ECAPACITY;  // too many atoms for 16 MiB
 
   unsigned char* b = static_cast<unsigned char*>(base);
@@ -1377,6 +1485,7 @@ extern "C" int h4d_eval_forces_static(const h4d_params* params, double L, int32_
   e.ncnt_out = reinterpret_cast<int*>(b + o_cno);
   e.ref_out = reinterpret_cast<uint4*>(b + o_rfo);
   e.rec = reinterpret_cast<h4d_record*>(b + o_rec);
+  e.red = reinterpret_cast<double*>(b + o_red);
   e.max_nbr = c.max_nbr;
   e.max_out = c.max_out;
   e.seed = 0;
@@ -1436,6 +1545,7 @@ static int prop_pack(PropDev* P, cudaStream_t s) {
 extern "C" {
 
 int h4d_proposal(h4d_ctx* c, int32_t mode, double cell_len, double eps, int32_t records_per_replica) {
+  if (c && c->eng.proto.single) return H4D_EINVAL;  // the proposal places ion pairs
   if (!c || (mode != H4D_PROPOSAL_UNIFORM && mode != H4D_PROPOSAL_LEARNED) || !(cell_len > 0) || !(eps > 0) ||
       !(eps <= 1) || records_per_replica < 0 || records_per_replica > (1 << 20))
     return H4D_EINVAL;

@@ -23,6 +23,14 @@
 #define H4D_MINBLOCKS 1
 #endif
 
+// Attribute of the phase functions (list build, filter, force pass, kick/drift, FP64
+// energy, the MD and NEMD step loops).  Empty: the compiler inlines them into the
+// persistent kernel (measured faster on GB300 than __noinline__, where each phase would
+// get a register budget of its own at the cost of a call and a context copy).
+#ifndef H4D_PHASE
+#define H4D_PHASE
+#endif
+
 namespace h4d {
 
 // ------------------------------------------------------------------------------------
@@ -171,7 +179,8 @@ struct GScal {
   int flag_rebuild, flag_overflow, flag_nan, n_tot;
   int fly0, fly1, ins, status;
   int flip_s, flip_e, cat, ani;
-  int n_before, accept, inst, pad1;  // inst: instantaneous move (early rejection)
+  int n_before, accept, inst;  // inst: instantaneous move (early rejection)
+  int flag_timeout;            // a bounded iteration (SHAKE, RATTLE, gamma draw) gave up
   float w_cur, g_scr, pad2, pad3;
   double alpha_th, dW[2], wprot, wprot_c, red_out;
   double ln_u, ustart, kstart, uend, kend;
@@ -206,13 +215,20 @@ __device__ __forceinline__ GView carve(char* base, int cap_atoms, int nc, int nt
   size_t ncell = nc > 0 ? (size_t)nc * nc * nc : 0;
   size_t slots = (size_t)cap_atoms + 3 * ncell;
   char* p = base;
-  v.pos = (uint4*)p; p += smem_align16(16 * (size_t)cap_atoms);
+  v.pos = (uint4*)p; p += smem_align16(16 * ((size_t)cap_atoms + 1));
   v.cstart = (int*)p; p += smem_align16(4 * (ncell + 1));
   v.cfill = (int*)p; p += smem_align16(4 * (ncell + 1));
   v.sorted = (uint16_t*)p; p += smem_align16(2 * slots);
   v.sorted8 = (unsigned*)p; p += smem_align16(4 * slots);
   v.s = (GScal*)p;
   return v;
+}
+
+// The sentinel slot after a replica's last possible atom: row padding (kNoAtom) is read
+// as min(index, cap_atoms), i.e. as this slot, whose infinite altitude puts it beyond every
+// cut-off, so padding needs neither a branch nor a mask in the pair loop.
+__device__ __forceinline__ void write_sentinel(const GView& v, int cap_atoms) {
+  v.pos[cap_atoms] = make_uint4(0u, 0u, 0u, 0x7F800000u);
 }
 
 __device__ __forceinline__ unsigned pack8(const uint4& p) {
@@ -278,23 +294,54 @@ __device__ __forceinline__ const uint2* nbr_packets(const Eng& e, const RepC& R)
   return reinterpret_cast<const uint2*>(e.nbr + (size_t)R.atom_off * e.max_nbr);
 }
 
-// deterministic group-wide FP64 sum: warp butterflies, then thread 0 adds warp slots in order
-__device__ double group_sum(const Ctx& c, double x) {
+// Exact group-wide sum of 64-bit fixed-point partials: integer addition is associative,
+// so the result does not depend on how atoms are spread over threads or on the order of
+// the warp slots (a replica gives the same sums in a CTA of its own and packed with others)
+__device__ long long group_sum_fx(const Ctx& c, long long x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  int warp = c.tid >> 5, lane = c.tid & 31;
+  const int warp = c.tid >> 5, lane = c.tid & 31;
+  long long* slot = reinterpret_cast<long long*>(c.v.s->kw);
   c.sync();
-  if (lane == 0) c.v.s->kw[warp] = x;
+  if (lane == 0) slot[warp] = x;
   c.sync();
   if (c.tid == 0) {
-    double s = 0.0, comp = 0.0;  // Kahan
-    for (int w = 0; w < (c.T >> 5); ++w) {
-      double y = c.v.s->kw[w] - comp;
-      double t = s + y;
-      comp = (t - s) - y;
-      s = t;
-    }
-    c.v.s->red_out = s;
+    long long s = 0;
+    for (int w = 0; w < (c.T >> 5); ++w) s += slot[w];
+    reinterpret_cast<long long*>(&c.v.s->red_out)[0] = s;
+  }
+  c.sync();
+  return reinterpret_cast<const long long*>(&c.v.s->red_out)[0];
+}
+
+// kinetic-energy units of the fixed-point sums: 2^-32 per unit, per-atom values clamped
+// at 2^16 so that 9160 atoms stay far inside int64 (a clamped atom also flags the state)
+constexpr float kFxScale = 4294967296.0f;
+constexpr float kFxClamp = 65536.0f;
+__device__ __forceinline__ long long to_fx(float v, int& bad) {
+  if (!(v <= kFxClamp)) { bad = 1; v = kFxClamp; }
+  return __float2ll_rn(v * kFxScale);
+}
+
+// Sum of buf[0, n) (this replica's per-atom partials in global memory, written before the
+// call) in an order fixed by n alone: thread k adds the 32 values of chunk k, then the
+// lanes of warp 0 add every 32nd chunk sum and a fixed butterfly combines the lanes
+__device__ double fixed_order_sum(const Ctx& c, double* buf, int n) {
+  c.sync();
+  const int nch = (n + 31) >> 5;
+  for (int k = c.tid; k < nch; k += c.T) {
+    double s = 0.0;
+    const int q1 = min(n, 32 * k + 32);
+    for (int q = 32 * k; q < q1; ++q) s += buf[q];
+    buf[32 * k] = s;
+  }
+  c.sync();
+  if (c.tid < 32) {
+    double s = 0.0;
+    for (int k = c.tid; k < nch; k += 32) s += buf[32 * k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (c.tid == 0) c.v.s->red_out = s;
   }
   c.sync();
   return c.v.s->red_out;
@@ -315,6 +362,12 @@ struct RowBuf {
   __device__ __forceinline__ void put(int j) {
     b = (b >> 16) | ((unsigned long long)(unsigned)j << 48);
     ++n;
+  }
+  // put(j) when ok, with selects instead of a branch
+  __device__ __forceinline__ void put_if(bool ok, int j) {
+    const unsigned long long nb = (b >> 16) | ((unsigned long long)(unsigned)j << 48);
+    b = ok ? nb : b;
+    n += ok ? 1 : 0;
   }
   __device__ __forceinline__ uint2 packet() const {
     const unsigned long long x = b >> (16 * (4 - n));  // shift in kNoAtom for missing entries
@@ -351,8 +404,8 @@ __device__ __forceinline__ bool excluded_pair(int i, int j, int nw3) {
   return i < nw3 && j < nw3 && (i / 3) == (j / 3);
 }
 
-__device__ void build_list_impl(const Ctx& c);
-__device__ void filter_list_impl(const Ctx& c);
+__device__ H4D_PHASE void build_list_impl(const Ctx& cref);
+__device__ H4D_PHASE void filter_list_impl(const Ctx& cref);
 // full build: outer rows from the cell grid, then the Verlet rows filtered from them
 __device__ void build_list(const Ctx& c) {
   const u64 t0 = (c.tid == 0) ? gtimer() : 0;
@@ -376,7 +429,11 @@ __device__ void refresh_list(const Ctx& c) {
     c.R->refreshes++;
   }
 }
-__device__ void build_list_impl(const Ctx& c) {
+// Each phase of the engine is a function of its own (not inlined), with the context copied
+// to locals at entry: its loops get the whole register budget instead of sharing it with
+// whatever the caller keeps live across the call.
+__device__ H4D_PHASE void build_list_impl(const Ctx& cref) {
+  const Ctx c = cref;
   const Eng& e = *c.e;
   const RepC& R = c.r;
   GView& v = const_cast<GView&>(c.v);
@@ -451,6 +508,7 @@ __device__ void build_list_impl(const Ctx& c) {
   // without cells, "cell" k is the k-th chunk of 32 home atoms and every atom is a candidate
   const int ncell_rows = (nc > 0) ? nc * nc * nc : (n + 31) / 32;
   const int maxo = e.max_out;
+  const bool has_water = R.nw3 > 0;  // uniform: the exclusion test only where waters exist
   int overflow = 0;
   // Work items are (cell, home pass of up to 32 atoms), handed out through a shared
   // counter so clustered (dense) cells do not leave one warp with all the work.  Without
@@ -531,15 +589,14 @@ __device__ void build_list_impl(const Ctx& c) {
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int j = jj[u];
-            const bool ok = act && near[u] && (j != (int)kNoAtom) && (j != i) && !excluded_pair(i, j, R.nw3);
-            if (ok) {
-              rb.put(j);
-              ++cnt;
-              if (rb.n == 4) {
-                if (cnt <= maxo)
-                  reinterpret_cast<uint2*>(e.nbr_out)[out_packet_index(e, R, i, (cnt - 1) >> 2)] = rb.packet();
-                rb.init();
-              }
+            const bool ok = act && near[u] && (j != (int)kNoAtom) && (j != i) &&
+                            !(has_water && excluded_pair(i, j, R.nw3));
+            rb.put_if(ok, j);
+            cnt += ok ? 1 : 0;
+            if (rb.n == 4) {
+              if (cnt <= maxo)
+                reinterpret_cast<uint2*>(e.nbr_out)[out_packet_index(e, R, i, (cnt - 1) >> 2)] = rb.packet();
+              rb.init();
             }
           }
         }
@@ -565,7 +622,8 @@ __device__ void build_list_impl(const Ctx& c) {
 // Verlet rows filtered from the outer rows: one thread per atom streams its outer row
 // (one 8-byte packet load per four candidates) and keeps the candidates inside r_list, in
 // outer-row order, so the Verlet rows are as deterministic as the outer ones.
-__device__ void filter_list_impl(const Ctx& c) {
+__device__ H4D_PHASE void filter_list_impl(const Ctx& cref) {
+  const Ctx c = cref;
   const Eng& e = *c.e;
   const RepC& R = c.r;
   const GView& v = c.v;
@@ -592,13 +650,12 @@ __device__ void filter_list_impl(const Ctx& c) {
       for (int u = 0; u < 4; ++u) pj[u] = v.pos[jj[u] == kNoAtom ? i : jj[u]];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        if (jj[u] != kNoAtom && fixed_d2(pi, pj[u]) <= R.T_list) {
-          rb.put(jj[u]);
-          ++cnt;
-          if (rb.n == 4) {
-            if (cnt <= maxn) nbr2[packet_index(e, R, i, (cnt - 1) >> 2, ltpa)] = rb.packet();
-            rb.init();
-          }
+        const bool ok = jj[u] != kNoAtom && fixed_d2(pi, pj[u]) <= R.T_list;
+        rb.put_if(ok, jj[u]);
+        cnt += ok ? 1 : 0;
+        if (rb.n == 4) {
+          if (cnt <= maxn) nbr2[packet_index(e, R, i, (cnt - 1) >> 2, ltpa)] = rb.packet();
+          rb.init();
         }
       }
       q = qn;
@@ -618,7 +675,7 @@ __device__ void filter_list_impl(const Ctx& c) {
 //            4 = flyer rows compute protocol work with previous altitude w_prev
 // ------------------------------------------------------------------------------------
 template <int SYS, bool NEMD>
-__device__ void force_pass_impl(const Ctx& c, int mode, float w_prev, double* kin_out);
+__device__ H4D_PHASE void force_pass_impl(const Ctx& cref, int mode, float w_prev, double* kin_out);
 // mode bits: 1 = apply the second half kick, 2 = return the kinetic energy after it,
 //            4 = flyer rows accumulate the protocol work between w_prev and the current w.
 // NEMD = false assumes every altitude is zero (equilibrium MD).
@@ -630,7 +687,8 @@ __device__ void force_pass(const Ctx& c, int mode, float w_prev, double* kin_out
 }
 
 template <int SYS, bool NEMD>
-__device__ void force_pass_impl(const Ctx& c, int mode, float w_prev, double* kin_out) {
+__device__ H4D_PHASE void force_pass_impl(const Ctx& cref, int mode, float w_prev, double* kin_out) {
+  const Ctx c = cref;
   const Eng& e = *c.e;
   const RepC& R = c.r;
   const Pot& P = e.pot;
@@ -645,7 +703,8 @@ __device__ void force_pass_impl(const Ctx& c, int mode, float w_prev, double* ki
   const float half_dt = 0.5f * (float)e.proto.dt;
   const uint2* packets = nbr_packets(e, R);
   const size_t pstride = (size_t)R.cap_atoms << ltpa;
-  float kin = 0.0f;
+  long long kin = 0;  // m v^2 of this thread's atoms, fixed point (exact, order-free sum)
+  int kbad = 0;
   for (int a0 = 0; a0 < n; a0 += nsub) {
     const int i = a0 + sub;
     const bool active = i < n;
@@ -664,6 +723,47 @@ __device__ void force_pass_impl(const Ctx& c, int mode, float w_prev, double* ki
       const int nP = (cnt + 3) >> 2;  // packets of the row; this lane owns lin, lin+tpa, ...
       const int npk = (nP > lin) ? (nP - lin + tpa - 1) >> ltpa : 0;
       uint2 q = (npk > 0) ? pk[0] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+      if (SYS == H4D_SYS_LJ) {
+        // LJ electrolyte.  Padding slots read the sentinel (its infinite altitude puts it
+        // beyond every cut-off), and the charge sign of a pair is the parity of i + j
+        // (cations even, anions odd): the same values as the generic loop below, with
+        // neither a branch nor a table load per slot.
+        const unsigned capa = (unsigned)R.cap_atoms;
+        const unsigned kq_i = __float_as_uint(P.kq[0]) ^ ((unsigned)i << 31);
+        for (int p = 0; p < npk; ++p) {
+          const uint2 qn = (p + 1 < npk) ? pk[(size_t)(p + 1) * pstride] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+          const unsigned jw[4] = {q.x & 0xFFFFu, q.x >> 16, q.y & 0xFFFFu, q.y >> 16};
+          uint4 pj[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) pj[u] = v.pos[min(jw[u], capa)];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float dx = (float)(int)(pj[u].x - pi.x) * scale;
+            const float dy = (float)(int)(pj[u].y - pi.y) * scale;
+            const float dz = (float)(int)(pj[u].z - pi.z) * scale;
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float wj = wbits(pj[u]);  // 0, a flyer's altitude, or +inf (sentinel)
+            PairCoef<SYS> cf;
+            cf.sig2 = P.sig2[0];
+            cf.eps4 = P.eps4[0];
+            cf.ljshift = P.ljshift[0];
+            cf.kq = __uint_as_float(kq_i ^ (jw[u] << 31));  // kq[1] = -kq[0] for charges +q/-q
+            float g = 1.0f;
+            if (NEMD) {
+              const float dw = wi - wj;
+              r2 = fmaf(dw, dw, r2);
+              g = (wnz_i != (wj != 0.0f)) ? gscr : 1.0f;
+            } else {
+              r2 = fmaf(wj, wj, r2);  // + 0 for every atom, +inf for the sentinel
+            }
+            const float fr = pair_fr<SYS>(P, cf, r2, g);
+            fx = fmaf(-fr, dx, fx);
+            fy = fmaf(-fr, dy, fy);
+            fz = fmaf(-fr, dz, fz);
+          }
+          q = qn;
+        }
+      } else
       for (int p = 0; p < npk; ++p) {
         const uint2 qn = (p + 1 < npk) ? pk[(size_t)(p + 1) * pstride] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
         const int jj[4] = {(int)(q.x & 0xFFFFu), (int)(q.x >> 16), (int)(q.y & 0xFFFFu), (int)(q.y >> 16)};
@@ -757,12 +857,15 @@ __device__ void force_pass_impl(const Ctx& c, int mode, float w_prev, double* ki
         }
         if (mode & 2) {
           const float vx = h.x + l.x, vy = h.y + l.y, vz = h.z + l.z;
-          kin += P.m_f[ti] * fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+          kin += to_fx(P.m_f[ti] * fmaf(vx, vx, fmaf(vy, vy, vz * vz)), kbad);
         }
       }
     }
   }
-  if (mode & 2) *kin_out = group_sum(c, (double)kin) * 0.5;
+  if (mode & 2) {
+    if (kbad) v.s->flag_nan = 1;
+    *kin_out = 0.5 * (double)group_sum_fx(c, kin) / (double)kFxScale;
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -817,8 +920,12 @@ __device__ void water_kick_drift(const Ctx& c, int m, float alpha, float& d1, fl
   const int ca[3] = {0, 0, 1}, cb[3] = {1, 2, 2};
   const float dd[3] = {(float)P.d_oh2, (float)P.d_oh2, (float)P.d_hh2};
   float dv[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-  for (int it = 0; it < 100; ++it) {
-    float worst = 0.f;
+  // iterate to the tolerance (2e-7, near the FP32 floor); 100 iterations that end with a
+  // violation above 1e-3 (or a non-finite one) mean the bonds could not be restored
+  bool converged = false;
+  float worst = 0.f;
+  for (int it = 0; it < 100 && !converged; ++it) {
+    worst = 0.f;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const int a = ca[q], b = cb[q];
@@ -842,8 +949,9 @@ __device__ void water_kick_drift(const Ctx& c, int m, float alpha, float& d1, fl
         dv[b][k] += db;
       }
     }
-    if (worst < 2e-7f) break;
+    converged = worst < 2e-7f;
   }
+  if (!(worst < 1e-3f)) v.s->flag_timeout = 1;
   for (int k = 0; k < 3; ++k) {
     const int ga = R.atom_off + a0 + k;
     ff_add(vh[k].x, vl[k].x, dv[k][0] / h);
@@ -876,7 +984,8 @@ __device__ double rattle_pass(const Ctx& c, bool want_k) {
   const float imv[3] = {P.inv_m[2], P.inv_m[3], P.inv_m[3]};
   const int ca[3] = {0, 0, 1}, cb[3] = {1, 2, 2};
   const float dd[3] = {(float)P.d_oh2, (float)P.d_oh2, (float)P.d_hh2};
-  double kin = 0.0;
+  long long kin = 0;  // kinetic energy, fixed point (exact, order-free sum)
+  int kbad = 0;
   for (int m = c.tid; m < R.n_water; m += c.T) {
     const int a0 = 3 * m;
     float4 vh[3], vl[3];
@@ -896,8 +1005,9 @@ __device__ double rattle_pass(const Ctx& c, bool want_k) {
       r[k][1] = (float)(int)(po[k].y - po[0].y) * R.scale;
       r[k][2] = (float)(int)(po[k].z - po[0].z) * R.scale;
     }
+    float worst = 0.f;
     for (int it = 0; it < 100; ++it) {
-      float worst = 0.f;
+      worst = 0.f;
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const int a = ca[q], b = cb[q];
@@ -917,6 +1027,9 @@ __device__ double rattle_pass(const Ctx& c, bool want_k) {
       }
       if (worst < 1e-7f) break;
     }
+    // the tolerance sits near the FP32 floor; a violation still above 1e-3 (or a non-finite
+    // one) after 100 iterations means the velocities could not be made consistent
+    if (!(worst < 1e-3f)) v.s->flag_timeout = 1;
     for (int k = 0; k < 3; ++k) {
       const int ga = R.atom_off + a0 + k;
       ff_add(vh[k].x, vl[k].x, dv[k][0]);
@@ -926,7 +1039,7 @@ __device__ double rattle_pass(const Ctx& c, bool want_k) {
       e.vlo[ga] = vl[k];
       if (want_k) {
         const float x = vh[k].x + vl[k].x, y = vh[k].y + vl[k].y, z = vh[k].z + vl[k].z;
-        kin += 0.5 * (double)(1.0f / imv[k]) * (double)fmaf(x, x, fmaf(y, y, z * z));
+        kin += to_fx(0.5f * (1.0f / imv[k]) * fmaf(x, x, fmaf(y, y, z * z)), kbad);
       }
     }
   }
@@ -936,13 +1049,15 @@ __device__ double rattle_pass(const Ctx& c, bool want_k) {
     const int ga = R.atom_off + a;
     const float4 h = e.vhi[ga], l = e.vlo[ga];
     const float x = h.x + l.x, y = h.y + l.y, z = h.z + l.z;
-    kin += 0.5 * (double)P.m_f[type_of(a, R.nw3)] * (double)fmaf(x, x, fmaf(y, y, z * z));
+    kin += to_fx(0.5f * P.m_f[type_of(a, R.nw3)] * fmaf(x, x, fmaf(y, y, z * z)), kbad);
   }
-  return group_sum(c, kin);
+  if (kbad) v.s->flag_nan = 1;
+  return (double)group_sum_fx(c, kin) / (double)kFxScale;
 }
 
 template <int SYS>
-__device__ void kick_drift(const Ctx& c, float alpha) {
+__device__ H4D_PHASE void kick_drift(const Ctx& cref, float alpha) {
+  const Ctx c = cref;
   const Eng& e = *c.e;
   const RepC& R = c.r;
   const Pot& P = e.pot;
@@ -1071,14 +1186,15 @@ __device__ void negate_velocities(const Ctx& c, int n) {
 // FP64 end-point energies
 // ------------------------------------------------------------------------------------
 // U over atoms [0, n_tot) leaving out ex0/ex1 (-1 = none); each unordered pair once
-__device__ double energy64_impl(const Ctx& c, int ex0, int ex1);
+__device__ H4D_PHASE double energy64_impl(const Ctx& cref, int ex0, int ex1);
 __device__ double energy64(const Ctx& c, int ex0, int ex1) {
   const u64 t0 = (c.tid == 0) ? gtimer() : 0;
   const double u = energy64_impl(c, ex0, ex1);
   if (c.tid == 0) c.R->t_energy_ns += (double)(gtimer() - t0);
   return u;
 }
-__device__ double energy64_impl(const Ctx& c, int ex0, int ex1) {
+__device__ H4D_PHASE double energy64_impl(const Ctx& cref, int ex0, int ex1) {
+  const Ctx c = cref;
   const Eng& e = *c.e;
   const RepC& R = c.r;
   const Pot& P = e.pot;
@@ -1087,9 +1203,13 @@ __device__ double energy64_impl(const Ctx& c, int ex0, int ex1) {
   const double scale = R.L * 0x1.0p-32;
   const double gscr = exp(-P.dkappa_sr * (double)v.s->w_cur);
   const double rc2max = P.drc2_lj > P.drc2_c ? P.drc2_lj : P.drc2_c;
-  double acc = 0.0, comp = 0.0;
+  // per-atom Kahan sums over the row (j > i), then a sum over atoms in a fixed order
   for (int i = c.tid; i < n; i += c.T) {
-    if (i == ex0 || i == ex1) continue;
+    double acc = 0.0, comp = 0.0;
+    if (i == ex0 || i == ex1) {
+      e.red[R.atom_off + i] = 0.0;
+      continue;
+    }
     const uint4 pi = v.pos[i];
     const int ti = type_of(i, R.nw3);
     const double wi = (double)wbits(pi);
@@ -1111,8 +1231,9 @@ __device__ double energy64_impl(const Ctx& c, int ex0, int ex1) {
       comp = (t - acc) - y;
       acc = t;
     }
+    e.red[R.atom_off + i] = acc;
   }
-  return group_sum(c, acc);
+  return fixed_order_sum(c, e.red + R.atom_off, n);
 }
 
 __device__ double kinetic64(const Ctx& c) {
@@ -1120,30 +1241,33 @@ __device__ double kinetic64(const Ctx& c) {
   const RepC& R = c.r;
   const int n = c.v.s->n_tot;
   const int fly0 = c.v.s->fly0, fly1 = c.v.s->fly1;
-  double acc = 0.0;
   for (int a = c.tid; a < n; a += c.T) {
-    if (a == fly0 || a == fly1) continue;
     const int ga = R.atom_off + a;
+    if (a == fly0 || a == fly1) {
+      e.red[ga] = 0.0;
+      continue;
+    }
     const float4 h = e.vhi[ga], l = e.vlo[ga];
     const double vx = (double)h.x + (double)l.x, vy = (double)h.y + (double)l.y,
                  vz = (double)h.z + (double)l.z;
-    acc += 0.5 * e.pot.dm[type_of(a, R.nw3)] * (vx * vx + vy * vy + vz * vz);
+    e.red[ga] = 0.5 * e.pot.dm[type_of(a, R.nw3)] * (vx * vx + vy * vy + vz * vz);
   }
-  return group_sum(c, acc);
+  return fixed_order_sum(c, e.red + R.atom_off, n);
 }
 
 // ------------------------------------------------------------------------------------
 // Thermostat (equilibrium MD only): CSVR (Bussi, Donadio, Parrinello 2007, Eq. A7) with
 // the chi-square variate from the Marsaglia-Tsang gamma sampler (ACM TOMS 2000).
 // ------------------------------------------------------------------------------------
-__device__ double chi2_variate(const Eng& e, const Rep& R, u64 rep_id, u64 step, double dof) {
+__device__ double chi2_variate(const Eng& e, const Rep& R, u64 rep_id, u64 step, double dof, int* timed_out) {
   double k = 0.5 * dof;
   if (k <= 0.0) return 0.0;
   const double k0 = k;
   if (k < 1.0) k += 1.0;
   const double d = k - 1.0 / 3.0, cc = 1.0 / sqrt(9.0 * d);
   double g = d, boost = 1.0;
-  for (u64 attempt = 0; attempt < 4096; ++attempt) {
+  bool done = false;
+  for (u64 attempt = 0; attempt < 4096 && !done; ++attempt) {
     u64 r[4];
     draw4(e.seed, rep_id, step, attempt, kPurGamma, r);
     const double z = gauss_c(r[0], r[1]);
@@ -1154,13 +1278,14 @@ __device__ double chi2_variate(const Eng& e, const Rep& R, u64 rep_id, u64 step,
     if (log(u) < 0.5 * z * z + d - d * t + d * log(t)) {
       g = d * t;
       if (k0 < 1.0) boost = pow(u01_open(r[3]), 1.0 / k0);
-      break;
+      done = true;
     }
   }
+  if (!done) *timed_out = 1;  // 4096 rejections in a row: reported, the mean is used
   return 2.0 * g * boost;
 }
 
-__device__ double csvr_alpha(const Eng& e, const Rep& R, u64 rep_id, u64 step, double K, int n) {
+__device__ double csvr_alpha(const Eng& e, const Rep& R, u64 rep_id, u64 step, double K, int n, int* timed_out) {
   const double dof = 3.0 * n - 3.0 * R.n_water;
   if (dof < 1.0 || e.proto.tau_t <= 0.0 || K <= 0.0) return 1.0;
   const double Kbar = 0.5 * dof / e.proto.beta;
@@ -1168,7 +1293,7 @@ __device__ double csvr_alpha(const Eng& e, const Rep& R, u64 rep_id, u64 step, d
   u64 r[4];
   draw4(e.seed, rep_id, step, 0, kPurThermo, r);
   const double R1 = gauss_c(r[0], r[1]);
-  const double S = chi2_variate(e, R, rep_id, step, dof - 1.0);
+  const double S = chi2_variate(e, R, rep_id, step, dof - 1.0, timed_out);
   const double Knew = K + (1.0 - cdec) * (Kbar * (S + R1 * R1) / dof - K) +
                       2.0 * R1 * sqrt(Kbar * K * (1.0 - cdec) * cdec / dof);
   double a = sqrt(Knew / K);
@@ -1202,12 +1327,31 @@ __device__ void initial_forces(const Ctx& c) {
 
 // equilibrium MD: n_steps velocity-Verlet steps at w = 0 with the CSVR thermostat
 template <int SYS>
+__device__ H4D_PHASE float md_steps(const Ctx& cref, int n_steps);
+
+template <int SYS>
 __device__ void md_phase(const Ctx& c, int n_steps) {
   const Eng& e = *c.e;
   Rep& R = *c.R;
   GScal* S = c.v.s;
-  if (c.tid == 0) S->flag_nan = 0;
+  if (c.tid == 0) { S->flag_nan = 0; S->flag_timeout = 0; }
   initial_forces<SYS>(c);
+  const float alpha = md_steps<SYS>(c, n_steps);
+  if (alpha != 1.0f) scale_velocities(c, alpha);
+  c.sync();
+  if (c.tid == 0 && S->flag_nan) R.err |= 2;
+  if (c.tid == 0 && S->flag_overflow) R.err |= 1;
+  if (c.tid == 0 && S->flag_timeout) R.err |= 4;
+}
+
+// equilibrium MD steps with the CSVR thermostat, out of line like the NEMD loop; returns
+// the last thermostat factor (applied by the caller)
+template <int SYS>
+__device__ H4D_PHASE float md_steps(const Ctx& cref, int n_steps) {
+  const Ctx c = cref;
+  const Eng& e = *c.e;
+  Rep& R = *c.R;
+  GScal* S = c.v.s;
   float alpha = 1.0f;
   for (int st = 0; st < n_steps; ++st) {
     kick_drift<SYS>(c, alpha);
@@ -1223,7 +1367,7 @@ __device__ void md_phase(const Ctx& c, int n_steps) {
     }
     if (c.tid == 0) {
       const int n = S->n_tot;
-      double a = csvr_alpha(e, R, (u64)(c.R - e.rep), R.step_ctr, K, n);
+      double a = csvr_alpha(e, R, R.key, R.step_ctr, K, n, &S->flag_timeout);
       if (!isfinite(a) || !isfinite(K)) { a = 1.0; S->flag_nan = 1; }
       S->alpha_th = a;
       R.step_ctr++;
@@ -1232,10 +1376,73 @@ __device__ void md_phase(const Ctx& c, int n_steps) {
     c.sync();
     alpha = (float)S->alpha_th;
   }
-  if (alpha != 1.0f) scale_velocities(c, alpha);
-  c.sync();
-  if (c.tid == 0 && S->flag_nan) R.err |= 2;
-  if (c.tid == 0 && S->flag_overflow) R.err |= 1;
+  return alpha;
+}
+
+// The NEMD trajectory of a trial (Sec. II.A, Eq. 2 protocol), out of line: its step loop
+// (force passes, list refreshes) gets the whole register budget of the engine instead of
+// sharing it with the trial's scalars, which the caller keeps across the call.
+template <int SYS>
+__device__ H4D_PHASE void nemd_steps(const Ctx& cref, int n_steps) {
+  const Ctx c = cref;
+  const Eng& e = *c.e;
+  Rep& R = *c.R;
+  GScal* S = c.v.s;
+  const int ins = S->ins;
+  const bool single = e.proto.single != 0;
+  const int f0 = S->fly0, f1 = S->fly1;
+  if (n_steps > 0) {
+    force_pass<SYS>(c, 0, 0.f, nullptr);
+    c.sync();
+  }
+  for (int k = 0; k < n_steps; ++k) {
+    kick_drift<SYS>(c, 1.0f);
+    c.sync();
+    maybe_rebuild(c);
+    // the altitude before this step, from the schedule (S->w_cur holds the same value, but
+    // thread 0 overwrites it below with no barrier in between when no rebuild happens)
+    const float w_prev = (float)altitude(e.proto, ins, k);
+    const float w_next = (float)altitude(e.proto, ins, k + 1);
+    const float w_next_a = (float)(e.proto.rw * altitude(e.proto, ins, k + 1));
+    if (c.tid == 0) {
+      uint4 p0 = c.v.pos[f0];
+      p0.w = __float_as_uint(w_next);
+      c.v.pos[f0] = p0;
+      if (!single) {
+        uint4 p1 = c.v.pos[f1];
+        p1.w = __float_as_uint(w_next_a);
+        c.v.pos[f1] = p1;
+      }
+      S->w_cur = w_next;
+      S->g_scr = expf(-e.pot.kappa_sr * (single ? w_next : 0.5f * (w_next + w_next_a)));
+    }
+    c.sync();
+    force_pass<SYS>(c, 1 | 4, w_prev, nullptr);
+    c.sync();
+    if (SYS == H4D_SYS_AQ && c.r.n_water > 0) {
+      rattle_pass(c, false);
+      c.sync();
+    }
+    if (c.tid == 0) {
+      double dff = 0.0;
+      if (e.proto.rw != 1.0) {
+        // the flyers' own pair: unscreened, its altitude gap changes with the step
+        const uint4 a = c.v.pos[f0], b = c.v.pos[f1];
+        const double s = R.L * 0x1.0p-32;
+        const double dx = (double)(int)(b.x - a.x) * s, dy = (double)(int)(b.y - a.y) * s,
+                     dz = (double)(int)(b.z - a.z) * s;
+        const double r3 = dx * dx + dy * dy + dz * dz;
+        const double dn = (double)w_next - (double)w_next_a;
+        const double dp = (double)w_prev - (double)(float)(e.proto.rw * altitude(e.proto, ins, k));
+        const int ta = type_of(f0, c.r.nw3), tb = type_of(f1, c.r.nw3);
+        dff = pair_u64(e.pot, ta, tb, r3 + dn * dn, 1.0) - pair_u64(e.pot, ta, tb, r3 + dp * dp, 1.0);
+      }
+      const double y = (S->dW[0] + S->dW[1] + dff) - S->wprot_c;
+      const double t = S->wprot + y;
+      S->wprot_c = (t - S->wprot) - y;
+      S->wprot = t;
+    }
+  }
 }
 
 // one pair-exchange trial (Sec. II.A); readings as in the oracle:
@@ -1551,7 +1758,7 @@ __device__ void trial_phase(const Ctx& c) {
   const Eng& e = *c.e;
   Rep& R = *c.R;
   GScal* S = c.v.s;
-  const u64 rep_id = (u64)(c.R - e.rep);
+  const u64 rep_id = R.key;
   if (c.tid == 0) {
     const u64 t = R.trial_ctr++;
     u64 b0[4], b1[4], b2[4], b3[4], b4[4];
@@ -1615,7 +1822,8 @@ __device__ void trial_phase(const Ctx& c) {
   }
   c.sync();
   const int N = S->n_before;
-  const int n = R.nw3 + 2 * N;
+  const bool single = e.proto.single != 0;  // one flyer (the draws of the anion are unused)
+  const int n = R.nw3 + e.proto.unit * N;
   const int ins = S->ins;
   if (S->flip_s) negate_velocities(c, n);
   if (S->status != 0) {
@@ -1703,30 +1911,34 @@ __device__ void trial_phase(const Ctx& c) {
     if (ins) {
       const int ci = n, ai = n + 1;
       c.v.pos[ci] = make_uint4(S->xfly[0], S->xfly[1], S->xfly[2], __float_as_uint(w0));
-      c.v.pos[ai] = make_uint4(S->xfly[3], S->xfly[4], S->xfly[5], __float_as_uint(w0a));
       e.vhi[R.atom_off + ci] = make_float4((float)S->vfly[0], (float)S->vfly[1], (float)S->vfly[2], 0.f);
       e.vlo[R.atom_off + ci] = make_float4((float)(S->vfly[0] - (double)(float)S->vfly[0]),
                                            (float)(S->vfly[1] - (double)(float)S->vfly[1]),
                                            (float)(S->vfly[2] - (double)(float)S->vfly[2]), 0.f);
-      e.vhi[R.atom_off + ai] = make_float4((float)S->vfly[3], (float)S->vfly[4], (float)S->vfly[5], 0.f);
-      e.vlo[R.atom_off + ai] = make_float4((float)(S->vfly[3] - (double)(float)S->vfly[3]),
-                                           (float)(S->vfly[4] - (double)(float)S->vfly[4]),
-                                           (float)(S->vfly[5] - (double)(float)S->vfly[5]), 0.f);
+      if (!single) {
+        c.v.pos[ai] = make_uint4(S->xfly[3], S->xfly[4], S->xfly[5], __float_as_uint(w0a));
+        e.vhi[R.atom_off + ai] = make_float4((float)S->vfly[3], (float)S->vfly[4], (float)S->vfly[5], 0.f);
+        e.vlo[R.atom_off + ai] = make_float4((float)(S->vfly[3] - (double)(float)S->vfly[3]),
+                                             (float)(S->vfly[4] - (double)(float)S->vfly[4]),
+                                             (float)(S->vfly[5] - (double)(float)S->vfly[5]), 0.f);
+      }
       S->fly0 = ci;
-      S->fly1 = ai;
-      S->n_tot = n + 2;
+      S->fly1 = single ? -1 : ai;
+      S->n_tot = n + e.proto.unit;
     } else {
-      S->fly0 = R.nw3 + 2 * S->cat;
-      S->fly1 = R.nw3 + 2 * S->ani + 1;
+      S->fly0 = R.nw3 + e.proto.unit * S->cat;
+      S->fly1 = single ? -1 : R.nw3 + 2 * S->ani + 1;
       S->n_tot = n;
     }
     S->w_cur = w0;
-    S->g_scr = expf(-e.pot.kappa_sr * (0.5f * (w0 + w0a)));
+    // screening at the mean altitude of the flyers (Sec. II.B.2)
+    S->g_scr = expf(-e.pot.kappa_sr * (single ? w0 : 0.5f * (w0 + w0a)));
     S->wprot = 0.0;
     S->wprot_c = 0.0;
     S->dW[0] = S->dW[1] = 0.0;
     S->flag_nan = 0;       // a blow-up inside NEMD only rejects this trial
     S->flag_overflow = 0;  // so does a neighbour row that overflowed during it
+    S->flag_timeout = 0;   // and a rigid-water constraint that did not converge
   }
   c.sync();
   build_list(c);
@@ -1735,53 +1947,7 @@ __device__ void trial_phase(const Ctx& c) {
   const double Us = ins ? energy64(c, f0, f1) : energy64(c, -1, -1);
   const double Ks = kinetic64(c);
   const int n_steps = inst ? 0 : e.proto.n_f;
-  if (n_steps > 0) {
-    force_pass<SYS>(c, 0, 0.f, nullptr);
-    c.sync();
-  }
-  for (int k = 0; k < n_steps; ++k) {
-    kick_drift<SYS>(c, 1.0f);
-    c.sync();
-    maybe_rebuild(c);
-    const float w_prev = S->w_cur;
-    const float w_next = (float)altitude(e.proto, ins, k + 1);
-    const float w_next_a = (float)(e.proto.rw * altitude(e.proto, ins, k + 1));
-    if (c.tid == 0) {
-      uint4 p0 = c.v.pos[f0], p1 = c.v.pos[f1];
-      p0.w = __float_as_uint(w_next);
-      p1.w = __float_as_uint(w_next_a);
-      c.v.pos[f0] = p0;
-      c.v.pos[f1] = p1;
-      S->w_cur = w_next;
-      S->g_scr = expf(-e.pot.kappa_sr * (0.5f * (w_next + w_next_a)));
-    }
-    c.sync();
-    force_pass<SYS>(c, 1 | 4, w_prev, nullptr);
-    c.sync();
-    if (SYS == H4D_SYS_AQ && c.r.n_water > 0) {
-      rattle_pass(c, false);
-      c.sync();
-    }
-    if (c.tid == 0) {
-      double dff = 0.0;
-      if (e.proto.rw != 1.0) {
-        // the flyers' own pair: unscreened, its altitude gap changes with the step
-        const uint4 a = c.v.pos[f0], b = c.v.pos[f1];
-        const double s = R.L * 0x1.0p-32;
-        const double dx = (double)(int)(b.x - a.x) * s, dy = (double)(int)(b.y - a.y) * s,
-                     dz = (double)(int)(b.z - a.z) * s;
-        const double r3 = dx * dx + dy * dy + dz * dz;
-        const double dn = (double)w_next - (double)w_next_a;
-        const double dp = (double)w_prev - (double)(float)(e.proto.rw * altitude(e.proto, ins, k));
-        const int ta = type_of(f0, c.r.nw3), tb = type_of(f1, c.r.nw3);
-        dff = pair_u64(e.pot, ta, tb, r3 + dn * dn, 1.0) - pair_u64(e.pot, ta, tb, r3 + dp * dp, 1.0);
-      }
-      const double y = (S->dW[0] + S->dW[1] + dff) - S->wprot_c;
-      const double t = S->wprot + y;
-      S->wprot_c = (t - S->wprot) - y;
-      S->wprot = t;
-    }
-  }
+  if (n_steps > 0) nemd_steps<SYS>(c, n_steps);
   c.sync();
   // H_end: insertion has everyone in 3D, deletion leaves the flyers out
   const double Ue = ins ? energy64(c, -1, -1) : energy64(c, f0, f1);
@@ -1806,11 +1972,14 @@ __device__ void trial_phase(const Ctx& c) {
     const double dH = (Ue + Ke) - (Us + Ks);
     const double V = R.L * R.L * R.L;
     double bdm, xacc;
+    // the phase-space factor V/(N+1) once per flyer: squared for a pair (Eqs. 6, 8), once
+    // for a single particle (Sec. II.A, the pair rule translated to one flyer)
+    const double nfly = single ? 1.0 : 2.0;
     if (ins) {
-      bdm = e.proto.beta * dH - 2.0 * log(V / (double)(N + 1));  // Eq. 6
+      bdm = e.proto.beta * dH - nfly * log(V / (double)(N + 1));  // Eq. 6
       xacc = -bdm + e.proto.beta_mu;
     } else {
-      bdm = -e.proto.beta * dH - 2.0 * log(V / (double)N);       // Eq. 8
+      bdm = -e.proto.beta * dH - nfly * log(V / (double)N);       // Eq. 8
       xacc = bdm - e.proto.beta_mu;
     }
     const double x_phys = xacc;
@@ -1821,16 +1990,17 @@ __device__ void trial_phase(const Ctx& c) {
       S->lnq = log(sum / (double)(N + 1));
     }
     xacc += ins ? -S->lnq : S->lnq;  // proposal density relative to uniform placement
-    int status = (isfinite(dH) && !S->flag_nan && !S->flag_overflow) ? 0 : 3;
+    int status = (isfinite(dH) && !S->flag_nan && !S->flag_overflow && !S->flag_timeout) ? 0 : 3;
     S->flag_nan = 0;
     S->flag_overflow = 0;
+    S->flag_timeout = 0;
     int acc = (status == 0) && (S->ln_u < xacc) && !e.proto.no_accept;
     S->accept = acc;
     h4d_record rr;
     rr.move = ins; rr.accepted = acc; rr.n_before = N;
     rr.n_after = N + (acc ? (ins ? 1 : -1) : 0);
     rr.status = status;
-    rr.cation = ins ? -1 : S->cat; rr.anion = ins ? -1 : S->ani;
+    rr.cation = ins ? -1 : S->cat; rr.anion = (ins || single) ? -1 : S->ani;
     rr.cell_c = S->cell_c; rr.cell_a = S->cell_a; rr.instant = S->inst;
     rr.dH = dH; rr.beta_dM = bdm; rr.w_prot = S->wprot; rr.ln_u = S->ln_u; rr.x_acc = xacc; rr.ln_q = S->lnq;
     if (S->prec_slot >= 0) {
@@ -1851,11 +2021,21 @@ __device__ void trial_phase(const Ctx& c) {
   if (acc) {
     if (c.tid == 0) {
       if (ins) {
-        uint4 p0 = c.v.pos[f0], p1 = c.v.pos[f1];
-        p0.w = 0u; p1.w = 0u;  // altitude(n_f) of an insertion is 0
+        uint4 p0 = c.v.pos[f0];
+        p0.w = 0u;  // altitude(n_f) of an insertion is 0
         c.v.pos[f0] = p0;
-        c.v.pos[f1] = p1;
+        if (!single) {
+          uint4 p1 = c.v.pos[f1];
+          p1.w = 0u;
+          c.v.pos[f1] = p1;
+        }
         R.n_pairs = N + 1;
+      } else if (single) {
+        const int last = R.nw3 + (N - 1);  // swap-with-last
+        c.v.pos[f0] = c.v.pos[last];
+        e.vhi[R.atom_off + f0] = e.vhi[R.atom_off + last];
+        e.vlo[R.atom_off + f0] = e.vlo[R.atom_off + last];
+        R.n_pairs = N - 1;
       } else {
         // swap-with-last keeps the interleaved cation/anion layout
         const int lc = R.nw3 + 2 * (N - 1), la = lc + 1;
@@ -1879,7 +2059,7 @@ __device__ void trial_phase(const Ctx& c) {
   }
   c.sync();
   if (c.tid == 0) {
-    S->n_tot = R.nw3 + 2 * R.n_pairs;
+    S->n_tot = R.nw3 + e.proto.unit * R.n_pairs;
     S->fly0 = S->fly1 = -1;
     S->w_cur = 0.f;
     S->g_scr = 1.f;
@@ -1917,10 +2097,11 @@ __device__ bool setup_ctx(const Eng& e, char* smem, Ctx& c) {
   c.v = carve(smem + G.smem_off, R->cap_atoms, R->nc, c.T);
   GScal* S = c.v.s;
   if (c.tid == 0) {
-    S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0;
-    S->n_tot = R->nw3 + 2 * R->n_pairs;
+    S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0; S->flag_timeout = 0;
+    S->n_tot = R->nw3 + e.proto.unit * R->n_pairs;
     S->fly0 = S->fly1 = -1;
     S->w_cur = 0.f; S->g_scr = 1.f;
+    write_sentinel(c.v, R->cap_atoms);
   }
   c.sync();
   for (int a = c.tid; a < S->n_tot; a += c.T) c.v.pos[a] = e.pos[R->atom_off + a];
@@ -1935,6 +2116,12 @@ __global__ void __launch_bounds__(H4D_MAXTHREADS, H4D_MINBLOCKS) cycles_kernel(c
   if (!setup_ctx(e, smem, c)) return;
   Rep* R = c.R;
   GScal* S = c.v.s;
+  if (c.tid == 0) {
+    unsigned sm;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    R->smid = (int)sm;
+    R->t_begin = gtimer();
+  }
   for (long long cyc = 0; cyc < k_cycles; ++cyc) {
     u64 t0 = gtimer();
     if (n_eq > 0) md_phase<SYS>(c, n_eq);
@@ -1949,6 +2136,7 @@ __global__ void __launch_bounds__(H4D_MAXTHREADS, H4D_MINBLOCKS) cycles_kernel(c
   c.sync();
   for (int a = c.tid; a < S->n_tot; a += c.T) e.pos[R->atom_off + a] = c.v.pos[a];
   if (c.tid == 0 && S->flag_overflow) R->err |= 1;
+  if (c.tid == 0) R->t_end = gtimer();
 }
 
 // current U (FP64) and K of each replica
@@ -2031,11 +2219,12 @@ __global__ void __launch_bounds__(1024) eval_kernel(const __grid_constant__ Eng 
   c.v = carve(smem + G.smem_off, R->cap_atoms, R->nc, c.T);
   GScal* S = c.v.s;
   if (c.tid == 0) {
-    S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0;
-    S->n_tot = R->nw3 + 2 * R->n_pairs;
+    S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0; S->flag_timeout = 0;
+    S->n_tot = R->nw3 + e.proto.unit * R->n_pairs;
     S->fly0 = S->fly1 = -1;
     S->w_cur = wbar;
     S->g_scr = expf(-e.pot.kappa_sr * wbar);
+    write_sentinel(c.v, R->cap_atoms);
   }
   c.sync();
   for (int a = c.tid; a < S->n_tot; a += c.T) c.v.pos[a] = e.pos[R->atom_off + a];
@@ -2104,6 +2293,14 @@ int launch_list(const Eng& e, int n_ctas, int cta_threads, size_t smem, void* st
 }
 
 static int check(cudaError_t err) { return err == cudaSuccess ? H4D_OK : H4D_ECUDA; }
+
+int engine_binary_version(int* binary_version, int* ptx_version) {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, cycles_kernel<H4D_SYS_LJ>) != cudaSuccess) return H4D_ECUDA;
+  *binary_version = a.binaryVersion;
+  *ptx_version = a.ptxVersion;
+  return H4D_OK;
+}
 
 int launch_cycles(const Eng& e, int n_ctas, int cta_threads, size_t smem, long long k_cycles, int n_eq,
                   int do_trial, void* stream) {

@@ -48,6 +48,8 @@ struct Proto {
   double fw;  // species w_max: the anion's w_max is w_max + 0.5 (sig_c + sig_a) fw
   double rw;  // its ratio to the cation's (1 = one w_max); the anion's altitude is rw w
   double vex_edge;  // early rejection: edge of the excluded cube around the flying cation (0 = off)
+  int single;       // single-particle exchange: one flyer, one atom per exchange unit
+  int unit;         // atoms per exchange unit (2 for ion pairs, 1 for single particles)
 };
 
 struct Rep {
@@ -83,6 +85,9 @@ struct Rep {
   int prop_off;   // first cell of this replica in the grid arrays (a multiple of 32)
   int prec_off, prec_cap;  // training-record ring of this replica
   long long prec_count;
+  unsigned long long key; // second Philox key word of this replica's random stream
+  int smid, pad_s;        // SM of the group in the most recent launch
+  unsigned long long t_begin, t_end;  // global timer at that launch's start and end
 };
 
 struct Group {
@@ -109,6 +114,7 @@ struct Eng {
   int* ncnt_out;
   uint4* ref_out;     // positions at the last outer build
   h4d_record* rec;
+  double* red;        // per-atom partial sums of the fixed-order FP64 reductions
   // learned proposal: packed network, per-cell grid of every replica, training records
   PropNet net;
   int4* pg_cnt;         // [cells] cation, anion, water-O counts of the cell itself
@@ -125,14 +131,15 @@ struct Eng {
 
 // shared-memory bytes a group needs for a replica
 __host__ __device__ inline size_t smem_align16(size_t b) { return (b + 15) & ~(size_t)15; }
-// Per-group shared memory: positions, cell starts, cell fill counters / work-item prefix,
+// Per-group shared memory: positions (plus one sentinel slot after the last atom, which
+// neighbour-row padding points at), cell starts, cell fill counters / work-item prefix,
 // cell-sorted atom list (each cell padded to a multiple of 4 entries), the same list as
 // packed 8-bit coordinates, scalars.  Every region starts on a 16-byte boundary.
 __host__ __device__ inline size_t group_smem_bytes(int cap_atoms, int nc, int nthreads) {
   (void)nthreads;
   size_t ncell = nc > 0 ? (size_t)nc * nc * nc : 0;
   size_t slots = (size_t)cap_atoms + 3 * ncell;
-  size_t b = smem_align16(16 * (size_t)cap_atoms);
+  size_t b = smem_align16(16 * ((size_t)cap_atoms + 1));
   b += smem_align16(4 * (ncell + 1));
   b += smem_align16(4 * (ncell + 1));
   b += smem_align16(2 * slots);
@@ -151,6 +158,8 @@ int launch_forces(const Eng& e, int n_ctas, int cta_threads, size_t smem, int n_
 int launch_list(const Eng& e, int n_ctas, int cta_threads, size_t smem, void* stream);
 int launch_count_pairs(const Eng& e, int n_ctas, int cta_threads, size_t smem,
                        unsigned long long* out, void* stream);
+// compute capability the engine kernel was compiled for and its PTX version (x10 + minor)
+int engine_binary_version(int* binary_version, int* ptx_version);
 int launch_prop_eval(const Eng& e, int n_ctas, int cta_threads, size_t smem, int replica, float* feat_out,
                      void* stream);
 

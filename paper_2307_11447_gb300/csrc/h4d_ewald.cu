@@ -1,0 +1,200 @@
+// h4d_ewald.cu -- long-range Coulomb term of Sec. II.B.2 (Eqs. 9-10): the reciprocal-space
+// Ewald sum and the self energy of one configuration, scaled by the altitude screening
+// g^lr(wbar) = exp(-kappa_lr wbar).  Two kernels, both O(k-vectors x atoms):
+//   - structure factor: S(k) = sum_j q_j exp(i k.r_j) for every k of one half space;
+//   - forces: F_j = g (8 pi K q_j / V) sum_half A_k k [Re S sin(k.r_j) - Im S cos(k.r_j)].
+// The phase k.r_j / 2 pi = (n_x X_j + n_y Y_j + n_z Z_j) / 2^32 is formed exactly in 32-bit
+// integer arithmetic from the fixed-point coordinates X = round(x/L 2^32) (wrap-around is
+// the periodicity); its conversion to a float in [-1, 1) half turns is the only rounding
+// of the argument (at most 2^-24 of a half turn), whatever the size of k.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "../../include/h4d.h"
+
+namespace {
+
+constexpr int kTile = 256;  // atoms (or k-vectors) staged in shared memory per step
+
+struct KVec {
+  int nx, ny, nz;
+  float pad;
+};
+
+// S(k) of the half space: thread t of block b owns k-vector b*blockDim + t; atoms are
+// staged in tiles; each tile's terms are summed in FP32 and added to FP64 totals
+__global__ void __launch_bounds__(256) ewald_sk_kernel(const uint4* __restrict__ xq, int n, const KVec* __restrict__ kv,
+                                                       int nk, double2* __restrict__ sk) {
+  __shared__ uint4 tile[kTile];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const KVec kk = (k < nk) ? kv[k] : KVec{0, 0, 0, 0.f};
+  double re = 0.0, im = 0.0;
+  for (int t0 = 0; t0 < n; t0 += kTile) {
+    const int m = min(kTile, n - t0);
+    __syncthreads();
+    for (int a = threadIdx.x; a < m; a += blockDim.x) tile[a] = xq[t0 + a];
+    __syncthreads();
+    float fr = 0.f, fi = 0.f;
+    for (int a = 0; a < m; ++a) {
+      const uint4 p = tile[a];
+      const unsigned ph = (unsigned)kk.nx * p.x + (unsigned)kk.ny * p.y + (unsigned)kk.nz * p.z;
+      float s, c;
+      sincospif((float)(int)ph * 4.656612873077393e-10f, &s, &c);  // 2 pi ph / 2^32 = pi (int)ph / 2^31
+      const float q = __uint_as_float(p.w);
+      fr = fmaf(q, c, fr);
+      fi = fmaf(q, s, fi);
+    }
+    re += (double)fr;
+    im += (double)fi;
+  }
+  if (k < nk) sk[k] = make_double2(re, im);
+}
+
+// forces: thread t owns atom b*blockDim + t; the k-vectors and their weighted structure
+// factors (A_k Re S, A_k Im S) are staged in tiles
+struct KW {
+  int nx, ny, nz;
+  float pad;
+  float ar, ai;  // A_k Re S(k), A_k Im S(k)
+  float pad2, pad3;
+};
+
+__global__ void __launch_bounds__(256) ewald_force_kernel(const uint4* __restrict__ xq, int n, const KW* __restrict__ kw,
+                                                          int nk, float two_pi_over_L, double pref,
+                                                          double* __restrict__ F) {
+  __shared__ KW tile[kTile];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint4 p = (j < n) ? xq[j] : make_uint4(0u, 0u, 0u, 0u);
+  double gx = 0.0, gy = 0.0, gz = 0.0;
+  for (int t0 = 0; t0 < nk; t0 += kTile) {
+    const int m = min(kTile, nk - t0);
+    __syncthreads();
+    for (int a = threadIdx.x; a < m; a += blockDim.x) tile[a] = kw[t0 + a];
+    __syncthreads();
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    for (int a = 0; a < m; ++a) {
+      const KW w = tile[a];
+      const unsigned ph = (unsigned)w.nx * p.x + (unsigned)w.ny * p.y + (unsigned)w.nz * p.z;
+      float s, c;
+      sincospif((float)(int)ph * 4.656612873077393e-10f, &s, &c);
+      const float f = fmaf(w.ar, s, -w.ai * c);  // A_k [Re S sin - Im S cos]
+      fx = fmaf(f, (float)w.nx, fx);
+      fy = fmaf(f, (float)w.ny, fy);
+      fz = fmaf(f, (float)w.nz, fz);
+    }
+    gx += (double)fx;
+    gy += (double)fy;
+    gz += (double)fz;
+  }
+  if (j < n) {
+    const double qj = (double)__uint_as_float(p.w);
+    const double c = pref * qj * (double)two_pi_over_L;  // k = (2 pi / L) n
+    F[3 * j] = c * gx;
+    F[3 * j + 1] = c * gy;
+    F[3 * j + 2] = c * gz;
+  }
+}
+
+int type_of_host(int a, int nw3) { return a < nw3 ? ((a % 3 == 0) ? 2 : 3) : ((a - nw3) & 1); }
+
+}  // namespace
+
+#define CKE(x)                       \
+  do {                               \
+    if ((x) != cudaSuccess) {        \
+      rc = H4D_ECUDA;                \
+      goto done;                     \
+    }                                \
+  } while (0)
+
+extern "C" int h4d_ewald_lr(const h4d_params* params, double L, int32_t n_water, int32_t n, const double* x,
+                            double alpha, int32_t kmax, double wbar, double kappa_lr, double* U_recip,
+                            double* U_self, double* F) {
+  if (!params || !x || n < 0 || n_water < 0 || 3 * n_water > n || !(L > 0) || !(alpha > 0) || kmax < 1 ||
+      kmax > 64 || !(wbar >= 0) || !(kappa_lr >= 0))
+    return H4D_EINVAL;
+  const int single = params->exchange == H4D_EXCHANGE_SINGLE;
+  const int nw3 = 3 * n_water;
+  const double K = params->kcoul, V = L * L * L;
+  const double g = std::exp(-kappa_lr * wbar);  // Eq. 10
+  // atoms: fixed-point coordinates and charges
+  std::vector<uint4> xq(n > 0 ? n : 1);
+  double qq = 0.0;
+  for (int a = 0; a < n; ++a) {
+    const int t = single && a >= nw3 ? 0 : type_of_host(a, nw3);
+    const float q = (float)params->q[t];
+    qq += (double)params->q[t] * params->q[t];
+    uint32_t X[3];
+    for (int d = 0; d < 3; ++d) {
+      double y = x[3 * a + d] - L * std::floor(x[3 * a + d] / L);
+      double s = std::nearbyint(y / L * 4294967296.0);
+      X[d] = (uint32_t)((uint64_t)s & 0xffffffffULL);
+    }
+    uint32_t qb;
+    std::memcpy(&qb, &q, 4);
+    xq[a] = make_uint4(X[0], X[1], X[2], qb);
+  }
+  // half space of k-vectors: n_x > 0, or n_x = 0 and n_y > 0, or n_x = n_y = 0 and n_z > 0
+  std::vector<KVec> kv;
+  std::vector<double> A;
+  for (int nx = 0; nx <= kmax; ++nx)
+    for (int ny = -kmax; ny <= kmax; ++ny)
+      for (int nz = -kmax; nz <= kmax; ++nz) {
+        if (nx == 0 && (ny < 0 || (ny == 0 && nz <= 0))) continue;
+        const double kx = 2.0 * M_PI * nx / L, ky = 2.0 * M_PI * ny / L, kz = 2.0 * M_PI * nz / L;
+        const double k2 = kx * kx + ky * ky + kz * kz;
+        kv.push_back(KVec{nx, ny, nz, 0.f});
+        A.push_back(std::exp(-k2 / (4.0 * alpha * alpha)) / k2);
+      }
+  const int nk = (int)kv.size();
+  int rc = H4D_OK;
+  uint4* d_xq = nullptr;
+  KVec* d_kv = nullptr;
+  double2* d_sk = nullptr;
+  KW* d_kw = nullptr;
+  double* d_F = nullptr;
+  std::vector<double2> sk(nk);
+  std::vector<KW> kw(nk);
+  double u = 0.0;
+  if (n == 0) {
+    if (U_recip) *U_recip = 0.0;
+    if (U_self) *U_self = 0.0;
+    return H4D_OK;
+  }
+  CKE(cudaMalloc(&d_xq, sizeof(uint4) * n));
+  CKE(cudaMalloc(&d_kv, sizeof(KVec) * nk));
+  CKE(cudaMalloc(&d_sk, sizeof(double2) * nk));
+  CKE(cudaMemcpy(d_xq, xq.data(), sizeof(uint4) * n, cudaMemcpyHostToDevice));
+  CKE(cudaMemcpy(d_kv, kv.data(), sizeof(KVec) * nk, cudaMemcpyHostToDevice));
+  ewald_sk_kernel<<<(nk + 255) / 256, 256>>>(d_xq, n, d_kv, nk, d_sk);
+  CKE(cudaGetLastError());
+  CKE(cudaMemcpy(sk.data(), d_sk, sizeof(double2) * nk, cudaMemcpyDeviceToHost));
+  // U_recip = (2 pi K / V) sum_{all k != 0} A_k |S_k|^2 = (4 pi K / V) sum_half A_k |S_k|^2
+  for (int k = 0; k < nk; ++k) {
+    u += A[k] * (sk[k].x * sk[k].x + sk[k].y * sk[k].y);
+    kw[k] = KW{kv[k].nx, kv[k].ny, kv[k].nz, 0.f, (float)(A[k] * sk[k].x), (float)(A[k] * sk[k].y), 0.f, 0.f};
+  }
+  if (U_recip) *U_recip = g * 4.0 * M_PI * K / V * u;
+  if (U_self) *U_self = -g * K * alpha / std::sqrt(M_PI) * qq;
+  if (F) {
+    CKE(cudaMalloc(&d_kw, sizeof(KW) * nk));
+    CKE(cudaMalloc(&d_F, sizeof(double) * 3 * n));
+    CKE(cudaMemcpy(d_kw, kw.data(), sizeof(KW) * nk, cudaMemcpyHostToDevice));
+    // F_j = g (4 pi K q_j / V) sum_{all k} A_k k [Re S sin - Im S cos]: twice the half space
+    ewald_force_kernel<<<(n + 255) / 256, 256>>>(d_xq, n, d_kw, nk, (float)(2.0 * M_PI / L), g * 8.0 * M_PI * K / V,
+                                                 d_F);
+    CKE(cudaGetLastError());
+    CKE(cudaMemcpy(F, d_F, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+  }
+done:
+  cudaFree(d_xq);
+  cudaFree(d_kv);
+  cudaFree(d_sk);
+  cudaFree(d_kw);
+  cudaFree(d_F);
+  return rc;
+}

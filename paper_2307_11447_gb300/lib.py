@@ -59,6 +59,8 @@ class h4d_params(ctypes.Structure):
         ("skin_outer", ctypes.c_double),
         ("max_nbr", ctypes.c_int32),
         ("threads_per_atom", ctypes.c_int32),
+        ("exchange", ctypes.c_int32),
+        ("pad_exchange", ctypes.c_int32),
     ]
 
 
@@ -71,6 +73,7 @@ class h4d_system(ctypes.Structure):
         ("cap_pairs", ctypes.POINTER(ctypes.c_int32)),
         ("host_x", ctypes.POINTER(ctypes.c_double)),
         ("host_v", ctypes.POINTER(ctypes.c_double)),
+        ("replica_key", ctypes.POINTER(ctypes.c_uint64)),
     ]
 
 
@@ -96,6 +99,11 @@ class h4d_counts(ctypes.Structure):
         ("threads_per_atom", ctypes.c_int64),
         ("nbr_refreshes", ctypes.c_int64),
         ("t_filter_ns", ctypes.c_double),
+        ("last_smid", ctypes.c_int64),
+        ("t_last_begin_ns", ctypes.c_double),
+        ("t_last_end_ns", ctypes.c_double),
+        ("plan_warps", ctypes.c_int64),
+        ("plan_cta_groups", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -163,6 +171,8 @@ def lib():
             "h4d_get_state": ([vp, i32, pd, pd, i64, ctypes.POINTER(i64)], i32),
             "h4d_set_state": ([vp, i32, i32, pd, pd], i32),
             "h4d_num_replicas": ([vp], i32),
+            "h4d_device_info": ([pi32, pi32, pi32], i32),
+            "h4d_measure_fp32_peak": ([pd, pd], i32),
             "h4d_autotune": ([vp, i32, pd, pd], i32),
             "h4d_count_pairs": ([vp, ctypes.POINTER(i64)], i32),
             "h4d_save": ([vp, ctypes.c_char_p], i32),
@@ -170,6 +180,7 @@ def lib():
             "h4d_eval_forces": ([ctypes.POINTER(h4d_params), d, i32, i32, pd, pd, pd, pd], i32),
             "h4d_eval_forces_static": ([ctypes.POINTER(h4d_params), d, i32, i32, pd, pd, pd, pd], i32),
             "h4d_neighbor_pairs": ([d, i32, pd, d, pi32, pi32, i64, ctypes.POINTER(i64)], i32),
+            "h4d_ewald_lr": ([ctypes.POINTER(h4d_params), d, i32, i32, pd, d, i32, d, d, pd, pd, pd], i32),
             "h4d_proposal": ([vp, i32, d, d, i32], i32),
             "h4d_proposal_set_weights": ([vp, pd, i64], i32),
             "h4d_proposal_get_weights": ([vp, pd, i64], i32),
@@ -231,12 +242,14 @@ def make_params(cfg: dict, **override) -> h4d_params:
     p.skin_outer = c.get("skin_outer", 0.0)
     p.max_nbr = c.get("max_nbr", 0)
     p.threads_per_atom = c.get("threads_per_atom", 0)
+    p.exchange = 1 if c.get("exchange", "pair") == "single" else 0
     return p
 
 
 class Context:
     """Owns an h4d_ctx.  Replicas: list of dicts with keys L, n_pairs, cap_pairs, x, v
-    (optional), n_water (optional)."""
+    (optional), n_water (optional), key (optional: the replica's random-stream key, by
+    default its index)."""
 
     def __init__(self, params: h4d_params, replicas: list, seed: int, stream: int | None = None):
         R = len(replicas)
@@ -256,11 +269,15 @@ class Context:
         s.cap_pairs = cap.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         s.host_x = _pd(xs)
         s.host_v = _pd(vs)
+        have_key = all(r.get("key") is not None for r in replicas)
+        keys = np.array([int(r["key"]) for r in replicas], np.uint64) if have_key else None
+        s.replica_key = keys.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) if have_key else None
         h = ctypes.c_void_p()
         _ck(lib().h4d_create(ctypes.byref(params), ctypes.byref(s), seed, ctypes.c_void_p(stream or 0), ctypes.byref(h)), "h4d_create")
         self.h = h
         self.R = R
-        self.cap_atoms = [3 * int(nw[i]) + 2 * int(cap[i]) for i in range(R)]
+        unit = 1 if params.exchange == 1 else 2  # atoms per exchange unit
+        self.cap_atoms = [3 * int(nw[i]) + unit * int(cap[i]) for i in range(R)]
 
     def close(self):
         if self.h:
@@ -439,3 +456,29 @@ def h4d_proposal_grad(w, feat, tgt):
     _ck(lib().h4d_proposal_grad(_pd(w), f.shape[0], f.ctypes.data, t.ctypes.data, ctypes.byref(loss), _pd(g)),
         "h4d_proposal_grad")
     return loss.value, g
+
+
+def h4d_device_info():
+    """(SM count, engine kernel binary version, PTX version) of the current device"""
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _ck(lib().h4d_device_info(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "h4d_device_info")
+    return a.value, b.value, c.value
+
+
+def h4d_measure_fp32_peak():
+    """(TFLOP/s, seconds) of the FMA-chain probe"""
+    t, s = ctypes.c_double(), ctypes.c_double()
+    _ck(lib().h4d_measure_fp32_peak(ctypes.byref(t), ctypes.byref(s)), "h4d_measure_fp32_peak")
+    return t.value, s.value
+
+
+def h4d_ewald_lr(params: h4d_params, L: float, x, alpha: float, kmax: int, wbar: float = 0.0,
+                 kappa_lr: float = 0.0, n_water: int = 0, forces: bool = True):
+    """(U_recip, U_self, F_recip or None) of the long-range Coulomb term (Eqs. 9-10)"""
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    n = x.shape[0]
+    ur, us = ctypes.c_double(), ctypes.c_double()
+    F = np.zeros((n, 3)) if forces else None
+    _ck(lib().h4d_ewald_lr(ctypes.byref(params), L, n_water, n, _pd(x), alpha, int(kmax), wbar, kappa_lr,
+                           ctypes.byref(ur), ctypes.byref(us), _pd(F)), "h4d_ewald_lr")
+    return ur.value, us.value, F

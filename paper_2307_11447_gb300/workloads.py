@@ -93,13 +93,15 @@ def lj_config(n_ions: int, rho: float, n_f: int, **extra) -> dict:
     return cfg
 
 
-# The five workloads.  beta_mu values are the pair chemical potentials used for the
-# grand-canonical runs (estimated with fixed-N work sampling and the BAR equation).
+# The five workloads.  beta_mu of the 250- and 4000-ion electrolytes is the BAR estimate
+# (SI Eq. S2) from fixed-N insertion and deletion work of the FP64 oracle at the
+# configuration's N (tests/golden/make_config_stats.py, stage "calibrate"): -8.694 +- 0.150
+# for 250 ions, -8.818 +- 0.524 for 4000 ions.
 CONFIGS = {
-    "lj250": lj_config(250, 0.2, 100, trials=200, n_eq=1000, cap_pairs=256, beta_mu=-6.0),
+    "lj250": lj_config(250, 0.2, 100, trials=200, n_eq=1000, cap_pairs=256, beta_mu=-8.694),
     # outer-list skin 6x the Verlet skin: fewer outer builds (measured best of a skin sweep)
     "lj4000": lj_config(4000, 0.3, 500, trials=10000, n_eq=1000, cap_pairs=2304, chains=304,
-                        beta_mu=-6.0, skin_outer=1.8),
+                        beta_mu=-8.818, skin_outer=1.8),
 }
 
 

@@ -48,3 +48,18 @@ def force_bounds(cfg, x, Fo, w=None, rel=1e-5, band=1e-6):
                 if j != i:
                     bound[i] += jumps.get((rc, types[i], types[j]), 0.0)
     return bound
+
+
+def trial_work_bound(beta_dM, x_acc):
+    """Allowed |beta dM_gpu - beta dM_oracle| of one trial (kT).  Near the acceptance
+    boundary (|x| < 20): 1e-3, the spread of the oracle's own binary32-force build
+    (tests/test_oracle_tolerance.py).  Farther out: 1e-3 + 1e-3 |beta dM|.  Trials that
+    exchange more than 1e4 kT are insertions onto overlaps, driven by forces beyond 1e10
+    whose FP32 rounding the dynamics amplify: 1e-2 |beta dM| (the binary32-force oracle
+    moves one such trial of the 250-ion electrolyte, beta dM = 4.2e6, by 5.2e-4 relative);
+    their decision is certain either way."""
+    if abs(x_acc) < 20:
+        return 1e-3
+    if abs(beta_dM) < 1e4:
+        return 1e-3 + 1e-3 * abs(beta_dM)
+    return 1e-2 * abs(beta_dM)

@@ -18,7 +18,7 @@ from oracle import oracle as orc
 from paper_2307_11447_gb300 import lib as h4d
 from paper_2307_11447_gb300 import workloads as wl
 
-from .parity_util import force_bounds
+from .parity_util import force_bounds, trial_work_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -209,7 +209,7 @@ def test_single_trials_with_nonlinear_schedules_match_oracle(sched, n):
         moves.add(int(ro["move"]))
         assert rg["move"] == ro["move"] and rg["status"] == ro["status"] == 0
         err = abs(rg["beta_dM"] - ro["beta_dM"])
-        bound = 1e-3 if abs(ro["x_acc"]) < 20 else 1e-3 + 1e-3 * abs(ro["beta_dM"])
+        bound = trial_work_bound(ro["beta_dM"], ro["x_acc"])
         assert err <= bound, (k, rg["beta_dM"], ro["beta_dM"])
         assert abs(rg["w_prot"] - ro["w_prot"]) <= bound
         if abs(ro["x_acc"]) < 20:
@@ -244,7 +244,7 @@ def test_single_trials_with_species_wmax_match_oracle():
               f"w_prot gpu {rg['w_prot']:.6f} oracle {ro['w_prot']:.6f}")
         assert rg["move"] == ro["move"] and rg["status"] == ro["status"] == 0
         err = abs(rg["beta_dM"] - ro["beta_dM"])
-        bound = 1e-3 if abs(ro["x_acc"]) < 20 else 1e-3 + 1e-3 * abs(ro["beta_dM"])
+        bound = trial_work_bound(ro["beta_dM"], ro["x_acc"])
         assert err <= bound, (k, rg["beta_dM"], ro["beta_dM"])
         assert abs(rg["w_prot"] - ro["w_prot"]) <= bound + 1e-4 * abs(ro["w_prot"])
         if abs(ro["x_acc"]) < 20:

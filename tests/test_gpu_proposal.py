@@ -31,6 +31,8 @@ from oracle import proposal as pr
 from paper_2307_11447_gb300 import lib as h4d
 from paper_2307_11447_gb300 import workloads as wl
 
+from .parity_util import trial_work_bound
+
 pytestmark = pytest.mark.gpu
 
 TWO32 = 4294967296.0
@@ -42,9 +44,7 @@ def quantize(x, L):
 
 
 def work_close(g, o, x_acc):
-    if abs(x_acc) < 20:
-        return abs(g - o) <= 1e-3
-    return abs(g - o) <= 1e-3 + 1e-3 * abs(o)
+    return abs(g - o) <= trial_work_bound(o, x_acc)
 
 
 def f32_weights(seed, scale1=1.0, scale3=1.0):
