@@ -1204,7 +1204,7 @@ int h4d_eval_forces(const h4d_params* params, double L, int32_t n_water, int32_t
                     const double* w, double* F, double* U) {
   int rc = check_params(params);
   if (rc) return rc;
-  if (!x || !F || n < 0 || n_water < 0 || 3 * n_water > n || !(L > 0)) return H4D_EINVAL;
+  if (((!x || !F) && n > 0) || n < 0 || n_water < 0 || 3 * n_water > n || !(L > 0)) return H4D_EINVAL;
   if (unit_of(*params) == 2 && ((n - 3 * n_water) & 1) != 0) return H4D_EINVAL;
   if (2.0 * (rmax_of(*params) + params->skin) >= L) return H4D_EINVAL;
   if (n > 65535) return H4D_ECAPACITY;
@@ -1405,7 +1405,7 @@ extern "C" int h4d_eval_forces_static(const h4d_params* params, double L, int32_
                                       const double* x, const double* w, double* F, double* U) {
   int rc = check_params(params);
   if (rc) return rc;
-  if (!x || !F || n < 0 || n_water < 0 || 3 * n_water > n || !(L > 0)) return H4D_EINVAL;
+  if (((!x || !F) && n > 0) || n < 0 || n_water < 0 || 3 * n_water > n || !(L > 0)) return H4D_EINVAL;
   if (unit_of(*params) == 2 && ((n - 3 * n_water) & 1) != 0) return H4D_EINVAL;
   if (2.0 * (rmax_of(*params) + params->skin) >= L) return H4D_EINVAL;
   rc = check_device();

@@ -53,3 +53,18 @@ def test_static_scratch_rejects_oversized_systems():
     with pytest.raises(h4d.H4DError) as ei:
         h4d.h4d_eval_forces_static(h4d.make_params(cfg), cfg["L"], x)
     assert ei.value.code == h4d.H4D_ECAPACITY
+
+
+def test_static_scratch_rigid_water_and_empty_system():
+    """the water path (O/H types, intramolecular exclusions, Kahan force sums) through the
+    static scratch, and n = 0, which both entry points accept with U = 0"""
+    L = 22.5
+    cfg = wl.aq_config(300, 4, L, 10)
+    x = _quantize(wl.aqueous_positions(300, 4, L, 12), L)
+    p = h4d.make_params(cfg)
+    Us, Fs = h4d.h4d_eval_forces_static(p, L, x, n_water=300)
+    Ua, Fa = h4d.h4d_eval_forces(p, L, x, n_water=300)
+    _close(Fs, Fa, Us, Ua)
+    U0s, F0s = h4d.h4d_eval_forces_static(p, L, np.zeros((0, 3)))
+    U0a, F0a = h4d.h4d_eval_forces(p, L, np.zeros((0, 3)))
+    assert U0s == U0a == 0.0 and F0s.shape == F0a.shape == (0, 3)
