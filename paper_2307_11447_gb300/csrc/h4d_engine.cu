@@ -138,6 +138,46 @@ __device__ __forceinline__ float pair_fr(const Pot& P, const PairCoef<SYS>& c, f
   return fr_lj + fr_c;
 }
 
+// Two LJ-electrolyte pair terms at once on the packed FP32x2 pipe (FFMA2 / FMUL2 / FADD2):
+// every operation of pair_fr<H4D_SYS_LJ> in the same order and association, each lane
+// rounded as the scalar operation is, so each result is bit-identical to pair_fr; the
+// special functions (rsqrt, ex2, rcp) and the cut-off selects stay per lane.  kqg is the
+// pair's charge prefactor times its screening factor.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float ex2_approx(float y) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+  return r;
+}
+__device__ __forceinline__ float rcp_approx(float y) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+  return r;
+}
+__device__ __forceinline__ float2 pair_fr_lj2(const Pot& P, float2 r2, float2 kqg) {
+  const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+  const float2 rinv2 = __fmul2_rn(rinv, rinv);
+  const float2 s2 = __fmul2_rn(f2(P.sig2[0]), rinv2);
+  const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
+  float2 fr_lj = __fmul2_rn(__fmul2_rn(__fmul2_rn(f2(P.eps4[0]), s6), __ffma2_rn(f2(12.0f), s6, f2(-6.0f))), rinv2);
+  fr_lj.x = (r2.x < P.rc2_lj) ? fr_lj.x : 0.0f;
+  fr_lj.y = (r2.y < P.rc2_lj) ? fr_lj.y : 0.0f;
+  const float2 x = __fmul2_rn(f2(P.alpha), __fmul2_rn(r2, rinv));
+  const float2 y = __fmul2_rn(__fmul2_rn(make_float2(-x.x, -x.y), x), f2(1.4426950408889634f));
+  const float2 ex = make_float2(ex2_approx(y.x), ex2_approx(y.y));
+  const float2 d = __ffma2_rn(f2(0.3275911f), x, f2(1.0f));
+  const float2 t = make_float2(rcp_approx(d.x), rcp_approx(d.y));
+  float2 p = __ffma2_rn(t, f2(1.061405429f), f2(-1.453152027f));
+  p = __ffma2_rn(t, p, f2(1.421413741f));
+  p = __ffma2_rn(t, p, f2(-0.284496736f));
+  p = __ffma2_rn(t, p, f2(0.254829592f));
+  const float2 erfcx = __fmul2_rn(__fmul2_rn(p, t), ex);
+  float2 fr_c = __fmul2_rn(__fmul2_rn(kqg, __ffma2_rn(erfcx, rinv, __fmul2_rn(f2(P.two_alpha_sqrtpi), ex))), rinv2);
+  fr_c.x = (r2.x < P.rc2_c) ? fr_c.x : 0.0f;
+  fr_c.y = (r2.y < P.rc2_c) ? fr_c.y : 0.0f;
+  return __fadd2_rn(fr_lj, fr_c);
+}
+
 // FP32 pair energy (protocol-work diagnostic only)
 template <int SYS>
 __device__ __forceinline__ float pair_u32(const Pot& P, const PairCoef<SYS>& c, float r2, float g) {
@@ -737,29 +777,30 @@ __device__ H4D_PHASE void force_pass_impl(const Ctx& cref, int mode, float w_pre
 #pragma unroll
           for (int u = 0; u < 4; ++u) pj[u] = v.pos[min(jw[u], capa)];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float dx = (float)(int)(pj[u].x - pi.x) * scale;
-            const float dy = (float)(int)(pj[u].y - pi.y) * scale;
-            const float dz = (float)(int)(pj[u].z - pi.z) * scale;
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float wj = wbits(pj[u]);  // 0, a flyer's altitude, or +inf (sentinel)
-            PairCoef<SYS> cf;
-            cf.sig2 = P.sig2[0];
-            cf.eps4 = P.eps4[0];
-            cf.ljshift = P.ljshift[0];
-            cf.kq = __uint_as_float(kq_i ^ (jw[u] << 31));  // kq[1] = -kq[0] for charges +q/-q
-            float g = 1.0f;
+          for (int h = 0; h < 4; h += 2) {  // slots h and h+1 on the packed FP32x2 pipe
+            const float2 dx = __fmul2_rn(make_float2((float)(int)(pj[h].x - pi.x), (float)(int)(pj[h + 1].x - pi.x)), f2(scale));
+            const float2 dy = __fmul2_rn(make_float2((float)(int)(pj[h].y - pi.y), (float)(int)(pj[h + 1].y - pi.y)), f2(scale));
+            const float2 dz = __fmul2_rn(make_float2((float)(int)(pj[h].z - pi.z), (float)(int)(pj[h + 1].z - pi.z)), f2(scale));
+            float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+            const float2 wj = make_float2(wbits(pj[h]), wbits(pj[h + 1]));  // 0, a flyer's altitude, or +inf
+            float2 kqg = make_float2(__uint_as_float(kq_i ^ (jw[h] << 31)), __uint_as_float(kq_i ^ (jw[h + 1] << 31)));
             if (NEMD) {
-              const float dw = wi - wj;
-              r2 = fmaf(dw, dw, r2);
-              g = (wnz_i != (wj != 0.0f)) ? gscr : 1.0f;
+              const float2 dw = __fadd2_rn(f2(wi), make_float2(-wj.x, -wj.y));
+              r2 = __ffma2_rn(dw, dw, r2);
+              // charge prefactor times the screening g of the generic loop (exact when g = 1)
+              kqg.x = (wnz_i != (wj.x != 0.0f)) ? kqg.x * gscr : kqg.x;
+              kqg.y = (wnz_i != (wj.y != 0.0f)) ? kqg.y * gscr : kqg.y;
             } else {
-              r2 = fmaf(wj, wj, r2);  // + 0 for every atom, +inf for the sentinel
+              r2 = __ffma2_rn(wj, wj, r2);  // + 0 for every atom, +inf for the sentinel
             }
-            const float fr = pair_fr<SYS>(P, cf, r2, g);
-            fx = fmaf(-fr, dx, fx);
-            fy = fmaf(-fr, dy, fy);
-            fz = fmaf(-fr, dz, fz);
+            const float2 fr = pair_fr_lj2(P, r2, kqg);
+            // the force sums in slot order, as in the generic loop
+            fx = fmaf(-fr.x, dx.x, fx);
+            fy = fmaf(-fr.x, dy.x, fy);
+            fz = fmaf(-fr.x, dz.x, fz);
+            fx = fmaf(-fr.y, dx.y, fx);
+            fy = fmaf(-fr.y, dy.y, fy);
+            fz = fmaf(-fr.y, dz.y, fz);
           }
           q = qn;
         }
