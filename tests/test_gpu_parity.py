@@ -261,6 +261,56 @@ def _c1_oracle_trial(args):
     return orc.trial(po, st)
 
 
+def _c1_state(pool_cfg):
+    """the 4000-ion electrolyte after 200 oracle MD steps from seeded random positions"""
+    cfg = dict(pool_cfg)
+    L = cfg["L"]
+    po = orc.make_params(cfg, use_cells=1)
+    st = orc.State(po, quantize(wl.lj_positions(cfg["n_pairs"], L, 9), L), None, cfg["n_pairs"], cfg["cap_pairs"])
+    orc.init_velocities(po, st)
+    orc.md(po, st, 200)
+    return quantize(st.positions(), L), st.velocities()
+
+
+def _c1_gpu_trials(cfg, x0, v0, n):
+    ctx = h4d.Context(h4d.make_params(cfg), [dict(L=cfg["L"], n_pairs=cfg["n_pairs"], cap_pairs=cfg["cap_pairs"],
+                                                  x=x0, v=v0)], seed=cfg["seed"])
+    gpu = []
+    for k in range(n):
+        ctx.h4d_set_state(0, cfg["n_pairs"], x0, v0)
+        ctx.h4d_run_trials(1, 0)
+        gpu.append(ctx.h4d_get_work(0, 1)[0])
+    ctx.close()
+    return gpu
+
+
+def test_c1_short_protocol_work_matches_oracle():
+    """The 4000-ion electrolyte with a 30-step protocol from the same equilibrated state as
+    the 500-step comparison below: before the trajectories have had time to diverge, the
+    per-trial work of the FP32-force / FP64-Kahan-work path holds the strict bound of the
+    small system, |beta dM_gpu - beta dM_orc| <= 1e-4 + 1e-6 |beta dM| kT.  (The engine
+    has no read-out in the middle of a trial, so a short protocol stands in for a prefix of
+    the long one; its altitude moves 17x faster, so its forces on the flyers are larger.)"""
+    import multiprocessing as mp
+
+    cfg = dict(wl.CONFIGS["lj4000"])
+    cfg.update(seed=9, replica=0, beta_mu=-6.0, n_f=30)
+    with mp.get_context("spawn").Pool(4) as pool:  # before the first GPU call
+        x0, v0 = _c1_state(cfg)
+        async_res = pool.map_async(_c1_oracle_trial, [(x0, v0, cfg, k) for k in range(4)])
+        gpu = _c1_gpu_trials(cfg, x0, v0, 4)
+        orc_recs = async_res.get(timeout=1800)
+    moves = set()
+    for k, (rg, ro) in enumerate(zip(gpu, orc_recs)):
+        err = abs(rg["beta_dM"] - ro["beta_dM"])
+        moves.add(int(ro["move"]))
+        print(f"C1 30-step trial {k}: move {ro['move']} beta dM gpu {rg['beta_dM']:.8f} oracle {ro['beta_dM']:.8f} "
+              f"|diff| {err:.2e} kT")
+        assert rg["move"] == ro["move"] and rg["status"] == ro["status"] == 0
+        assert err <= 1e-4 + 1e-6 * abs(ro["beta_dM"]), (k, rg["beta_dM"], ro["beta_dM"])
+    assert moves == {0, 1}
+
+
 def test_c1_trial_work_error_against_oracle():
     """The 4000-ion electrolyte at rho 0.3 with the 500-step protocol: the per-trial work of
     four GPU trials against the FP64 oracle (cell list) from the same state, printed as the
@@ -273,21 +323,10 @@ def test_c1_trial_work_error_against_oracle():
 
     cfg = dict(wl.CONFIGS["lj4000"])
     cfg.update(seed=9, replica=0, beta_mu=-6.0)
-    L = cfg["L"]
     with mp.get_context("spawn").Pool(4) as pool:  # before the first GPU call
-        po = orc.make_params(cfg, use_cells=1)
-        st = orc.State(po, quantize(wl.lj_positions(cfg["n_pairs"], L, 9), L), None, cfg["n_pairs"], cfg["cap_pairs"])
-        orc.init_velocities(po, st)
-        orc.md(po, st, 200)
-        x0, v0 = quantize(st.positions(), L), st.velocities()
+        x0, v0 = _c1_state(cfg)
         async_res = pool.map_async(_c1_oracle_trial, [(x0, v0, cfg, k) for k in range(4)])
-        ctx = h4d.Context(h4d.make_params(cfg), [dict(L=L, n_pairs=cfg["n_pairs"], cap_pairs=cfg["cap_pairs"],
-                                                      x=x0, v=v0)], seed=cfg["seed"])
-        gpu = []
-        for k in range(4):
-            ctx.h4d_set_state(0, cfg["n_pairs"], x0, v0)
-            ctx.h4d_run_trials(1, 0)
-            gpu.append(ctx.h4d_get_work(0, 1)[0])
+        gpu = _c1_gpu_trials(cfg, x0, v0, 4)
         orc_recs = async_res.get(timeout=1800)
     for k, (rg, ro) in enumerate(zip(gpu, orc_recs)):
         err = abs(rg["beta_dM"] - ro["beta_dM"])
