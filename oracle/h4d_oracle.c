@@ -396,8 +396,9 @@ static void water_constraint(const orc_params* p, int k, int* a, int* b, double*
 /* SHAKE position stage of RATTLE (Andersen 1983): after an unconstrained drift, iterate
  * pairwise corrections along the old bond vectors until every bond length holds; the
  * same impulse corrects the half-step velocities. xold holds positions before the drift. */
-static void shake(const orc_params* p, double* x, double* v, const double* xold, double h) {
+static void shake(const orc_params* p, double* x, double* v, const double* xold, double h, const uint8_t* fly) {
   for (int m = 0; m < p->n_water; ++m) {
+    if (fly && fly[3 * m] == 1) continue; /* a flying water is frozen in 3D */
     for (int it = 0; it < 1000; ++it) {
       double worst = 0.0;
       for (int k = 0; k < 3; ++k) {
@@ -430,8 +431,9 @@ static void shake(const orc_params* p, double* x, double* v, const double* xold,
 }
 
 /* RATTLE velocity stage: remove the bond-parallel relative velocity of every constraint */
-static void rattle_v(const orc_params* p, const double* x, double* v) {
+static void rattle_v(const orc_params* p, const double* x, double* v, const uint8_t* fly) {
   for (int m = 0; m < p->n_water; ++m) {
+    if (fly && fly[3 * m] == 1) continue;
     for (int it = 0; it < 1000; ++it) {
       double worst = 0.0;
       for (int k = 0; k < 3; ++k) {
@@ -466,18 +468,28 @@ static void vv_step(const orc_params* p, int n, double* x, double* v, double* F,
   kick(p, n, v, F, fly, 0.5 * h);
   if (p->n_water) memcpy(xold, x, sizeof(double) * 3 * (size_t)(3 * p->n_water));
   drift(p, n, x, v, fly, h);
-  if (p->n_water) shake(p, x, v, xold, h);
+  if (p->n_water) shake(p, x, v, xold, h, fly);
   if (w && fly)
     for (int i = 0; i < n; ++i) w[i] = (fly[i] == 1) ? w_next : 0.0;
   orc_energy_forces(p, n, x, w, fly, F);
   kick(p, n, v, F, fly, 0.5 * h);
-  if (p->n_water) rattle_v(p, x, v);
+  if (p->n_water) rattle_v(p, x, v, fly);
 }
 
 /* atoms of a state with n_pairs exchange units: ion pairs, or particles in single mode */
 static int n_atoms(const orc_params* p, int n_pairs) { return 3 * p->n_water + (p->single ? 1 : 2) * n_pairs; }
 
+/* the parameters with the state's number of waters (water exchange: the count varies) */
+static const orc_params* with_waters(const orc_params* p, const orc_state* s, orc_params* tmp) {
+  if (!p->water_ex) return p;
+  *tmp = *p;
+  tmp->n_water = s->n_water;
+  return tmp;
+}
+
 double orc_nve(const orc_params* p, orc_state* s, int64_t n_steps, double* e_trace) {
+  orc_params pw;
+  p = with_waters(p, s, &pw);
   int n = n_atoms(p, s->n_pairs);
   double* F = (double*)calloc(3 * (size_t)(n + 1), sizeof(double));
   double* xold = (double*)calloc(3 * (size_t)(n + 1), sizeof(double));
@@ -543,6 +555,8 @@ static void csvr(const orc_params* p, int n, double* v, uint64_t step) {
 }
 
 void orc_md(const orc_params* p, orc_state* s, int64_t n_steps) {
+  orc_params pw;
+  p = with_waters(p, s, &pw);
   int n = n_atoms(p, s->n_pairs);
   double* F = (double*)calloc(3 * (size_t)(n + 1), sizeof(double));
   double* xold = (double*)calloc(3 * (size_t)(n + 1), sizeof(double));
@@ -566,13 +580,15 @@ static void mb_velocity(const orc_params* p, int type, const uint64_t r[4], doub
 }
 
 void orc_init_velocities(const orc_params* p, orc_state* s) {
+  orc_params pw;
+  p = with_waters(p, s, &pw);
   int n = n_atoms(p, s->n_pairs);
   for (int i = 0; i < n; ++i) {
     uint64_t r[4];
     draw(p, (uint64_t)i, 0, ORC_PUR_VINIT, r);
     mb_velocity(p, orc_atom_type(p, i), r, &s->v[3 * i]);
   }
-  if (p->n_water) rattle_v(p, s->x, s->v);
+  if (p->n_water) rattle_v(p, s->x, s->v, NULL);
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -595,12 +611,12 @@ static double nemd(const orc_params* p, int n, double* x, double* v, const uint8
     kick(p, n, v, F, fly, 0.5 * h);
     if (p->n_water) memcpy(xold, x, sizeof(double) * 9 * (size_t)p->n_water);
     drift(p, n, x, v, fly, h);
-    if (p->n_water) shake(p, x, v, xold, h);
+    if (p->n_water) shake(p, x, v, xold, h, fly);
     wprot += flyer_energy(p, n, x, fly, wk1, wbuf) - flyer_energy(p, n, x, fly, wk, wbuf);
     for (int i = 0; i < n; ++i) w[i] = (fly[i] == 1) ? species_w(p, i, wk1) : 0.0;
     orc_energy_forces(p, n, x, w, fly, F);
     kick(p, n, v, F, fly, 0.5 * h);
-    if (p->n_water) rattle_v(p, x, v);
+    if (p->n_water) rattle_v(p, x, v, fly);
   }
   free(F);
   free(w);
@@ -611,6 +627,8 @@ static double nemd(const orc_params* p, int n, double* x, double* v, const uint8
 
 double orc_nemd_path(const orc_params* p, orc_state* s, const int32_t* flyers, int n_flyers,
                      int insertion, double* U_end) {
+  orc_params pw;
+  p = with_waters(p, s, &pw);
   int n = n_atoms(p, s->n_pairs);
   uint8_t* fly = (uint8_t*)calloc((size_t)n, 1);
   for (int k = 0; k < n_flyers; ++k) fly[flyers[k]] = 1;
@@ -828,9 +846,11 @@ static void flip_all(double* v, int n) {
  * deletion discards it, so it cancels against the e^{-beta K}/N_k factors of Eqs. 3-4.
  */
 static int trial_single(const orc_params* p, orc_state* s, orc_record* rec);
+static int trial_water(const orc_params* p, orc_state* s, orc_record* rec);
 
 int orc_trial_prop(const orc_params* p, const orc_proposal* q, orc_state* s, orc_record* rec,
                    double* site_feat, double* site_y) {
+  if (p->water_ex) return trial_water(p, s, rec); /* likewise */
   if (p->single) return trial_single(p, s, rec); /* no proposal, bias or early rejection */
   uint64_t t = s->trial_ctr++;
   uint64_t b0[4], b1[4], b2[4], b3[4], b4[4], b5[4], b6[4];
@@ -1168,6 +1188,196 @@ static int trial_single(const orc_params* p, orc_state* s, orc_record* rec) {
   free(xs);
   free(vs);
   free(fly);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Rigid-water exchange (Sec. II.A: the exchange rule with one flyer; Sec. II.C: a       */
+/* flying rigid water gets Maxwell-Boltzmann velocities drawn in its molecular frame)    */
+/* ------------------------------------------------------------------------------------ */
+
+/* The water in its body frame: O at the origin, the H atoms in the xy plane at
+ * (+-d_oh sin(theta/2), d_oh cos(theta/2), 0), so the y axis is the symmetry axis and the
+ * body axes are principal axes.  com: centre of mass; I: principal moments about it. */
+typedef struct {
+  double h[2][3], com[3], M, I[3];
+} water_body;
+
+static void water_frame(const orc_params* p, water_body* b) {
+  double sh = 0.5 * p->d_hh / p->d_oh, ch = sqrt(1.0 - sh * sh);
+  double mO = p->mass[2], mH = p->mass[3];
+  b->h[0][0] = p->d_oh * sh;
+  b->h[1][0] = -p->d_oh * sh;
+  b->h[0][1] = b->h[1][1] = p->d_oh * ch;
+  b->h[0][2] = b->h[1][2] = 0.0;
+  b->M = mO + 2.0 * mH;
+  b->com[0] = b->com[2] = 0.0;
+  b->com[1] = 2.0 * mH * p->d_oh * ch / b->M;
+  double yo = -b->com[1], yh = p->d_oh * ch - b->com[1], xh = p->d_oh * sh;
+  b->I[0] = mO * yo * yo + 2.0 * mH * yh * yh; /* sum m (y^2 + z^2) */
+  b->I[1] = 2.0 * mH * xh * xh;                /* sum m (x^2 + z^2) */
+  b->I[2] = b->I[0] + b->I[1];                 /* sum m (x^2 + y^2), planar body */
+}
+
+/* A uniformly distributed rotation from three uniforms: the unit quaternion
+ * (sqrt(1-u1) sin 2 pi u2, sqrt(1-u1) cos 2 pi u2, sqrt(u1) sin 2 pi u3, sqrt(u1) cos 2 pi u3)
+ * (Shoemake, Graphics Gems III, 1992) and its rotation matrix. */
+static void random_rotation(double u1, double u2, double u3, double R[3][3]) {
+  double a = sqrt(1.0 - u1), b = sqrt(u1);
+  double qx = a * sin(2.0 * M_PI * u2), qy = a * cos(2.0 * M_PI * u2);
+  double qz = b * sin(2.0 * M_PI * u3), qw = b * cos(2.0 * M_PI * u3);
+  R[0][0] = 1.0 - 2.0 * (qy * qy + qz * qz);
+  R[0][1] = 2.0 * (qx * qy - qw * qz);
+  R[0][2] = 2.0 * (qx * qz + qw * qy);
+  R[1][0] = 2.0 * (qx * qy + qw * qz);
+  R[1][1] = 1.0 - 2.0 * (qx * qx + qz * qz);
+  R[1][2] = 2.0 * (qy * qz - qw * qx);
+  R[2][0] = 2.0 * (qx * qz - qw * qy);
+  R[2][1] = 2.0 * (qy * qz + qw * qx);
+  R[2][2] = 1.0 - 2.0 * (qx * qx + qy * qy);
+}
+
+/* Place an inserted water (atoms O, H, H at x[0..8], v[0..8]).  Position: the O at the
+ * 32-bit box fractions of block 1 words 0-2; each H at the O's fixed-point coordinate plus
+ * its rotated body offset rounded to the 32-bit grid.  Orientation: uniform, from the
+ * three uniforms of block 2.  Velocities, drawn in the molecular frame and handed to the
+ * lab frame: centre-of-mass velocity V with N(0, kT/M) per axis and angular velocity
+ * omega with N(0, kT/I_k) on body axis k (six normals from blocks 3-4: V_x, V_y, V_z,
+ * omega_x, omega_y, omega_z in the order of the pair draws); atom a moves with
+ * V + R (omega x (a_body - com)). */
+static void place_water(const orc_params* p, const uint64_t b1[4], const uint64_t b2[4], const uint64_t b3[4],
+                        const uint64_t b4[4], double* x, double* v) {
+  water_body wb;
+  water_frame(p, &wb);
+  double R[3][3];
+  random_rotation(u01(b2[0]), u01(b2[1]), u01(b2[2]), R);
+  double q = p->L / 4294967296.0;
+  uint32_t XO[3];
+  for (int d = 0; d < 3; ++d) {
+    XO[d] = (uint32_t)(b1[d] >> 32);
+    x[d] = (double)XO[d] * q;
+  }
+  for (int k = 0; k < 2; ++k)
+    for (int d = 0; d < 3; ++d) {
+      double off = R[d][0] * wb.h[k][0] + R[d][1] * wb.h[k][1] + R[d][2] * wb.h[k][2];
+      int64_t dk = (int64_t)nearbyint(off / p->L * 4294967296.0);
+      x[3 * (k + 1) + d] = (double)(uint32_t)(XO[d] + (uint32_t)dk) * q;
+    }
+  double kT = 1.0 / (p->beta * p->mvv2e);
+  double sv = sqrt(kT / wb.M);
+  double V[3] = {sv * gauss_cos(b3[0], b3[1]), sv * gauss_sin(b3[0], b3[1]), sv * gauss_cos(b3[2], b3[3])};
+  double om[3] = {sqrt(kT / wb.I[0]) * gauss_sin(b3[2], b3[3]), sqrt(kT / wb.I[1]) * gauss_cos(b4[0], b4[1]),
+                  sqrt(kT / wb.I[2]) * gauss_sin(b4[0], b4[1])};
+  for (int a = 0; a < 3; ++a) {
+    double r[3];
+    for (int d = 0; d < 3; ++d) r[d] = (a == 0 ? 0.0 : wb.h[a - 1][d]) - wb.com[d];
+    double u[3] = {om[1] * r[2] - om[2] * r[1], om[2] * r[0] - om[0] * r[2], om[0] * r[1] - om[1] * r[0]};
+    for (int d = 0; d < 3; ++d) v[3 * a + d] = V[d] + R[d][0] * u[0] + R[d][1] * u[1] + R[d][2] * u[2];
+  }
+}
+
+/* Trial t of a water-exchange chain.  Draws as for pairs: block 0 (move, reversals,
+ * acceptance uniform); block 1: deletion [0] the water (uniform in [0, N_w)), insertion
+ * [0..2] the O position; block 2: insertion [0..2] the orientation; blocks 3-4: the
+ * velocities.  The flying water stays frozen in 3D (Sec. II.B.1 for ions, read the same
+ * way for a molecule: no drift, no kick, no constraint step) while its altitude follows
+ * the schedule; Delta H, the momentum reversals and the exponents are those of a single
+ * particle (reading of Sec. II.A: V/(N_w+1) once), N counting waters.  Layout: the
+ * inserted water is the last water, so the ions move up by three atoms; a deletion moves
+ * the last water into the deleted slot and the ions down by three. */
+static int trial_water(const orc_params* p, orc_state* s, orc_record* rec) {
+  uint64_t t = s->trial_ctr++;
+  uint64_t b0[4], b1[4], b2[4], b3[4], b4[4];
+  draw(p, t, 0, ORC_PUR_TRIAL, b0);
+  draw(p, t, 1, ORC_PUR_TRIAL, b1);
+  draw(p, t, 2, ORC_PUR_TRIAL, b2);
+  draw(p, t, 3, ORC_PUR_TRIAL, b3);
+  draw(p, t, 4, ORC_PUR_TRIAL, b4);
+  int insertion = (int)(b0[0] >> 63);
+  int flip_start = (int)(b0[1] >> 63), flip_end = (int)(b0[2] >> 63);
+  double ln_u = log(u01_open(b0[3]));
+  int N = s->n_water;
+  int n_ion = 2 * s->n_pairs;
+  int n = 3 * N + n_ion;
+  double V = p->L * p->L * p->L;
+
+  memset(rec, 0, sizeof(*rec));
+  rec->move = insertion;
+  rec->n_before = N;
+  rec->n_after = N;
+  rec->cation = rec->anion = -1;
+  rec->cell_c = rec->cell_a = -1;
+  rec->ln_u = ln_u;
+  if (flip_start) flip_all(s->v, n);
+  if ((!insertion && N == 0) || (insertion && N >= s->cap_water)) {
+    rec->status = insertion ? 2 : 1;
+    if (flip_end) flip_all(s->v, n);
+    return 0;
+  }
+  int ntot = insertion ? n + 3 : n;
+  double* xs = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+  double* vs = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+  memcpy(xs, s->x, sizeof(double) * 3 * (size_t)n);
+  memcpy(vs, s->v, sizeof(double) * 3 * (size_t)n);
+  uint8_t* fly = (uint8_t*)calloc((size_t)ntot, 1);
+  uint8_t* gone = (uint8_t*)calloc((size_t)ntot, 1);
+  orc_params pt = *p; /* the layout of the trial: an inserted water counts among the waters */
+  pt.n_water = insertion ? N + 1 : N;
+  int m = insertion ? N : pick(b1[0], N);
+  for (int a = 3 * m; a < 3 * m + 3; ++a) fly[a] = 1, gone[a] = 2;
+  double Ustart, Uend, Kstart, Kend;
+  if (insertion) {
+    memmove(s->x + 9 * (N + 1), s->x + 9 * N, sizeof(double) * 3 * (size_t)n_ion);
+    memmove(s->v + 9 * (N + 1), s->v + 9 * N, sizeof(double) * 3 * (size_t)n_ion);
+    place_water(p, b1, b2, b3, b4, s->x + 9 * N, s->v + 9 * N);
+    /* H_start: the N-water system, the flyer absent; H_end: N + 1 waters in 3D */
+    Ustart = orc_energy_forces(&pt, ntot, s->x, NULL, gone, NULL);
+    Kstart = orc_kinetic(&pt, ntot, s->v, fly);
+    rec->w_prot = nemd(&pt, ntot, s->x, s->v, fly, 1);
+    Uend = orc_energy_forces(&pt, ntot, s->x, NULL, NULL, NULL);
+    Kend = orc_kinetic(&pt, ntot, s->v, fly);
+  } else {
+    rec->cation = m; /* the deleted water */
+    Ustart = orc_energy_forces(&pt, n, s->x, NULL, NULL, NULL);
+    Kstart = orc_kinetic(&pt, n, s->v, fly);
+    rec->w_prot = nemd(&pt, n, s->x, s->v, fly, 0);
+    Uend = orc_energy_forces(&pt, n, s->x, NULL, gone, NULL);
+    Kend = orc_kinetic(&pt, n, s->v, fly);
+  }
+  double dH = (Uend + Kend) - (Ustart + Kstart);
+  rec->dH = dH;
+  double x_acc;
+  if (insertion) {
+    rec->beta_dM = p->beta * dH - log(V / (double)(N + 1));
+    x_acc = -rec->beta_dM + p->beta_mu;
+  } else {
+    rec->beta_dM = -p->beta * dH - log(V / (double)N);
+    x_acc = rec->beta_dM - p->beta_mu;
+  }
+  rec->x_acc = x_acc;
+  int accept = isfinite(dH) && (ln_u < x_acc) && !p->no_accept;
+  if (!isfinite(dH)) rec->status = 3;
+  if (accept) {
+    if (insertion) {
+      s->n_water = N + 1;
+    } else {
+      memcpy(s->x + 9 * m, s->x + 9 * (N - 1), sizeof(double) * 9); /* swap-with-last */
+      memcpy(s->v + 9 * m, s->v + 9 * (N - 1), sizeof(double) * 9);
+      memmove(s->x + 9 * (N - 1), s->x + 9 * N, sizeof(double) * 3 * (size_t)n_ion);
+      memmove(s->v + 9 * (N - 1), s->v + 9 * N, sizeof(double) * 3 * (size_t)n_ion);
+      s->n_water = N - 1;
+    }
+  } else {
+    memcpy(s->x, xs, sizeof(double) * 3 * (size_t)n);
+    memcpy(s->v, vs, sizeof(double) * 3 * (size_t)n);
+  }
+  rec->accepted = accept;
+  rec->n_after = s->n_water;
+  if (flip_end) flip_all(s->v, 3 * s->n_water + n_ion);
+  free(xs);
+  free(vs);
+  free(fly);
+  free(gone);
   return 0;
 }
 

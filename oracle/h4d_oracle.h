@@ -79,13 +79,20 @@ typedef struct {
    * particle): every atom after the waters is one species of type 0, and a trial inserts
    * or deletes one of them; n_pairs and cap_pairs of the state count particles */
   int32_t single;
+  /* rigid-water exchange (Sec. II.A for one flyer; Sec. II.C on flying rigid waters): a
+   * trial inserts or deletes one rigid water, which flies frozen in 3D (position and
+   * orientation) while the others move.  The number of waters then lives in the state
+   * (orc_state.n_water, at most cap_water) and p->n_water is ignored by the functions
+   * that take a state; ions keep their pairs and follow the waters in the layout. */
+  int32_t water_ex, pad_w;
 } orc_params;
 
 typedef struct {
   int32_t n_pairs, cap_pairs;
-  double *x, *v;       /* [(3*n_water + 2*cap_pairs) * 3] */
+  double *x, *v;       /* [(3*n_water + 2*cap_pairs) * 3]; 3*cap_water with water exchange */
   uint64_t trial_ctr;  /* trials done by this chain (Philox counter of trial draws) */
   uint64_t step_ctr;   /* equilibrium MD steps done (Philox counter of thermostat draws) */
+  int32_t n_water, cap_water; /* water exchange only: current and largest number of waters */
 } orc_state;
 
 typedef struct {

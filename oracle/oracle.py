@@ -92,6 +92,8 @@ class Params(ctypes.Structure):
         ("v_ex", ctypes.c_double),
         ("no_accept", ctypes.c_int32),
         ("single", ctypes.c_int32),
+        ("water_ex", ctypes.c_int32),
+        ("pad_w", ctypes.c_int32),
     ]
 
 
@@ -103,6 +105,8 @@ class _State(ctypes.Structure):
         ("v", ctypes.POINTER(ctypes.c_double)),
         ("trial_ctr", ctypes.c_uint64),
         ("step_ctr", ctypes.c_uint64),
+        ("n_water", ctypes.c_int32),
+        ("cap_water", ctypes.c_int32),
     ]
 
 
@@ -252,16 +256,23 @@ def make_params(cfg: dict, **override) -> Params:
     p.v_ex = float(c.get("v_ex", 0.0))
     p.no_accept = int(bool(c.get("no_accept", 0)))
     p.single = int(c.get("exchange", "pair") == "single")
+    p.water_ex = int(c.get("exchange", "pair") == "water")
     return p
 
 
 class State:
     """A chain's state: positions and velocities of 3*n_water + 2*cap_pairs atoms (one atom
-    per unit instead of two with single-particle exchange)."""
+    per unit instead of two with single-particle exchange).  With water exchange the
+    number of waters starts at p.n_water and varies up to cap_water."""
 
-    def __init__(self, p: Params, x: np.ndarray, v: np.ndarray | None, n_pairs: int, cap_pairs: int):
+    def __init__(self, p: Params, x: np.ndarray, v: np.ndarray | None, n_pairs: int, cap_pairs: int,
+                 cap_water: int | None = None):
         self.unit = 1 if p.single else 2
-        n_cap = 3 * p.n_water + self.unit * cap_pairs
+        self.water_ex = bool(p.water_ex)
+        cap_w = p.n_water if cap_water is None else int(cap_water)
+        if cap_w < p.n_water:
+            raise ValueError("cap_water below the number of waters")
+        n_cap = 3 * cap_w + self.unit * cap_pairs
         self.x = np.zeros((n_cap, 3), np.float64)
         self.v = np.zeros((n_cap, 3), np.float64)
         n = 3 * p.n_water + self.unit * n_pairs
@@ -275,7 +286,13 @@ class State:
         self.s.v = _ptr(self.v)
         self.s.trial_ctr = 0
         self.s.step_ctr = 0
-        self.n_water = p.n_water
+        self.s.n_water = p.n_water
+        self.s.cap_water = cap_w
+        self._n_water = p.n_water
+
+    @property
+    def n_water(self) -> int:
+        return self.s.n_water if self.water_ex else self._n_water
 
     @property
     def n_pairs(self) -> int:
