@@ -67,6 +67,8 @@ typedef struct h4d_ctx h4d_ctx;
 #define H4D_EXCHANGE_PAIR 0   /* cation-anion pairs (Eqs. 3-8) */
 #define H4D_EXCHANGE_SINGLE 1 /* single particles of one neutral species (Sec. II.A: the
                                  pair rule with one flyer, V/(N+1) to the first power) */
+#define H4D_EXCHANGE_WATER 2  /* one rigid water per trial (Sec. II.A with one flyer; Sec.
+                                 II.C: molecular-frame velocities), frozen in 3D while it flies */
 
 /* Physics, protocol and engine settings common to all replicas of a context. */
 typedef struct h4d_params {
@@ -98,7 +100,11 @@ typedef struct h4d_params {
                              every ion-block atom is one species with the parameters of
                              type 0, and the "pair" counts of h4d_system, h4d_counts and the
                              records count particles; bias, learned proposal, species w_max
-                             and early rejection are pair moves (H4D_EINVAL) */
+                             and early rejection are pair moves (H4D_EINVAL); or
+                             H4D_EXCHANGE_WATER: aqueous system, one w_max (species w_max
+                             off), the ion pairs stay, the "pair" counts of h4d_counts.sum_n
+                             and of the records count waters, and a deletion record's
+                             cation field holds the deleted water's index */
   int32_t pad_exchange;
 } h4d_params;
 
@@ -118,6 +124,10 @@ typedef struct h4d_system {
   const double* host_x;
   const double* host_v;
   const uint64_t* replica_key; /* [R] or NULL */
+  const int32_t* cap_water;    /* [R] or NULL (= n_water): the most waters a replica may hold
+                                  under water exchange; atoms [0, 3 n_water) are the waters and
+                                  the ions follow them, so a water insertion moves every ion up
+                                  by three atoms and a deletion moves them down */
 } h4d_system;
 
 /* Per-replica counters. */
@@ -143,6 +153,7 @@ typedef struct h4d_counts {
   double t_last_end_ns;     /* finished the most recent launch (ns; compare across replicas) */
   int64_t plan_warps;       /* warps of this replica's group in the launch plan */
   int64_t plan_cta_groups;  /* replicas (groups) sharing its CTA, itself included */
+  int64_t n_water;          /* current rigid waters (varies under water exchange) */
 } h4d_counts;
 
 /* One trial record; Delta M follows the insertion direction (Eqs. 6, 8). */
@@ -151,7 +162,8 @@ typedef struct h4d_record {
   int32_t accepted;
   int32_t n_before, n_after;
   int32_t status;     /* 0 ok, 1 deletion from empty system, 2 capacity, 3 non-finite work */
-  int32_t cation, anion; /* chosen pair index (deletion), else -1 */
+  int32_t cation, anion; /* chosen pair index (deletion), else -1; water exchange: the
+                            deleted water in cation, anion -1 */
   int32_t cell_c, cell_a; /* proposal-grid cells of the exchanged cation and anion, or -1
                              when no proposal grid is enabled */
   int32_t instant;    /* 1: instantaneous move of the early-rejection scheme (no NEMD) */
@@ -252,6 +264,11 @@ int h4d_get_state(h4d_ctx* ctx, int32_t replica, double* host_x, double* host_v,
  * above the replica's cap_pairs.  Neighbour rows are rebuilt at the next launch. */
 int h4d_set_state(h4d_ctx* ctx, int32_t replica, int32_t n_pairs, const double* host_x,
                   const double* host_v);
+/* the same with the number of waters (water exchange: up to the replica's cap_water;
+ * otherwise it must equal the replica's n_water): host_x [3*n_water + 2*n_pairs][3];
+ * H4D_ECAPACITY when n_water is negative or above the capacity */
+int h4d_set_water_state(h4d_ctx* ctx, int32_t replica, int32_t n_water, int32_t n_pairs,
+                        const double* host_x, const double* host_v);
 int32_t h4d_num_replicas(h4d_ctx* ctx);
 
 /* ---- device facts (no paper counterpart; measurement support) ---- */

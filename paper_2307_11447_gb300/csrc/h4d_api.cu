@@ -216,7 +216,12 @@ static int check_params(const h4d_params* p) {
     // the LJ specialisation assumes equal sizes/energies and charges +q/-q
     if (p->sig[0] != p->sig[1] || p->eps[0] != p->eps[1] || p->q[0] != -p->q[1]) return H4D_EINVAL;
   }
-  if (p->exchange != H4D_EXCHANGE_PAIR && p->exchange != H4D_EXCHANGE_SINGLE) return H4D_EINVAL;
+  if (p->exchange != H4D_EXCHANGE_PAIR && p->exchange != H4D_EXCHANGE_SINGLE && p->exchange != H4D_EXCHANGE_WATER)
+    return H4D_EINVAL;
+  // rigid-water exchange needs the water model: the aqueous system with its bond lengths
+  if (p->exchange == H4D_EXCHANGE_WATER &&
+      (p->system != H4D_SYS_AQ || p->ntypes < 4 || !(p->d_oh > 0) || !(p->d_hh > 0) || !(p->d_hh < 2 * p->d_oh)))
+    return H4D_EINVAL;
   // single particles: one neutral species (a lone charge would leave the box charged)
   if (p->exchange == H4D_EXCHANGE_SINGLE && (p->system != H4D_SYS_LJ || p->q[0] != 0.0 || p->q[1] != 0.0))
     return H4D_EINVAL;
@@ -295,6 +300,27 @@ static void fill_pot(const h4d_params& p, Pot& P, Proto& pr) {
   pr.rw = 1.0;
   pr.single = p.exchange == H4D_EXCHANGE_SINGLE;
   pr.unit = unit_of(p);
+  pr.water = p.exchange == H4D_EXCHANGE_WATER;
+  if (pr.water) {
+    // body frame of the rigid water: O at the origin, H at (+-d_oh sin(t/2), d_oh cos(t/2), 0)
+    const double sh = 0.5 * p.d_hh / p.d_oh, ch = std::sqrt(1.0 - sh * sh);
+    const double mO = p.mass[2], mH = p.mass[3];
+    pr.wh[0][0] = p.d_oh * sh;
+    pr.wh[1][0] = -p.d_oh * sh;
+    pr.wh[0][1] = pr.wh[1][1] = p.d_oh * ch;
+    pr.wh[0][2] = pr.wh[1][2] = 0.0;
+    const double M = mO + 2.0 * mH;
+    pr.wcom_y = 2.0 * mH * p.d_oh * ch / M;
+    const double yo = -pr.wcom_y, yh = p.d_oh * ch - pr.wcom_y, xh = p.d_oh * sh;
+    const double Ix = mO * yo * yo + 2.0 * mH * yh * yh;  // about x: sum m (y^2 + z^2)
+    const double Iy = 2.0 * mH * xh * xh;                 // about y: sum m (x^2 + z^2)
+    // mass and moments times mvv2e: the velocity draw of an insertion has
+    // var V = 1 / (beta M mvv2e) and var omega_k = 1 / (beta I_k mvv2e)
+    pr.wM = M * p.mvv2e;
+    pr.wI[0] = Ix * p.mvv2e;
+    pr.wI[1] = Iy * p.mvv2e;
+    pr.wI[2] = (Ix + Iy) * p.mvv2e;  // about z (a planar body)
+  }
 }
 
 // neighbour-row capacity from the densest plausible packing (about one particle per sigma^3
@@ -686,16 +712,19 @@ int h4d_create(const h4d_params* params, const h4d_system* sys, uint64_t seed, v
     Rep& R = c->rep_h[r];
     std::memset(&R, 0, sizeof(Rep));
     int nw = sys->n_water ? sys->n_water[r] : 0;
-    if (nw < 0 || sys->n_pairs[r] < 0 || sys->cap_pairs[r] < sys->n_pairs[r] || !(sys->L[r] > 0)) {
+    int cw = sys->cap_water ? sys->cap_water[r] : nw;
+    if (nw < 0 || cw < nw || sys->n_pairs[r] < 0 || sys->cap_pairs[r] < sys->n_pairs[r] || !(sys->L[r] > 0)) {
       h4d_destroy(c);
       return H4D_EINVAL;
     }
-    if (nw > 0 && params->system != H4D_SYS_AQ) { h4d_destroy(c); return H4D_EINVAL; }
+    if (cw > 0 && params->system != H4D_SYS_AQ) { h4d_destroy(c); return H4D_EINVAL; }
+    if (cw != nw && params->exchange != H4D_EXCHANGE_WATER) { h4d_destroy(c); return H4D_EINVAL; }
     R.n_water = nw;
     R.nw3 = 3 * nw;
+    R.cap_water = cw;
     R.n_pairs = sys->n_pairs[r];
     R.cap_pairs = sys->cap_pairs[r];
-    R.cap_atoms = R.nw3 + unit_of(*params) * R.cap_pairs;
+    R.cap_atoms = 3 * cw + unit_of(*params) * R.cap_pairs;
     if (R.cap_atoms > 65535 || R.cap_atoms < 1) { h4d_destroy(c); return H4D_ECAPACITY; }
     if (2.0 * (rmax_of(*params) + params->skin) >= sys->L[r]) { h4d_destroy(c); return H4D_EINVAL; }
     R.atom_off = off;
@@ -778,7 +807,7 @@ int h4d_set_protocol(h4d_ctx* c, int32_t n_f, double w_max, double dt, double ka
 }
 
 int h4d_set_species_wmax(h4d_ctx* c, double f_w) {
-  if (c && c->eng.proto.single && f_w != 0.0) return H4D_EINVAL;  // a pair move
+  if (c && (c->eng.proto.single || c->eng.proto.water) && f_w != 0.0) return H4D_EINVAL;  // a pair move
   if (!c || !std::isfinite(f_w) || f_w < 0 || (f_w > 0 && !(c->prm.w_max > 0))) return H4D_EINVAL;
   c->eng.proto.fw = f_w;
   c->eng.proto.rw = species_rw(c->prm, f_w);
@@ -787,7 +816,7 @@ int h4d_set_species_wmax(h4d_ctx* c, double f_w) {
 }
 
 int h4d_set_bias(h4d_ctx* c, double alpha_b, double x_b) {
-  if (c && c->eng.proto.single && alpha_b != 0.0) return H4D_EINVAL;  // a pair move
+  if (c && (c->eng.proto.single || c->eng.proto.water) && alpha_b != 0.0) return H4D_EINVAL;  // a pair move
   if (!c || !std::isfinite(alpha_b) || !std::isfinite(x_b) || alpha_b < 0 || x_b < 0) return H4D_EINVAL;
   if (alpha_b > 0 && c->eng.proto.prop_mode) return H4D_EINVAL;  // one placement rule at a time
   c->eng.proto.bias_on = alpha_b > 0 ? 1 : 0;
@@ -798,7 +827,7 @@ int h4d_set_bias(h4d_ctx* c, double alpha_b, double x_b) {
 }
 
 int h4d_set_early_rejection(h4d_ctx* c, double v_ex) {
-  if (c && c->eng.proto.single && v_ex != 0.0) return H4D_EINVAL;  // a pair move
+  if (c && (c->eng.proto.single || c->eng.proto.water) && v_ex != 0.0) return H4D_EINVAL;  // a pair move
   if (!c || !std::isfinite(v_ex) || v_ex < 0) return H4D_EINVAL;
   c->eng.proto.vex_edge = v_ex > 0 ? std::cbrt(v_ex) : 0.0;
   invalidate_graphs(c);
@@ -936,6 +965,7 @@ int h4d_get_counts(h4d_ctx* c, int32_t r, h4d_counts* out) {
   out->last_smid = R.smid;
   out->t_last_begin_ns = (double)R.t_begin;
   out->t_last_end_ns = (double)R.t_end;
+  out->n_water = R.n_water;
   out->plan_warps = 0;
   out->plan_cta_groups = 0;
   for (size_t k = 0; k + 1 < c->cta_groups_h.size(); ++k)
@@ -1020,6 +1050,25 @@ int h4d_set_state(h4d_ctx* c, int32_t r, int32_t n_pairs, const double* x, const
   return push_plan(c);
 }
 
+int h4d_set_water_state(h4d_ctx* c, int32_t r, int32_t n_water, int32_t n_pairs, const double* x, const double* v) {
+  if (!c || r < 0 || r >= c->R || !x) return H4D_EINVAL;
+  int rc = pull_reps(c);
+  if (rc) return rc;
+  Rep& R = c->rep_h[r];
+  if (n_water < 0 || n_water > R.cap_water) return H4D_ECAPACITY;
+  if (!c->eng.proto.water && n_water != R.n_water) return H4D_EINVAL;
+  const int nw = R.n_water;
+  R.n_water = n_water;
+  R.nw3 = 3 * n_water;
+  rc = upload_replica(c, r, n_pairs, x, v);
+  if (rc) {
+    R.n_water = nw;
+    R.nw3 = 3 * nw;
+    return rc;
+  }
+  return push_plan(c);
+}
+
 int h4d_count_pairs(h4d_ctx* c, int64_t* n) {
   if (!c || !n) return H4D_EINVAL;
   CK(cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->stream));
@@ -1098,7 +1147,7 @@ int h4d_measure_fp32_peak(double* tflops, double* seconds) {
 }
 
 // ---- checkpoint: a flat binary image of the replica table and per-atom state ----
-static const uint64_t kMagic = 0x3430303044344848ULL;  // "HH4D0004"
+static const uint64_t kMagic = 0x3530303044344848ULL;  // "HH4D0005"
 
 int h4d_save(h4d_ctx* c, const char* path) {
   if (!c || !path) return H4D_EINVAL;
@@ -1153,14 +1202,18 @@ int h4d_load(h4d_ctx* c, const char* path) {
     // a checkpoint of the same system: its layout must be this context's, and the fields
     // the kernels index with must be in range
     if (f.atom_off != cur.atom_off || f.cap_atoms != cur.cap_atoms || f.cap_pairs != cur.cap_pairs ||
-        f.n_water != cur.n_water || f.L != cur.L)
+        f.cap_water != cur.cap_water || f.L != cur.L)
       return H4D_EINVAL;
+    if (!c->eng.proto.water && f.n_water != cur.n_water) return H4D_EINVAL;
+    if (f.n_water < 0 || f.n_water > cur.cap_water || f.nw3 != 3 * f.n_water) return H4D_EINVAL;
     if (f.n_pairs < 0 || f.n_pairs > cur.cap_pairs || f.rec_count < 0) return H4D_EINVAL;
     if (f.tpa < 1 || f.tpa > 32 || (f.tpa & (f.tpa - 1))) return H4D_EINVAL;  // lanes per row: 1..32, a power of two
     // only the chain's state and statistics come from the file; geometry, thresholds,
     // offsets, the proposal grid and the record rings stay this context's
     Rep m = cur;
     m.n_pairs = f.n_pairs;
+    m.n_water = f.n_water;
+    m.nw3 = f.nw3;
     m.tpa = f.tpa;
     m.rec_count = f.rec_count;
     m.trial_ctr = f.trial_ctr;
@@ -1224,6 +1277,7 @@ int h4d_eval_forces(const h4d_params* params, double L, int32_t n_water, int32_t
   std::memset(&R, 0, sizeof(Rep));
   R.n_water = n_water;
   R.nw3 = 3 * n_water;
+  R.cap_water = n_water;
   R.n_pairs = (n - 3 * n_water) / unit_of(*params);
   R.cap_pairs = R.n_pairs;
   R.cap_atoms = std::max(n, 1);
@@ -1431,6 +1485,7 @@ extern "C" int h4d_eval_forces_static(const h4d_params* params, double L, int32_
   std::memset(&R, 0, sizeof(Rep));
   R.n_water = n_water;
   R.nw3 = 3 * n_water;
+  R.cap_water = n_water;
   R.n_pairs = (n - 3 * n_water) / unit_of(*params);
   R.cap_pairs = R.n_pairs;
   R.cap_atoms = n;
@@ -1545,7 +1600,7 @@ static int prop_pack(PropDev* P, cudaStream_t s) {
 extern "C" {
 
 int h4d_proposal(h4d_ctx* c, int32_t mode, double cell_len, double eps, int32_t records_per_replica) {
-  if (c && c->eng.proto.single) return H4D_EINVAL;  // the proposal places ion pairs
+  if (c && (c->eng.proto.single || c->eng.proto.water)) return H4D_EINVAL;  // the proposal places ion pairs
   if (!c || (mode != H4D_PROPOSAL_UNIFORM && mode != H4D_PROPOSAL_LEARNED) || !(cell_len > 0) || !(eps > 0) ||
       !(eps <= 1) || records_per_replica < 0 || records_per_replica > (1 << 20))
     return H4D_EINVAL;

@@ -221,11 +221,15 @@ struct GScal {
   int flip_s, flip_e, cat, ani;
   int n_before, accept, inst;  // inst: instantaneous move (early rejection)
   int flag_timeout;            // a bounded iteration (SHAKE, RATTLE, gamma draw) gave up
+  int fly2, flyw;              // water exchange: third flying atom, flying water (-1 = none)
+  int nw_trial, pad_t;         // waters in the layout of the running trial
   float w_cur, g_scr, pad2, pad3;
-  double alpha_th, dW[2], wprot, wprot_c, red_out;
+  double alpha_th, dW[3], wprot, wprot_c, red_out;
   double ln_u, ustart, kstart, uend, kend;
   double vfly[6];
   unsigned int xfly[6];
+  double vw[9];            // velocities of an inserted water (O, H, H)
+  unsigned int xw[9];      // its fixed-point coordinates
   double kw[32];
   float d1w[32], d2w[32];  // per-warp largest and second-largest displacement since the build
   float o1w[32], o2w[32];  // the same since the outer-list build
@@ -737,7 +741,7 @@ __device__ H4D_PHASE void force_pass_impl(const Ctx& cref, int mode, float w_pre
   const int tpa = c.tpa, ltpa = c.ltpa;
   const int nsub = c.T >> ltpa;
   const int sub = c.tid >> ltpa, lin = c.tid & (tpa - 1);
-  const int fly0 = NEMD ? v.s->fly0 : -1, fly1 = NEMD ? v.s->fly1 : -1;
+  const int fly0 = NEMD ? v.s->fly0 : -1, fly1 = NEMD ? v.s->fly1 : -1, fly2 = NEMD ? v.s->fly2 : -1;
   const float gscr = NEMD ? v.s->g_scr : 1.0f;
   const float scale = R.scale;
   const float half_dt = 0.5f * (float)e.proto.dt;
@@ -752,7 +756,7 @@ __device__ H4D_PHASE void force_pass_impl(const Ctx& cref, int mode, float w_pre
     // aqueous: the per-atom force is a sum of hundreds of large, cancelling Coulomb
     // terms, so it is accumulated with Kahan compensation (cx, cy, cz)
     float cx = 0.f, cy = 0.f, cz = 0.f;
-    const bool iflyer = NEMD && active && (i == fly0 || i == fly1);
+    const bool iflyer = NEMD && active && (i == fly0 || i == fly1 || i == fly2);
     if (active) {
       const uint4 pi = v.pos[i];
       const int ti = type_t<SYS>(i, R.nw3);
@@ -855,7 +859,7 @@ __device__ H4D_PHASE void force_pass_impl(const Ctx& cref, int mode, float w_pre
         const float go = __expf(-P.kappa_sr * (0.5f * (1.0f + rw) * w_prev));
         for (int s2 = lin; s2 < cnt; s2 += tpa) {
           const int j = e.nbr[nbr_index(e, R, i, s2, ltpa)];
-          if (j == fly0 || j == fly1) continue;
+          if (j == fly0 || j == fly1 || j == fly2) continue;
           const uint4 pj = v.pos[j];
           const float dx = (float)(int)(pj.x - pi.x) * scale;
           const float dy = (float)(int)(pj.y - pi.y) * scale;
@@ -884,7 +888,7 @@ __device__ H4D_PHASE void force_pass_impl(const Ctx& cref, int mode, float w_pre
     if (active && lin == 0) {
       const int ga = R.atom_off + i;
       e.force[ga] = make_float4(fx, fy, fz, 0.f);
-      if (NEMD && (mode & 4) && iflyer) v.s->dW[i == fly0 ? 0 : 1] = (double)dwk;
+      if (NEMD && (mode & 4) && iflyer) v.s->dW[i == fly0 ? 0 : (i == fly1 ? 1 : 2)] = (double)dwk;
       if (!iflyer && (mode & 3)) {
         float4 h = e.vhi[ga], l = e.vlo[ga];
         const int ti = type_t<SYS>(i, R.nw3);
@@ -1027,7 +1031,9 @@ __device__ double rattle_pass(const Ctx& c, bool want_k) {
   const float dd[3] = {(float)P.d_oh2, (float)P.d_oh2, (float)P.d_hh2};
   long long kin = 0;  // kinetic energy, fixed point (exact, order-free sum)
   int kbad = 0;
+  const int flyw = v.s->flyw;
   for (int m = c.tid; m < R.n_water; m += c.T) {
+    if (m == flyw) continue;  // frozen: its held velocities stay as drawn
     const int a0 = 3 * m;
     float4 vh[3], vl[3];
     uint4 po[3];
@@ -1110,9 +1116,10 @@ __device__ H4D_PHASE void kick_drift(const Ctx& cref, float alpha) {
   float d1 = 0.f, d2 = 0.f;  // this thread's two largest displacements (Verlet list)
   float o1 = 0.f, o2 = 0.f;  // the same against the outer-list reference
   const int n_units = R.n_water + (n - R.nw3);  // rigid waters first, then ions
+  const int flyw = v.s->flyw;  // a flying water is frozen in 3D like a flying ion
   for (int u = c.tid; u < n_units; u += c.T) {
     if (SYS == H4D_SYS_AQ && u < R.n_water) {
-      water_kick_drift(c, u, alpha, d1, d2, o1, o2, bad);
+      if (u != flyw) water_kick_drift(c, u, alpha, d1, d2, o1, o2, bad);
       continue;
     }
     const int a = R.nw3 + (u - R.n_water);
@@ -1226,15 +1233,15 @@ __device__ void negate_velocities(const Ctx& c, int n) {
 // ------------------------------------------------------------------------------------
 // FP64 end-point energies
 // ------------------------------------------------------------------------------------
-// U over atoms [0, n_tot) leaving out ex0/ex1 (-1 = none); each unordered pair once
-__device__ H4D_PHASE double energy64_impl(const Ctx& cref, int ex0, int ex1);
-__device__ double energy64(const Ctx& c, int ex0, int ex1) {
+// U over atoms [0, n_tot) leaving out ex0/ex1/ex2 (-1 = none); each unordered pair once
+__device__ H4D_PHASE double energy64_impl(const Ctx& cref, int ex0, int ex1, int ex2);
+__device__ double energy64(const Ctx& c, int ex0, int ex1, int ex2 = -1) {
   const u64 t0 = (c.tid == 0) ? gtimer() : 0;
-  const double u = energy64_impl(c, ex0, ex1);
+  const double u = energy64_impl(c, ex0, ex1, ex2);
   if (c.tid == 0) c.R->t_energy_ns += (double)(gtimer() - t0);
   return u;
 }
-__device__ H4D_PHASE double energy64_impl(const Ctx& cref, int ex0, int ex1) {
+__device__ H4D_PHASE double energy64_impl(const Ctx& cref, int ex0, int ex1, int ex2) {
   const Ctx c = cref;
   const Eng& e = *c.e;
   const RepC& R = c.r;
@@ -1247,7 +1254,7 @@ __device__ H4D_PHASE double energy64_impl(const Ctx& cref, int ex0, int ex1) {
   // per-atom Kahan sums over the row (j > i), then a sum over atoms in a fixed order
   for (int i = c.tid; i < n; i += c.T) {
     double acc = 0.0, comp = 0.0;
-    if (i == ex0 || i == ex1) {
+    if (i == ex0 || i == ex1 || i == ex2) {
       e.red[R.atom_off + i] = 0.0;
       continue;
     }
@@ -1257,7 +1264,7 @@ __device__ H4D_PHASE double energy64_impl(const Ctx& cref, int ex0, int ex1) {
     const int cnt = e.ncnt[R.atom_off + i];
     for (int s = 0; s < cnt; ++s) {
       const int j = e.nbr[nbr_index(e, R, i, s, c.ltpa)];
-      if (j <= i || j == ex0 || j == ex1) continue;
+      if (j <= i || j == ex0 || j == ex1 || j == ex2) continue;
       const uint4 pj = v.pos[j];
       const double dx = (double)(int)(pj.x - pi.x) * scale;
       const double dy = (double)(int)(pj.y - pi.y) * scale;
@@ -1281,10 +1288,10 @@ __device__ double kinetic64(const Ctx& c) {
   const Eng& e = *c.e;
   const RepC& R = c.r;
   const int n = c.v.s->n_tot;
-  const int fly0 = c.v.s->fly0, fly1 = c.v.s->fly1;
+  const int fly0 = c.v.s->fly0, fly1 = c.v.s->fly1, fly2 = c.v.s->fly2;
   for (int a = c.tid; a < n; a += c.T) {
     const int ga = R.atom_off + a;
-    if (a == fly0 || a == fly1) {
+    if (a == fly0 || a == fly1 || a == fly2) {
       e.red[ga] = 0.0;
       continue;
     }
@@ -1431,7 +1438,7 @@ __device__ H4D_PHASE void nemd_steps(const Ctx& cref, int n_steps) {
   GScal* S = c.v.s;
   const int ins = S->ins;
   const bool single = e.proto.single != 0;
-  const int f0 = S->fly0, f1 = S->fly1;
+  const int f0 = S->fly0, f1 = S->fly1, f2 = S->fly2;
   if (n_steps > 0) {
     force_pass<SYS>(c, 0, 0.f, nullptr);
     c.sync();
@@ -1453,6 +1460,11 @@ __device__ H4D_PHASE void nemd_steps(const Ctx& cref, int n_steps) {
         uint4 p1 = c.v.pos[f1];
         p1.w = __float_as_uint(w_next_a);
         c.v.pos[f1] = p1;
+      }
+      if (f2 >= 0) {  // the third atom of a flying water (one w_max: w_next_a = w_next)
+        uint4 p2 = c.v.pos[f2];
+        p2.w = __float_as_uint(w_next);
+        c.v.pos[f2] = p2;
       }
       S->w_cur = w_next;
       S->g_scr = expf(-e.pot.kappa_sr * (single ? w_next : 0.5f * (w_next + w_next_a)));
@@ -1478,7 +1490,7 @@ __device__ H4D_PHASE void nemd_steps(const Ctx& cref, int n_steps) {
         const int ta = type_of(f0, c.r.nw3), tb = type_of(f1, c.r.nw3);
         dff = pair_u64(e.pot, ta, tb, r3 + dn * dn, 1.0) - pair_u64(e.pot, ta, tb, r3 + dp * dp, 1.0);
       }
-      const double y = (S->dW[0] + S->dW[1] + dff) - S->wprot_c;
+      const double y = (S->dW[0] + S->dW[1] + S->dW[2] + dff) - S->wprot_c;
       const double t = S->wprot + y;
       S->wprot_c = (t - S->wprot) - y;
       S->wprot = t;
@@ -1794,8 +1806,282 @@ __device__ __noinline__ double bias_sum(const Proto& pr, double L, const uint4* 
   return sum;
 }
 
+// ------------------------------------------------------------------------------------
+// Rigid-water exchange (Sec. II.A with one flyer; Sec. II.C: molecular-frame velocities).
+// Readings as in the oracle: the flying water is frozen in 3D (position and orientation;
+// no drift, kick or constraint step) while its altitude follows the schedule; Delta H and
+// the momentum reversals as for pairs; V/(N_w+1) once.  Layout: waters first, ions
+// after them, so an insertion moves the ions up by three atoms and places the new water
+// last, and an accepted deletion moves the last water into the deleted slot and the ions
+// down by three.
+// ------------------------------------------------------------------------------------
+
+// The inserted water from its trial draws: the O at the 32-bit box fractions of block 1
+// words 0-2; the H atoms at the O's fixed-point coordinate plus the rotated body offsets
+// rounded to the grid; a uniform orientation from the three uniforms of block 2 (unit
+// quaternion (sqrt(1-u1) sin 2 pi u2, sqrt(1-u1) cos 2 pi u2, sqrt(u1) sin 2 pi u3,
+// sqrt(u1) cos 2 pi u3), Shoemake 1992); velocities drawn in the molecular frame: centre of
+// mass N(0, 1/(beta M)) per axis, angular velocity N(0, 1/(beta I_k)) about body axis k
+// (six normals of blocks 3-4), atom a moving with V + R (omega x (a_body - com)).
+__device__ __noinline__ void water_placement(const Proto& pr, double L, const u64* b1, const u64* b2,
+                                             const u64* b3, const u64* b4, unsigned* xw, double* vw) {
+  const double u1 = u01(b2[0]), u2 = u01(b2[1]), u3 = u01(b2[2]);
+  const double a = sqrt(1.0 - u1), b = sqrt(u1);
+  double s2, c2, s3, c3;
+  sincospi(2.0 * u2, &s2, &c2);
+  sincospi(2.0 * u3, &s3, &c3);
+  const double qx = a * s2, qy = a * c2, qz = b * s3, qw = b * c3;
+  const double Rm[3][3] = {{1.0 - 2.0 * (qy * qy + qz * qz), 2.0 * (qx * qy - qw * qz), 2.0 * (qx * qz + qw * qy)},
+                           {2.0 * (qx * qy + qw * qz), 1.0 - 2.0 * (qx * qx + qz * qz), 2.0 * (qy * qz - qw * qx)},
+                           {2.0 * (qx * qz - qw * qy), 2.0 * (qy * qz + qw * qx), 1.0 - 2.0 * (qx * qx + qy * qy)}};
+  for (int d = 0; d < 3; ++d) xw[d] = (unsigned)(b1[d] >> 32);
+  for (int k = 0; k < 2; ++k)
+    for (int d = 0; d < 3; ++d) {
+      const double off = Rm[d][0] * pr.wh[k][0] + Rm[d][1] * pr.wh[k][1] + Rm[d][2] * pr.wh[k][2];
+      const long long dk = __double2ll_rn(off / L * 4294967296.0);
+      xw[3 * (k + 1) + d] = xw[d] + (unsigned)(unsigned long long)dk;
+    }
+  const double sv = sqrt(1.0 / (pr.beta * pr.wM));
+  const double V[3] = {sv * gauss_c(b3[0], b3[1]), sv * gauss_s(b3[0], b3[1]), sv * gauss_c(b3[2], b3[3])};
+  const double om[3] = {sqrt(1.0 / (pr.beta * pr.wI[0])) * gauss_s(b3[2], b3[3]),
+                        sqrt(1.0 / (pr.beta * pr.wI[1])) * gauss_c(b4[0], b4[1]),
+                        sqrt(1.0 / (pr.beta * pr.wI[2])) * gauss_s(b4[0], b4[1])};
+  for (int at = 0; at < 3; ++at) {
+    double r[3];
+    for (int d = 0; d < 3; ++d) r[d] = (at == 0 ? 0.0 : pr.wh[at - 1][d]) - (d == 1 ? pr.wcom_y : 0.0);
+    const double u[3] = {om[1] * r[2] - om[2] * r[1], om[2] * r[0] - om[0] * r[2], om[0] * r[1] - om[1] * r[0]};
+    for (int d = 0; d < 3; ++d) vw[3 * at + d] = V[d] + Rm[d][0] * u[0] + Rm[d][1] * u[1] + Rm[d][2] * u[2];
+  }
+}
+
+// NEMD, decision and commit of a water trial whose flyer is in place (N waters before it,
+// n atoms in the start layout)
+template <int SYS>
+__device__ void trial_water_run(const Ctx& c, int N, int n) {
+  const Eng& e = *c.e;
+  Rep& R = *c.R;
+  GScal* S = c.v.s;
+  const int ins = S->ins;
+  Ctx cw = c;  // the trial's layout: an inserted water counts among the waters
+  cw.r.n_water = S->nw_trial;
+  cw.r.nw3 = 3 * S->nw_trial;
+  build_list(cw);
+  const int f0 = S->fly0, f1 = S->fly1, f2 = S->fly2;
+  // H_start: insertion leaves the flyer out, deletion has everyone in 3D
+  const double Us = ins ? energy64(cw, f0, f1, f2) : energy64(cw, -1, -1, -1);
+  const double Ks = kinetic64(cw);
+  if (e.proto.n_f > 0) nemd_steps<SYS>(cw, e.proto.n_f);
+  c.sync();
+  const double Ue = ins ? energy64(cw, -1, -1, -1) : energy64(cw, f0, f1, f2);
+  const double Ke = kinetic64(cw);
+  if (c.tid == 0) {
+    const double dH = (Ue + Ke) - (Us + Ks);
+    const double V = R.L * R.L * R.L;
+    double bdm, xacc;
+    if (ins) {
+      bdm = e.proto.beta * dH - log(V / (double)(N + 1));
+      xacc = -bdm + e.proto.beta_mu;
+    } else {
+      bdm = -e.proto.beta * dH - log(V / (double)N);
+      xacc = bdm - e.proto.beta_mu;
+    }
+    const int status = (isfinite(dH) && !S->flag_nan && !S->flag_overflow && !S->flag_timeout) ? 0 : 3;
+    S->flag_nan = 0;
+    S->flag_overflow = 0;
+    S->flag_timeout = 0;
+    const int acc = (status == 0) && (S->ln_u < xacc) && !e.proto.no_accept;
+    S->accept = acc;
+    h4d_record rr;
+    rr.move = ins; rr.accepted = acc; rr.n_before = N;
+    rr.n_after = N + (acc ? (ins ? 1 : -1) : 0);
+    rr.status = status;
+    rr.cation = ins ? -1 : S->flyw; rr.anion = -1;
+    rr.cell_c = -1; rr.cell_a = -1; rr.instant = 0;
+    rr.dH = dH; rr.beta_dM = bdm; rr.w_prot = S->wprot; rr.ln_u = S->ln_u; rr.x_acc = xacc; rr.ln_q = 0.0;
+    e.rec[R.rec_off + (int)(R.rec_count % R.rec_cap)] = rr;
+    R.rec_count++;
+    R.cycles++;
+    if (ins) { R.trials_ins++; R.acc_ins += acc; } else { R.trials_del++; R.acc_del += acc; }
+    if (status) R.rej_status++;
+    S->ustart = Us; S->uend = Ue; S->kstart = Ks; S->kend = Ke;
+  }
+  c.sync();
+  if (S->accept) {
+    if (ins) {
+      if (c.tid == 0) {
+        for (int k = 0; k < 3; ++k) {
+          uint4 p = c.v.pos[f0 + k];
+          p.w = 0u;  // altitude(n_f) of an insertion is 0
+          c.v.pos[f0 + k] = p;
+        }
+        R.n_water = N + 1;
+        R.nw3 = 3 * (N + 1);
+      }
+    } else {
+      const int m = S->flyw, last = N - 1;
+      if (c.tid == 0 && m != last) {  // swap-with-last
+        for (int k = 0; k < 3; ++k) {
+          c.v.pos[3 * m + k] = c.v.pos[3 * last + k];
+          e.vhi[R.atom_off + 3 * m + k] = e.vhi[R.atom_off + 3 * last + k];
+          e.vlo[R.atom_off + 3 * m + k] = e.vlo[R.atom_off + 3 * last + k];
+        }
+      }
+      // the ions move down by three atoms, staged through the (no longer needed) copy
+      for (int a = 3 * N + c.tid; a < n; a += c.T) {
+        const int ga = R.atom_off + a;
+        e.pos_save[ga] = c.v.pos[a];
+        e.vhi_save[ga] = e.vhi[ga];
+        e.vlo_save[ga] = e.vlo[ga];
+      }
+      c.sync();
+      for (int a = 3 * N + c.tid; a < n; a += c.T) {
+        const int ga = R.atom_off + a;
+        c.v.pos[a - 3] = e.pos_save[ga];
+        e.vhi[ga - 3] = e.vhi_save[ga];
+        e.vlo[ga - 3] = e.vlo_save[ga];
+      }
+      if (c.tid == 0) {
+        R.n_water = N - 1;
+        R.nw3 = 3 * (N - 1);
+      }
+    }
+  } else {
+    for (int a = c.tid; a < n; a += c.T) {
+      const int ga = R.atom_off + a;
+      c.v.pos[a] = e.pos_save[ga];
+      e.vhi[ga] = e.vhi_save[ga];
+      e.vlo[ga] = e.vlo_save[ga];
+    }
+  }
+  c.sync();
+  if (c.tid == 0) {
+    S->n_tot = R.nw3 + e.proto.unit * R.n_pairs;
+    S->fly0 = S->fly1 = S->fly2 = S->flyw = -1;
+    S->w_cur = 0.f;
+    S->g_scr = 1.f;
+    const double Nn = (double)R.n_water;
+    R.sum_n += Nn;
+    R.sum_n2 += Nn * Nn;
+  }
+  c.sync();
+  if (S->flip_e) negate_velocities(c, S->n_tot);
+  c.sync();
+}
+
+template <int SYS>
+__device__ __noinline__ void trial_water(const Ctx& c) {
+  const Eng& e = *c.e;
+  Rep& R = *c.R;
+  GScal* S = c.v.s;
+  const u64 rep_id = R.key;
+  if (c.tid == 0) {
+    const u64 t = R.trial_ctr++;
+    u64 b0[4], b1[4], b2[4], b3[4], b4[4];
+    draw4(e.seed, rep_id, t, 0, kPurTrial, b0);
+    draw4(e.seed, rep_id, t, 1, kPurTrial, b1);
+    draw4(e.seed, rep_id, t, 2, kPurTrial, b2);
+    draw4(e.seed, rep_id, t, 3, kPurTrial, b3);
+    draw4(e.seed, rep_id, t, 4, kPurTrial, b4);
+    S->ins = (int)(b0[0] >> 63);
+    S->flip_s = (int)(b0[1] >> 63);
+    S->flip_e = (int)(b0[2] >> 63);
+    S->ln_u = log(u01_open(b0[3]));
+    const int N = R.n_water;
+    S->n_before = N;
+    S->status = 0;
+    if (!S->ins && N == 0) S->status = 1;
+    if (S->ins && N >= R.cap_water) S->status = 2;
+    S->cat = -1;
+    S->ani = -1;
+    S->inst = 0;
+    if (S->status == 0) {
+      if (S->ins) water_placement(e.proto, R.L, b1, b2, b3, b4, S->xw, S->vw);
+      else S->cat = pick_index(b1[0], N);
+    }
+  }
+  c.sync();
+  const int N = S->n_before;
+  const int n_ion = e.proto.unit * R.n_pairs;
+  const int n = 3 * N + n_ion;
+  const int ins = S->ins;
+  if (S->flip_s) negate_velocities(c, n);
+  if (S->status != 0) {
+    c.sync();
+    if (S->flip_e) negate_velocities(c, n);
+    if (c.tid == 0) {
+      h4d_record rr;
+      rr.move = ins; rr.accepted = 0; rr.n_before = N; rr.n_after = N; rr.status = S->status;
+      rr.cation = -1; rr.anion = -1; rr.cell_c = -1; rr.cell_a = -1; rr.instant = 0;
+      rr.dH = 0.0; rr.beta_dM = 0.0; rr.w_prot = 0.0; rr.ln_u = S->ln_u; rr.x_acc = 0.0; rr.ln_q = 0.0;
+      e.rec[R.rec_off + (int)(R.rec_count % R.rec_cap)] = rr;
+      R.rec_count++;
+      R.cycles++;
+      if (ins) R.trials_ins++; else R.trials_del++;
+      R.rej_status++;
+      R.sum_n += (double)N;
+      R.sum_n2 += (double)N * (double)N;
+    }
+    c.sync();
+    return;
+  }
+  // save the state for a rejection (positions from shared memory, velocities)
+  for (int a = c.tid; a < n; a += c.T) {
+    const int ga = R.atom_off + a;
+    e.pos_save[ga] = c.v.pos[a];
+    e.vhi_save[ga] = e.vhi[ga];
+    e.vlo_save[ga] = e.vlo[ga];
+  }
+  c.sync();
+  if (ins) {
+    // room for the new water: every ion moves up by three atoms (read from the copy)
+    for (int a = 3 * N + c.tid; a < n; a += c.T) {
+      const int ga = R.atom_off + a;
+      c.v.pos[a + 3] = e.pos_save[ga];
+      e.vhi[ga + 3] = e.vhi_save[ga];
+      e.vlo[ga + 3] = e.vlo_save[ga];
+    }
+  }
+  const float w0 = (float)altitude(e.proto, ins, 0);
+  if (c.tid == 0) {
+    const int m = ins ? N : S->cat;
+    if (ins) {
+      for (int k = 0; k < 3; ++k) {
+        const int a = 3 * N + k, ga = R.atom_off + a;
+        c.v.pos[a] = make_uint4(S->xw[3 * k], S->xw[3 * k + 1], S->xw[3 * k + 2], __float_as_uint(w0));
+        float4 h, l;
+        h.x = (float)S->vw[3 * k]; l.x = (float)(S->vw[3 * k] - (double)h.x);
+        h.y = (float)S->vw[3 * k + 1]; l.y = (float)(S->vw[3 * k + 1] - (double)h.y);
+        h.z = (float)S->vw[3 * k + 2]; l.z = (float)(S->vw[3 * k + 2] - (double)h.z);
+        h.w = 0.f; l.w = 0.f;
+        e.vhi[ga] = h;
+        e.vlo[ga] = l;
+      }
+    }
+    S->fly0 = 3 * m;
+    S->fly1 = 3 * m + 1;
+    S->fly2 = 3 * m + 2;
+    S->flyw = m;
+    S->nw_trial = ins ? N + 1 : N;
+    S->n_tot = ins ? n + 3 : n;
+    S->w_cur = w0;
+    S->g_scr = expf(-e.pot.kappa_sr * w0);  // screening at the flyer's altitude (Sec. II.B.2)
+    S->wprot = 0.0;
+    S->wprot_c = 0.0;
+    S->dW[0] = S->dW[1] = S->dW[2] = 0.0;
+    S->flag_nan = 0;
+    S->flag_overflow = 0;
+    S->flag_timeout = 0;
+  }
+  c.sync();
+  trial_water_run<SYS>(c, N, n);
+}
+
 template <int SYS>
 __device__ void trial_phase(const Ctx& c) {
+  if (SYS == H4D_SYS_AQ && c.e->proto.water) {
+    trial_water<SYS>(c);
+    return;
+  }
   const Eng& e = *c.e;
   Rep& R = *c.R;
   GScal* S = c.v.s;
@@ -1976,7 +2262,7 @@ __device__ void trial_phase(const Ctx& c) {
     S->g_scr = expf(-e.pot.kappa_sr * (single ? w0 : 0.5f * (w0 + w0a)));
     S->wprot = 0.0;
     S->wprot_c = 0.0;
-    S->dW[0] = S->dW[1] = 0.0;
+    S->dW[0] = S->dW[1] = S->dW[2] = 0.0;
     S->flag_nan = 0;       // a blow-up inside NEMD only rejects this trial
     S->flag_overflow = 0;  // so does a neighbour row that overflowed during it
     S->flag_timeout = 0;   // and a rigid-water constraint that did not converge
@@ -2101,7 +2387,7 @@ __device__ void trial_phase(const Ctx& c) {
   c.sync();
   if (c.tid == 0) {
     S->n_tot = R.nw3 + e.proto.unit * R.n_pairs;
-    S->fly0 = S->fly1 = -1;
+    S->fly0 = S->fly1 = S->fly2 = S->flyw = -1;
     S->w_cur = 0.f;
     S->g_scr = 1.f;
     const double Nn = (double)R.n_pairs;
@@ -2140,7 +2426,7 @@ __device__ bool setup_ctx(const Eng& e, char* smem, Ctx& c) {
   if (c.tid == 0) {
     S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0; S->flag_timeout = 0;
     S->n_tot = R->nw3 + e.proto.unit * R->n_pairs;
-    S->fly0 = S->fly1 = -1;
+    S->fly0 = S->fly1 = S->fly2 = S->flyw = -1;
     S->w_cur = 0.f; S->g_scr = 1.f;
     write_sentinel(c.v, R->cap_atoms);
   }
@@ -2167,7 +2453,12 @@ __global__ void __launch_bounds__(H4D_MAXTHREADS, H4D_MINBLOCKS) cycles_kernel(c
     u64 t0 = gtimer();
     if (n_eq > 0) md_phase<SYS>(c, n_eq);
     u64 t1 = gtimer();
-    if (do_trial) trial_phase<SYS>(c);
+    if (do_trial) {
+      trial_phase<SYS>(c);
+      // a water exchange changes where the ions start (every thread saw R after the sync)
+      c.r.n_water = R->n_water;
+      c.r.nw3 = R->nw3;
+    }
     u64 t2 = gtimer();
     if (c.tid == 0) {
       R->t_md_ns += (double)(t1 - t0);
@@ -2262,7 +2553,7 @@ __global__ void __launch_bounds__(1024) eval_kernel(const __grid_constant__ Eng 
   if (c.tid == 0) {
     S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0; S->flag_timeout = 0;
     S->n_tot = R->nw3 + e.proto.unit * R->n_pairs;
-    S->fly0 = S->fly1 = -1;
+    S->fly0 = S->fly1 = S->fly2 = S->flyw = -1;
     S->w_cur = wbar;
     S->g_scr = expf(-e.pot.kappa_sr * wbar);
     write_sentinel(c.v, R->cap_atoms);

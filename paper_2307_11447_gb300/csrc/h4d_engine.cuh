@@ -50,6 +50,12 @@ struct Proto {
   double vex_edge;  // early rejection: edge of the excluded cube around the flying cation (0 = off)
   int single;       // single-particle exchange: one flyer, one atom per exchange unit
   int unit;         // atoms per exchange unit (2 for ion pairs, 1 for single particles)
+  int water;        // rigid-water exchange: one flying water per trial, frozen in 3D
+  int pad_w;
+  // the water in its body frame (O at the origin, H atoms in the xy plane symmetric about
+  // y): H offsets, centre of mass on y, total mass and principal moments about the centre
+  // of mass, both times mvv2e, for the molecular-frame velocity draw of an insertion
+  double wh[2][3], wcom_y, wM, wI[3];
 };
 
 struct Rep {
@@ -59,6 +65,7 @@ struct Rep {
   int n_water, nw3;
   int n_pairs, cap_pairs;
   int atom_off, cap_atoms;
+  int cap_water, pad_cw;  // most waters the replica may hold (water exchange)
   int nc;         // cells per dimension (0 = all pairs)
   int reach;      // stencil half-width: cells are at least r_list / reach wide
   int tpa;

@@ -74,6 +74,7 @@ class h4d_system(ctypes.Structure):
         ("host_x", ctypes.POINTER(ctypes.c_double)),
         ("host_v", ctypes.POINTER(ctypes.c_double)),
         ("replica_key", ctypes.POINTER(ctypes.c_uint64)),
+        ("cap_water", ctypes.POINTER(ctypes.c_int32)),
     ]
 
 
@@ -104,6 +105,7 @@ class h4d_counts(ctypes.Structure):
         ("t_last_end_ns", ctypes.c_double),
         ("plan_warps", ctypes.c_int64),
         ("plan_cta_groups", ctypes.c_int64),
+        ("n_water", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -170,6 +172,7 @@ def lib():
             "h4d_get_work": ([vp, i32, vp, i64, ctypes.POINTER(i64)], i32),
             "h4d_get_state": ([vp, i32, pd, pd, i64, ctypes.POINTER(i64)], i32),
             "h4d_set_state": ([vp, i32, i32, pd, pd], i32),
+            "h4d_set_water_state": ([vp, i32, i32, i32, pd, pd], i32),
             "h4d_num_replicas": ([vp], i32),
             "h4d_device_info": ([pi32, pi32, pi32], i32),
             "h4d_measure_fp32_peak": ([pd, pd], i32),
@@ -242,14 +245,15 @@ def make_params(cfg: dict, **override) -> h4d_params:
     p.skin_outer = c.get("skin_outer", 0.0)
     p.max_nbr = c.get("max_nbr", 0)
     p.threads_per_atom = c.get("threads_per_atom", 0)
-    p.exchange = 1 if c.get("exchange", "pair") == "single" else 0
+    p.exchange = {"pair": 0, "single": 1, "water": 2}[c.get("exchange", "pair")]
     return p
 
 
 class Context:
     """Owns an h4d_ctx.  Replicas: list of dicts with keys L, n_pairs, cap_pairs, x, v
-    (optional), n_water (optional), key (optional: the replica's random-stream key, by
-    default its index)."""
+    (optional), n_water (optional), cap_water (optional, water exchange: the most waters
+    the replica may hold), key (optional: the replica's random-stream key, by default its
+    index)."""
 
     def __init__(self, params: h4d_params, replicas: list, seed: int, stream: int | None = None):
         R = len(replicas)
@@ -258,6 +262,7 @@ class Context:
         nw = np.array([r.get("n_water", 0) for r in replicas], np.int32)
         npair = np.array([r["n_pairs"] for r in replicas], np.int32)
         cap = np.array([r["cap_pairs"] for r in replicas], np.int32)
+        capw = np.array([r.get("cap_water", r.get("n_water", 0)) for r in replicas], np.int32)
         xs = np.ascontiguousarray(np.concatenate([np.asarray(r["x"], np.float64).reshape(-1, 3) for r in replicas]))
         have_v = all(r.get("v") is not None for r in replicas)
         vs = np.ascontiguousarray(np.concatenate([np.asarray(r["v"], np.float64).reshape(-1, 3) for r in replicas])) if have_v else None
@@ -272,12 +277,13 @@ class Context:
         have_key = all(r.get("key") is not None for r in replicas)
         keys = np.array([int(r["key"]) for r in replicas], np.uint64) if have_key else None
         s.replica_key = keys.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) if have_key else None
+        s.cap_water = capw.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         h = ctypes.c_void_p()
         _ck(lib().h4d_create(ctypes.byref(params), ctypes.byref(s), seed, ctypes.c_void_p(stream or 0), ctypes.byref(h)), "h4d_create")
         self.h = h
         self.R = R
         unit = 1 if params.exchange == 1 else 2  # atoms per exchange unit
-        self.cap_atoms = [3 * int(nw[i]) + unit * int(cap[i]) for i in range(R)]
+        self.cap_atoms = [3 * int(capw[i]) + unit * int(cap[i]) for i in range(R)]
 
     def close(self):
         if self.h:
@@ -343,6 +349,11 @@ class Context:
         x = np.ascontiguousarray(x, np.float64)
         v = None if v is None else np.ascontiguousarray(v, np.float64)
         _ck(lib().h4d_set_state(self.h, r, n_pairs, _pd(x), _pd(v)), "h4d_set_state")
+
+    def h4d_set_water_state(self, r, n_water, n_pairs, x, v):
+        x = np.ascontiguousarray(x, np.float64)
+        v = None if v is None else np.ascontiguousarray(v, np.float64)
+        _ck(lib().h4d_set_water_state(self.h, r, n_water, n_pairs, _pd(x), _pd(v)), "h4d_set_water_state")
 
     def h4d_autotune(self, n_iter=20):
         """Returns {tpa: (mean ns per force pass, mean ns per build)} per candidate."""

@@ -54,4 +54,4 @@ def test_structure_sizes_match_header_layout():
     import ctypes
     # h4d_record: 10 int32 + 6 double
     assert h4d.RECORD_DTYPE.itemsize == 88
-    assert ctypes.sizeof(h4d.h4d_counts) == 8 * 25
+    assert ctypes.sizeof(h4d.h4d_counts) == 8 * 26

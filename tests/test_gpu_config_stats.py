@@ -10,8 +10,10 @@ both sides; the z-scores are printed):
   the batched replicas): <N>, chi_osmotic = Var(N)/<N> of the pooled N series (Eq. 1 at
   fixed V), the fraction of trials accepted (Eqs. 6, 8), and the acceptance estimated from
   the same trials' work (Eq. 21);
-* fixed-N runs (aqueous NaCl, where no exchange is accepted at N_f = 1000): the Eq. 21
-  acceptance and the mean beta Delta M of insertions and of deletions (Sec. II.E).
+* fixed-N runs (aqueous NaCl, where exchanges are rare at N_f = 1000): the mean beta
+  Delta M of insertions and of deletions (Sec. II.E) and the Eq. 21 acceptance at the
+  configuration's working beta mu (at -60 it is carried by insertions, whose exponent is
+  far above zero; the two works never overlap, so no beta mu accepts both directions).
 
 The chains of both sides are exact samples of the same Markov process, so each z-score
 is a standard normal draw when the two implementations agree; the seeds are fixed, so a
@@ -153,8 +155,7 @@ def test_config_stats_nacl_aq():
         return an.eq21_acceptance([c["sums"] for c in g])
 
     stats = {"mean beta dM ins": lambda g: an.mean_work([c["sums"] for c in g], True),
-             "mean beta dM del": lambda g: an.mean_work([c["sums"] for c in g], False)}
+             "mean beta dM del": lambda g: an.mean_work([c["sums"] for c in g], False),
+             "acceptance (Eq. 21)": eq21}
     worst, gpu_chains, orc_chains = _compare("nacl_aq", stats)
-    # no overlap of the work distributions at N_f = 1000: both acceptance estimates vanish
-    assert eq21(gpu_chains)[0] < 1e-8 and eq21(orc_chains)[0] < 1e-8
     assert worst < Z_MAX
