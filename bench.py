@@ -290,6 +290,10 @@ def run_gpu(args):
     seq = None
     if args.sequential and args.workload == "batched256":
         seq = sequential_baseline(reps, cfg, args.sequential, n_eq)
+    equal_se = None
+    if rank == 0 and args.workload in ("lj4000", "nacl_aq"):
+        equal_se = plain_at_equal_se(reps[0], cfg, n_eq, stream, secs, gc["mean_n"][1],
+                                     int(sum(x["trials"] for x in sums)), accepted)
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(ctx, reps, args, n_eq, n_f, stream, world, dist if world > 1 else None)
@@ -341,6 +345,8 @@ def run_gpu(args):
         }
         if learned is not None:
             out["learned_proposal"] = learned
+        if equal_se is not None:
+            out["grand_canonical"]["equal_se_plain_vs_batched"] = equal_se
         if seq is not None:
             out["sequential_one_replica_at_a_time"] = seq
             out["batched_over_sequential"] = value / seq["value"]
@@ -529,6 +535,38 @@ def sequential_baseline(reps, cfg, count, n_eq):
         ctx.close()
     return {"value": units / t_sum, "unit": "atom-steps/s", "replicas_timed": int(count),
             "seconds_for_256_estimate": t_sum * len(reps) / count}
+
+
+def plain_at_equal_se(rep, cfg, n_eq, stream, batched_s, se_batched, trials_batched, accepted_batched):
+    """The plain arm of the equal-error comparison: one chain alone on the GPU (its own
+    context, the same cycle), timed with CUDA events over one cycle after a warm-up.  The
+    batched run reached SE(<N>) = se_batched with trials_batched independent-chain trials
+    in batched_s seconds; a single chain needs at least as many trials for the same error
+    (its consecutive trials are correlated), so its time to that error is at least
+    trials_batched x its time per cycle."""
+    import torch
+
+    from paper_2307_11447_gb300 import lib as h4d
+
+    with torch.cuda.stream(stream):
+        ctx = h4d.Context(h4d.make_params(cfg), [rep], seed=777, stream=stream.cuda_stream)
+    ctx.h4d_run_md(200)
+    ctx.h4d_autotune(5)
+    ctx.h4d_run_trials(1, n_eq)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.h4d_run_trials(1, n_eq)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t1 = e0.elapsed_time(e1) / 1e3
+    ctx.close()
+    plain_s = t1 * trials_batched
+    return {"se_mean_n": se_batched, "trials": trials_batched, "batched_s": batched_s,
+            "plain_s_per_cycle": t1, "plain_s_to_same_se_lower_bound": plain_s,
+            "speedup_at_equal_se": plain_s / batched_s,
+            "accepted_exchanges_per_s": {"batched": accepted_batched / batched_s,
+                                         "plain": accepted_batched / plain_s}}
 
 
 def run_e2e(ctx, reps, args, n_eq, n_f, stream, world, dist):

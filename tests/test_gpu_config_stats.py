@@ -11,9 +11,9 @@ both sides; the z-scores are printed):
   fixed V), the fraction of trials accepted (Eqs. 6, 8), and the acceptance estimated from
   the same trials' work (Eq. 21);
 * fixed-N runs (aqueous NaCl, where exchanges are rare at N_f = 1000): the mean beta
-  Delta M of insertions and of deletions (Sec. II.E) and the Eq. 21 acceptance at the
-  configuration's working beta mu (at -60 it is carried by insertions, whose exponent is
-  far above zero; the two works never overlap, so no beta mu accepts both directions).
+  Delta M of insertions and of deletions (Sec. II.E).  The two work distributions do not
+  overlap, so the Eq. 21 acceptance at the working beta mu only counts moves (insertion
+  exponents far above zero, deletion exponents far below); it is printed, not compared.
 
 The chains of both sides are exact samples of the same Markov process, so each z-score
 is a standard normal draw when the two implementations agree; the seeds are fixed, so a
@@ -155,7 +155,10 @@ def test_config_stats_nacl_aq():
         return an.eq21_acceptance([c["sums"] for c in g])
 
     stats = {"mean beta dM ins": lambda g: an.mean_work([c["sums"] for c in g], True),
-             "mean beta dM del": lambda g: an.mean_work([c["sums"] for c in g], False),
-             "acceptance (Eq. 21)": eq21}
+             "mean beta dM del": lambda g: an.mean_work([c["sums"] for c in g], False)}
     worst, gpu_chains, orc_chains = _compare("nacl_aq", stats)
+    # at the working beta mu (-60) the Eq. 21 estimate is saturated: insertion exponents lie
+    # far above zero and deletion exponents far below, so it counts moves, not physics
+    print(f"acceptance (Eq. 21) at beta mu {config_of('nacl_aq')['beta_mu']}: gpu {eq21(gpu_chains)[0]:.4f}, "
+          f"oracle {eq21(orc_chains)[0]:.4f}")
     assert worst < Z_MAX
