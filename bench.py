@@ -93,7 +93,9 @@ def workload(name, chains, rank):
         if ARGS.n_f is not None:
             cfg["n_f"] = ARGS.n_f
         return cfg, reps
-    cfg = dict(wl.CONFIGS["nacl_aq" if name == "nacl_learned" else name])
+    cfg = dict(wl.CONFIGS["nacl_aq" if name in ("nacl_learned", "nacl_water") else name])
+    if name == "nacl_water":
+        cfg["exchange"] = "water"  # one rigid water per trial; the NaCl pairs stay
     if ARGS.skin is not None:
         cfg["skin"] = ARGS.skin
     if ARGS.skin_outer is not None:
@@ -102,12 +104,13 @@ def workload(name, chains, rank):
         cfg["n_eq"] = ARGS.n_eq
     if ARGS.n_f is not None:
         cfg["n_f"] = ARGS.n_f
-    if name in ("nacl_aq", "nacl_learned"):
+    if name in ("nacl_aq", "nacl_learned", "nacl_water"):
         reps = []
         for c in range(chains):
             x = wl.aqueous_positions(cfg["n_water"], cfg["n_pairs"], cfg["L"], 2000 * (rank + 1) + c)
             reps.append(dict(L=cfg["L"], n_pairs=cfg["n_pairs"], cap_pairs=cfg["cap_pairs"], x=x,
-                             n_water=cfg["n_water"]))
+                             n_water=cfg["n_water"],
+                             cap_water=cfg["n_water"] + (32 if name == "nacl_water" else 0)))
         return cfg, reps
     reps = []
     for c in range(chains):
@@ -124,6 +127,16 @@ def src_hash():
     for f in ("h4d_engine.cu", "h4d_engine.cuh"):
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
+
+
+def default_launch(args, cfg):
+    """True for the launch the committed traffic figure was scaled to: the 4000-ion
+    workload with its own chain count, protocol and skins"""
+    from paper_2307_11447_gb300 import workloads as wl
+
+    ref = wl.CONFIGS["lj4000"]
+    return (args.workload == "lj4000" and args.chains == ref["chains"] and cfg["n_eq"] == ref["n_eq"]
+            and cfg["n_f"] == ref["n_f"] and args.skin is None and args.skin_outer is None)
 
 
 def traffic_from_profile():
@@ -203,6 +216,9 @@ def run_gpu(args):
     learned = None
     if args.workload == "nacl_learned":
         learned = learned_setup(ctx, cfg, args, stream)
+    water_cal = None
+    if args.workload == "nacl_water":
+        water_cal = water_calibration(ctx, cfg, args)
     tune = ctx.h4d_autotune(args.tune_iters)
     tpa_hist = {}
     for r in range(ctx.R):
@@ -238,8 +254,11 @@ def run_gpu(args):
     nemd_atom_steps = 0.0
     accepted = 0
     for r, (a, b) in enumerate(zip(c0, c1)):
-        mean_pairs = (b["sum_n"] - a["sum_n"]) / max(b["cycles"] - a["cycles"], 1)
-        n_atoms = 2.0 * mean_pairs + 3.0 * reps[r].get("n_water", 0)
+        mean_n = (b["sum_n"] - a["sum_n"]) / max(b["cycles"] - a["cycles"], 1)  # exchanged units
+        if args.workload == "nacl_water":  # the waters vary, the ion pairs stay
+            n_atoms = 3.0 * mean_n + 2.0 * reps[r]["n_pairs"]
+        else:
+            n_atoms = 2.0 * mean_n + 3.0 * reps[r].get("n_water", 0)
         atom_steps += n_atoms * (n_eq + n_f) * args.steps
         nemd_atom_steps += n_atoms * n_f * args.steps
         accepted += (b["accepted_ins"] + b["accepted_del"]) - (a["accepted_ins"] + a["accepted_del"])
@@ -329,7 +348,9 @@ def run_gpu(args):
             "gpu_launches": args.steps,
             "clocks": clk,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": traffic_from_profile(),
+                         "frac": achieved / peak,
+                         # the ncu figure belongs to the default workload's launch (and source)
+                         "traffic": traffic_from_profile() if default_launch(args, cfg) else None,
                          "kernel": "cycles_kernel (persistent: list build, 4D pair forces, VV, FP64 work, Metropolis)",
                          "peak_basis": f"measured FP32 FMA-chain throughput on this GPU ({sm_count} SMs); "
                                        f"nominal {sm_count} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz = "
@@ -345,6 +366,8 @@ def run_gpu(args):
         }
         if learned is not None:
             out["learned_proposal"] = learned
+        if water_cal is not None:
+            out["water_exchange_calibration"] = water_cal
         if equal_se is not None:
             out["grand_canonical"]["equal_se_plain_vs_batched"] = equal_se
         if seq is not None:
@@ -365,6 +388,12 @@ def workload_config(args, cfg, reps, n_f, n_eq, world):
                             f"{args.cell_len} A proposal cells", "chains_per_gpu": len(reps),
                 "n_f": n_f, "n_eq": n_eq, "parallelism": f"replicas x{world}",
                 "l2": "state > L2; no flush needed"}
+    if args.workload == "nacl_water":
+        return {"workload": f"water exchange in aqueous NaCl: {cfg['n_water']} rigid waters (capacity +32) + "
+                            f"{cfg['n_pairs']} NaCl, L={cfg['L']} A, N_f={n_f}, N_eq={n_eq}, {len(reps)} chains/GPU, "
+                            f"beta mu of the water by BAR", "chains_per_gpu": len(reps),
+                "n_f": n_f, "n_eq": n_eq, "parallelism": f"replicas x{world}",
+                "l2": "state > L2; no flush needed"}
     if args.workload == "nacl_aq":
         return {"workload": f"aqueous NaCl: {cfg['n_water']} rigid waters + {cfg['n_pairs']} NaCl, L={cfg['L']} A, "
                             f"N_f={n_f}, N_eq={n_eq}, {len(reps)} chains/GPU", "chains_per_gpu": len(reps),
@@ -376,10 +405,16 @@ def workload_config(args, cfg, reps, n_f, n_eq, world):
                             f"rho 0.1-0.4, N_f={n_f}, N_eq={n_eq}", "replicas_per_gpu": len(reps),
                 "n_f": n_f, "n_eq": n_eq, "parallelism": f"replicas x{world}",
                 "l2": "state smaller than L2 after warm-up; every step re-reads it (persistent launch)"}
-    return {"workload": f"LJ electrolyte 4000 ions rho=0.3 (L={cfg['L']:.3f}), N_f={n_f}, N_eq={n_eq}, "
+    rho = cfg["n_ions"] / cfg["L"] ** 3
+    # per atom: position, velocity pair, force, two reference positions, save copies, and
+    # the Verlet and outer rows
+    state_gb = args.chains * cfg["n_ions"] * 1.0e-9 * (16 * 6 + 2 * 256)
+    l2 = (f"state > L2 (about {state_gb:.1f} GB per GPU); no flush needed" if state_gb > 0.129 else
+          f"state about {state_gb * 1e3:.0f} MB per GPU, inside L2 after warm-up; every step re-reads it "
+          f"(persistent launch)")
+    return {"workload": f"LJ electrolyte {cfg['n_ions']} ions rho={rho:.1f} (L={cfg['L']:.3f}), N_f={n_f}, N_eq={n_eq}, "
                         f"{args.chains} chains/GPU", "chains_per_gpu": args.chains, "ions": cfg["n_ions"],
-            "n_f": n_f, "n_eq": n_eq, "parallelism": f"replicas x{world}",
-            "l2": "state > L2 (about 1.3 GB per GPU); no flush needed"}
+            "n_f": n_f, "n_eq": n_eq, "parallelism": f"replicas x{world}", "l2": l2}
 
 
 # ---------------------------------------------------------------------------------------
@@ -537,6 +572,32 @@ def sequential_baseline(reps, cfg, count, n_eq):
             "seconds_for_256_estimate": t_sum * len(reps) / count}
 
 
+def water_calibration(ctx, cfg, args):
+    """Untimed: beta mu of the rigid water by BAR (SI Eq. S2) on fixed-N water trials of
+    every chain at the configuration's protocol, then set for the timed cycles."""
+    from paper_2307_11447_gb300 import analysis as an
+
+    ctx.h4d_set_no_accept(1)
+    ins, dele = [], []
+    ctx.h4d_run_trials(args.calib_cycles, 100)
+    for r in range(ctx.R):
+        w = ctx.h4d_get_work(r, args.calib_cycles)
+        ok = w["status"] == 0
+        ins.append(w["beta_dM"][ok & (w["move"] == 1)])
+        dele.append(w["beta_dM"][ok & (w["move"] == 0)])
+    groups = list(zip(ins, dele))
+    mu, se = an.jackknife(groups, lambda g: an.bar_mu(np.concatenate([a for a, _ in g]),
+                                                      np.concatenate([b for _, b in g])))
+    a, b = np.concatenate(ins), np.concatenate(dele)
+    acc = 0.5 * (an.p_acc(a, mu, True) + an.p_acc(b, mu, False))
+    ctx.h4d_set_no_accept(0)
+    ctx.h4d_set_mu(mu)
+    cfg["beta_mu"] = mu
+    return {"beta_mu_bar": mu, "beta_mu_se": se, "fixed_n_trials": int(a.size + b.size),
+            "mean_beta_dM_ins": float(a.mean()), "mean_beta_dM_del": float(b.mean()),
+            "acceptance_eq21_at_bar_mu": float(acc), "cycles": args.calib_cycles, "n_eq": 100}
+
+
 def plain_at_equal_se(rep, cfg, n_eq, stream, batched_s, se_batched, trials_batched, accepted_batched):
     """The plain arm of the equal-error comparison: one chain alone on the GPU (its own
     context, the same cycle), timed with CUDA events over one cycle after a warm-up.  The
@@ -579,9 +640,11 @@ def run_e2e(ctx, reps, args, n_eq, n_f, stream, world, dist):
 
     from paper_2307_11447_gb300.lib import h4d_counts as h4d_counts_t
 
-    xs, vs = [], []
+    xs, vs, counts = [], [], []
     for r in range(ctx.R):
         x, v = ctx.h4d_get_state(r)
+        c = ctx.h4d_get_counts(r)
+        counts.append((int(c["n_water"]), int(c["n_pairs"])))  # the layout of the snapshot
         xs.append(torch.from_numpy(x).pin_memory())
         vs.append(torch.from_numpy(v).pin_memory())
     torch.cuda.synchronize()
@@ -591,16 +654,14 @@ def run_e2e(ctx, reps, args, n_eq, n_f, stream, world, dist):
     atom_steps = 0.0
     for k in range(args.steps):
         for r in range(ctx.R):
-            x = xs[r].numpy()
-            nw = reps[r].get("n_water", 0)
-            ctx.h4d_set_state(r, (x.shape[0] - 3 * nw) // 2, x, vs[r].numpy())
+            ctx.h4d_set_water_state(r, counts[r][0], counts[r][1], xs[r].numpy(), vs[r].numpy())
         ctx.h4d_run_trials(1, n_eq)
         d2h = 0
         for r in range(ctx.R):
             c = ctx.h4d_get_counts(r)
             rec = ctx.h4d_get_work(r, 1)
             d2h += ctypes.sizeof(h4d_counts_t) + rec.nbytes
-            atom_steps += (2.0 * c["n_pairs"] + 3.0 * reps[r].get("n_water", 0)) * (n_eq + n_f)
+            atom_steps += (2.0 * c["n_pairs"] + 3.0 * c["n_water"]) * (n_eq + n_f)
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
     secs, tot = reduce_over_ranks(secs, [atom_steps], dist)
@@ -618,7 +679,13 @@ def _oracle_chain(job):
     from oracle import oracle as orc
     from paper_2307_11447_gb300 import workloads as wl
 
-    cfg = dict(wl.CONFIGS["nacl_aq" if name == "nacl_learned" else name])
+    if name == "batched256":
+        # one replica of the batched workload (sizes 100-1000 ions, rho 0.1-0.4) per process
+        cfg, reps = wl.batched_system(256, seed=7)
+        rep = reps[(seed * 37) % len(reps)]
+        cfg = dict(cfg, L=rep["L"], n_pairs=rep["n_pairs"], cap_pairs=rep["cap_pairs"])
+    else:
+        cfg = dict(wl.CONFIGS["nacl_aq" if name in ("nacl_learned", "nacl_water") else name])
     p = orc.make_params(cfg, use_cells=1, seed=seed)
     if cfg.get("n_water", 0):
         x = wl.aqueous_positions(cfg["n_water"], cfg["n_pairs"], cfg["L"], seed)
@@ -646,7 +713,9 @@ def cpu_baseline(name, sample_steps=8, cores=None, one_core=True):
     wall = time.perf_counter() - t0
     units = sum(r[0] for r in res)
     busy = max(r[1] for r in res)
-    system = "aqueous NaCl system" if name in ("nacl_aq", "nacl_learned") else "4000-ion system"
+    system = {"nacl_aq": "aqueous NaCl system", "nacl_learned": "aqueous NaCl system",
+              "nacl_water": "aqueous NaCl system", "batched256": "batched workload (one replica each)",
+              "lj250": "250-ion system"}.get(name, "4000-ion system")
     out = {"value": units / busy, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
            "sample": f"{cores} chains x {sample_steps} MD steps of the {system}, cell list, FP64 "
                      f"(wall {wall:.1f} s incl. process start)"}
@@ -711,7 +780,7 @@ def main():
     global ARGS
     args = parse()
     if args.chains is None:
-        args.chains = 152 if args.workload in ("nacl_aq", "nacl_learned") else 304
+        args.chains = 152 if args.workload in ("nacl_aq", "nacl_learned", "nacl_water") else 304
     ARGS = args
     if args.impl == "reference":
         run_reference(args)
