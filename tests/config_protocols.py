@@ -29,8 +29,10 @@ STATS = {
     # eight replicas of the batched workload spanning its size range, several chains each
     "batched_subset": dict(kind="gc", replicas=(0, 37, 74, 111, 148, 185, 222, 255), chains_oracle=4, chains_gpu=16,
                            equil=500, trials=40, n_eq=100, burn=0, seed_oracle=24000, seed_gpu=34000),
+    # fixed N: the works do not depend on beta mu; the run (and the BAR estimate of the
+    # configuration's beta mu drawn from it) took the exponents at -60
     "nacl_aq": dict(kind="fixed_n", chains_oracle=8, chains_gpu=152, equil=200, trials=3, n_eq=100, burn=0,
-                    seed_oracle=25000, seed_gpu=35000),
+                    seed_oracle=25000, seed_gpu=35000, beta_mu=-60.0),
 }
 
 
@@ -40,7 +42,10 @@ def config_of(name: str) -> dict:
     if name == "batched_subset":
         cfg, _ = wl.batched_system(256, seed=7)
         return dict(cfg)
-    return dict(wl.CONFIGS[name])
+    cfg = dict(wl.CONFIGS[name])
+    if "beta_mu" in STATS.get(name, {}):
+        cfg["beta_mu"] = STATS[name]["beta_mu"]
+    return cfg
 
 
 def chain_inputs(name: str, k: int, seed: int) -> dict:
