@@ -136,12 +136,12 @@ def default_launch(args, cfg):
 
     ref = wl.CONFIGS["lj4000"]
     return (args.workload == "lj4000" and args.chains == ref["chains"] and cfg["n_eq"] == ref["n_eq"]
-            and cfg["n_f"] == ref["n_f"] and args.skin is None and args.skin_outer is None)
+            and cfg["n_f"] == ref["n_f"] and cfg["skin"] == ref["skin"] and cfg["skin_outer"] == ref["skin_outer"])
 
 
-def traffic_from_profile():
+def traffic_from_profile(cfg):
     """DRAM bytes per launch of the engine kernel from the committed ncu summary, or None
-    when the kernel source changed since it was captured."""
+    when the kernel source or the list skins changed since it was captured."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -149,7 +149,7 @@ def traffic_from_profile():
         t = json.load(open(p))
     except Exception:
         return None
-    if t.get("src_sha") != src_hash():
+    if t.get("src_sha") != src_hash() or t.get("skins") != [cfg["skin"], cfg["skin_outer"]]:
         return None
     return t.get("dram_bytes_per_launch")
 
@@ -350,7 +350,7 @@ def run_gpu(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
                          # the ncu figure belongs to the default workload's launch (and source)
-                         "traffic": traffic_from_profile() if default_launch(args, cfg) else None,
+                         "traffic": traffic_from_profile(cfg) if default_launch(args, cfg) else None,
                          "kernel": "cycles_kernel (persistent: list build, 4D pair forces, VV, FP64 work, Metropolis)",
                          "peak_basis": f"measured FP32 FMA-chain throughput on this GPU ({sm_count} SMs); "
                                        f"nominal {sm_count} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz = "
@@ -370,6 +370,7 @@ def run_gpu(args):
             out["water_exchange_calibration"] = water_cal
         if equal_se is not None:
             out["grand_canonical"]["equal_se_plain_vs_batched"] = equal_se
+        out["long_range_coulomb"] = ewald_timing()
         if seq is not None:
             out["sequential_one_replica_at_a_time"] = seq
             out["batched_over_sequential"] = value / seq["value"]
@@ -596,6 +597,26 @@ def water_calibration(ctx, cfg, args):
     return {"beta_mu_bar": mu, "beta_mu_se": se, "fixed_n_trials": int(a.size + b.size),
             "mean_beta_dM_ins": float(a.mean()), "mean_beta_dM_del": float(b.mean()),
             "acceptance_eq21_at_bar_mu": float(acc), "cycles": args.calib_cycles, "n_eq": 100}
+
+
+def ewald_timing(kmax=14, alpha=0.25):
+    """The long-range Coulomb term (Eqs. 9-10, reciprocal-space Ewald sum with forces) of
+    one configuration of the aqueous NaCl system (9110 atoms, L = 45 A), evaluated once to
+    warm up and once timed: the two kernels' device time from CUDA events inside the call.
+    A term is one (k-vector, atom) phase, its sine and cosine and their accumulation; each
+    kernel evaluates every term of the half space of k-vectors once."""
+    from paper_2307_11447_gb300 import lib as h4d
+    from paper_2307_11447_gb300 import workloads as wl
+
+    cfg = dict(wl.CONFIGS["nacl_aq"])
+    x = wl.aqueous_positions(cfg["n_water"], cfg["n_pairs"], cfg["L"], 5)
+    p = h4d.make_params(cfg)
+    h4d.h4d_ewald_lr(p, cfg["L"], x, alpha, kmax, n_water=cfg["n_water"])
+    ur, us, _, ms = h4d.h4d_ewald_lr(p, cfg["L"], x, alpha, kmax, n_water=cfg["n_water"], kernel_ms=True)
+    n_k = ((2 * kmax + 1) ** 3 - 1) // 2  # half space of 0 < max_d |n_d| <= kmax
+    n = len(x)
+    return {"atoms": n, "kmax": kmax, "alpha_per_A": alpha, "k_vectors_half_space": n_k, "kernel_ms": ms,
+            "terms_per_s": 2.0 * n_k * n / (ms * 1e-3), "U_recip_kJ_mol": ur, "U_self_kJ_mol": us}
 
 
 def plain_at_equal_se(rep, cfg, n_eq, stream, batched_s, se_batched, trials_batched, accepted_batched):

@@ -17,7 +17,11 @@
  *   - the FP64 nonequilibrium work Delta M and the pair-exchange Metropolis rule of
  *     Eqs. 3-8 with symmetric two-end momentum reversal (Sec. II.A), committed on the
  *     device with no host round trip;
- *   - equilibrium MD between trials (Fig. 1) with a CSVR thermostat.
+ *   - equilibrium MD between trials (Fig. 1) with a CSVR thermostat;
+ *   - the same rule with one flyer (Sec. II.A): single particles of a neutral species, or
+ *     one rigid water frozen in 3D with molecular-frame velocities (Sec. II.C);
+ *   - the long-range Coulomb part of one configuration as a reciprocal-space Ewald sum
+ *     scaled by exp(-kappa_lr wbar) (Eqs. 9-10), as an evaluation entry point.
  *
  * Conventions shared by every entry point:
  *   - Return value: H4D_OK (0) on success, a negative H4D_E* code on error; no C++
@@ -397,11 +401,13 @@ int h4d_eval_forces_static(const h4d_params* params, double L, int32_t n_water, 
  * Charges follow the atom layout of h4d_eval_forces (params->q by type, K = params->kcoul);
  * host_x [n][3] in [0, L) (wrapped otherwise).  Intramolecular exclusion corrections of
  * rigid waters are not included (they do not depend on the positions of other molecules).
+ * t_kernel_ms (may be NULL) receives the device time of the two kernels (structure factors,
+ * forces), from CUDA events recorded around each launch.
  * H4D_EINVAL for alpha <= 0, kmax outside 1..64, negative wbar or kappa_lr.  Allocates
  * device scratch per call; runs on the legacy default stream and synchronises it. */
 int h4d_ewald_lr(const h4d_params* params, double L, int32_t n_water, int32_t n, const double* host_x,
                  double alpha, int32_t kmax, double wbar, double kappa_lr, double* U_recip,
-                 double* U_self, double* host_F);
+                 double* U_self, double* host_F, double* t_kernel_ms);
 
 /* Neighbour pairs (i < j) under the fixed-point criterion: X = round(x/L 2^32) mod 2^32
  * per coordinate, pair iff sum ((int32)(X_i - X_j))^2 <= floor((r_list/L 2^32)^2).

@@ -113,7 +113,7 @@ int type_of_host(int a, int nw3) { return a < nw3 ? ((a % 3 == 0) ? 2 : 3) : ((a
 
 extern "C" int h4d_ewald_lr(const h4d_params* params, double L, int32_t n_water, int32_t n, const double* x,
                             double alpha, int32_t kmax, double wbar, double kappa_lr, double* U_recip,
-                            double* U_self, double* F) {
+                            double* U_self, double* F, double* t_kernel_ms) {
   if (!params || !x || n < 0 || n_water < 0 || 3 * n_water > n || !(L > 0) || !(alpha > 0) || kmax < 1 ||
       kmax > 64 || !(wbar >= 0) || !(kappa_lr >= 0))
     return H4D_EINVAL;
@@ -160,18 +160,24 @@ extern "C" int h4d_ewald_lr(const h4d_params* params, double L, int32_t n_water,
   std::vector<double2> sk(nk);
   std::vector<KW> kw(nk);
   double u = 0.0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  float ms_sk = 0.f, ms_f = 0.f;
+  if (t_kernel_ms) *t_kernel_ms = 0.0;
   if (n == 0) {
     if (U_recip) *U_recip = 0.0;
     if (U_self) *U_self = 0.0;
     return H4D_OK;
   }
+  for (auto& x_ev : ev) CKE(cudaEventCreate(&x_ev));
   CKE(cudaMalloc(&d_xq, sizeof(uint4) * n));
   CKE(cudaMalloc(&d_kv, sizeof(KVec) * nk));
   CKE(cudaMalloc(&d_sk, sizeof(double2) * nk));
   CKE(cudaMemcpy(d_xq, xq.data(), sizeof(uint4) * n, cudaMemcpyHostToDevice));
   CKE(cudaMemcpy(d_kv, kv.data(), sizeof(KVec) * nk, cudaMemcpyHostToDevice));
+  CKE(cudaEventRecord(ev[0]));
   ewald_sk_kernel<<<(nk + 255) / 256, 256>>>(d_xq, n, d_kv, nk, d_sk);
   CKE(cudaGetLastError());
+  CKE(cudaEventRecord(ev[1]));
   CKE(cudaMemcpy(sk.data(), d_sk, sizeof(double2) * nk, cudaMemcpyDeviceToHost));
   // U_recip = (2 pi K / V) sum_{all k != 0} A_k |S_k|^2 = (4 pi K / V) sum_half A_k |S_k|^2
   for (int k = 0; k < nk; ++k) {
@@ -185,12 +191,19 @@ extern "C" int h4d_ewald_lr(const h4d_params* params, double L, int32_t n_water,
     CKE(cudaMalloc(&d_F, sizeof(double) * 3 * n));
     CKE(cudaMemcpy(d_kw, kw.data(), sizeof(KW) * nk, cudaMemcpyHostToDevice));
     // F_j = g (4 pi K q_j / V) sum_{all k} A_k k [Re S sin - Im S cos]: twice the half space
+    CKE(cudaEventRecord(ev[2]));
     ewald_force_kernel<<<(n + 255) / 256, 256>>>(d_xq, n, d_kw, nk, (float)(2.0 * M_PI / L), g * 8.0 * M_PI * K / V,
                                                  d_F);
     CKE(cudaGetLastError());
+    CKE(cudaEventRecord(ev[3]));
     CKE(cudaMemcpy(F, d_F, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+    CKE(cudaEventElapsedTime(&ms_f, ev[2], ev[3]));
   }
+  CKE(cudaEventElapsedTime(&ms_sk, ev[0], ev[1]));
+  if (t_kernel_ms) *t_kernel_ms = (double)ms_sk + (double)ms_f;
 done:
+  for (auto& x_ev : ev)
+    if (x_ev) cudaEventDestroy(x_ev);
   cudaFree(d_xq);
   cudaFree(d_kv);
   cudaFree(d_sk);

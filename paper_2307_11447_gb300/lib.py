@@ -183,7 +183,7 @@ def lib():
             "h4d_eval_forces": ([ctypes.POINTER(h4d_params), d, i32, i32, pd, pd, pd, pd], i32),
             "h4d_eval_forces_static": ([ctypes.POINTER(h4d_params), d, i32, i32, pd, pd, pd, pd], i32),
             "h4d_neighbor_pairs": ([d, i32, pd, d, pi32, pi32, i64, ctypes.POINTER(i64)], i32),
-            "h4d_ewald_lr": ([ctypes.POINTER(h4d_params), d, i32, i32, pd, d, i32, d, d, pd, pd, pd], i32),
+            "h4d_ewald_lr": ([ctypes.POINTER(h4d_params), d, i32, i32, pd, d, i32, d, d, pd, pd, pd, pd], i32),
             "h4d_proposal": ([vp, i32, d, d, i32], i32),
             "h4d_proposal_set_weights": ([vp, pd, i64], i32),
             "h4d_proposal_get_weights": ([vp, pd, i64], i32),
@@ -484,12 +484,13 @@ def h4d_measure_fp32_peak():
 
 
 def h4d_ewald_lr(params: h4d_params, L: float, x, alpha: float, kmax: int, wbar: float = 0.0,
-                 kappa_lr: float = 0.0, n_water: int = 0, forces: bool = True):
-    """(U_recip, U_self, F_recip or None) of the long-range Coulomb term (Eqs. 9-10)"""
+                 kappa_lr: float = 0.0, n_water: int = 0, forces: bool = True, kernel_ms: bool = False):
+    """(U_recip, U_self, F_recip or None) of the long-range Coulomb term (Eqs. 9-10), plus
+    the kernels' device time in ms when kernel_ms"""
     x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
     n = x.shape[0]
-    ur, us = ctypes.c_double(), ctypes.c_double()
+    ur, us, tk = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     F = np.zeros((n, 3)) if forces else None
     _ck(lib().h4d_ewald_lr(ctypes.byref(params), L, n_water, n, _pd(x), alpha, int(kmax), wbar, kappa_lr,
-                           ctypes.byref(ur), ctypes.byref(us), _pd(F)), "h4d_ewald_lr")
-    return ur.value, us.value, F
+                           ctypes.byref(ur), ctypes.byref(us), _pd(F), ctypes.byref(tk)), "h4d_ewald_lr")
+    return (ur.value, us.value, F, tk.value) if kernel_ms else (ur.value, us.value, F)

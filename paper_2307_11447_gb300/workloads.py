@@ -99,9 +99,11 @@ def lj_config(n_ions: int, rho: float, n_f: int, **extra) -> dict:
 # for 250 ions, -8.818 +- 0.524 for 4000 ions.
 CONFIGS = {
     "lj250": lj_config(250, 0.2, 100, trials=200, n_eq=1000, cap_pairs=256, beta_mu=-8.694),
-    # outer-list skin 6x the Verlet skin: fewer outer builds (measured best of a skin sweep)
+    # Verlet skin 0.4, outer-list skin 1.8: the best of two skin sweeps on two GPUs (+2%
+    # over 0.3 / 1.8; larger Verlet skins cost more in the force pass than they save in
+    # list passes, larger outer skins more in the outer rows)
     "lj4000": lj_config(4000, 0.3, 500, trials=10000, n_eq=1000, cap_pairs=2304, chains=304,
-                        beta_mu=-8.818, skin_outer=1.8),
+                        beta_mu=-8.818, skin=0.4, skin_outer=1.8),
 }
 
 
