@@ -1,6 +1,8 @@
 // h4d_ewald.cu -- long-range Coulomb term of Sec. II.B.2 (Eqs. 9-10): the reciprocal-space
 // Ewald sum and the self energy of one configuration, scaled by the altitude screening
-// g^lr(wbar) = exp(-kappa_lr wbar).  Two kernels, both O(k-vectors x atoms):
+// g^lr(wbar) = exp(-kappa_lr wbar).  Two passes, both O(k-vectors x atoms), each a kernel
+// over (k-vectors or atoms) x chunks of the other axis sized to fill the GPU, and an
+// ordered reduction of the chunk partials:
 //   - structure factor: S(k) = sum_j q_j exp(i k.r_j) for every k of one half space;
 //   - forces: F_j = g (8 pi K q_j / V) sum_half A_k k [Re S sin(k.r_j) - Im S cos(k.r_j)].
 // The phase k.r_j / 2 pi = (n_x X_j + n_y Y_j + n_z Z_j) / 2^32 is formed exactly in 32-bit
@@ -25,16 +27,23 @@ struct KVec {
   float pad;
 };
 
-// S(k) of the half space: thread t of block b owns k-vector b*blockDim + t; atoms are
-// staged in tiles; each tile's terms are summed in FP32 and added to FP64 totals
+// The grids cover the GPU: the k-vectors (or atoms) of a block times chunks of the other
+// axis, each chunk a whole number of 256-wide tiles; every block writes its chunk's partial
+// sums, and a second kernel adds the chunks in chunk order (a fixed order: the result does
+// not depend on scheduling).  Within a chunk each tile's terms are summed in FP32 and added
+// to FP64 partials.
+constexpr int kBlocksTarget = 152 * 8;  // 8 resident 256-thread blocks on each of 152 SMs
+
+// S(k) partials: thread t of block (bx, c) owns k-vector bx*256 + t and the atoms of chunk c
 __global__ void __launch_bounds__(256) ewald_sk_kernel(const uint4* __restrict__ xq, int n, const KVec* __restrict__ kv,
-                                                       int nk, double2* __restrict__ sk) {
+                                                       int nk, int chunk_atoms, double2* __restrict__ part) {
   __shared__ uint4 tile[kTile];
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const KVec kk = (k < nk) ? kv[k] : KVec{0, 0, 0, 0.f};
+  const int a0 = blockIdx.y * chunk_atoms, a1 = min(n, a0 + chunk_atoms);
   double re = 0.0, im = 0.0;
-  for (int t0 = 0; t0 < n; t0 += kTile) {
-    const int m = min(kTile, n - t0);
+  for (int t0 = a0; t0 < a1; t0 += kTile) {
+    const int m = min(kTile, a1 - t0);
     __syncthreads();
     for (int a = threadIdx.x; a < m; a += blockDim.x) tile[a] = xq[t0 + a];
     __syncthreads();
@@ -51,11 +60,23 @@ __global__ void __launch_bounds__(256) ewald_sk_kernel(const uint4* __restrict__
     re += (double)fr;
     im += (double)fi;
   }
-  if (k < nk) sk[k] = make_double2(re, im);
+  if (k < nk) part[(size_t)blockIdx.y * nk + k] = make_double2(re, im);
 }
 
-// forces: thread t owns atom b*blockDim + t; the k-vectors and their weighted structure
-// factors (A_k Re S, A_k Im S) are staged in tiles
+__global__ void ewald_sk_reduce(const double2* __restrict__ part, int nk, int n_chunks, double2* __restrict__ sk) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nk) return;
+  double re = 0.0, im = 0.0;
+  for (int c = 0; c < n_chunks; ++c) {
+    const double2 v = part[(size_t)c * nk + k];
+    re += v.x;
+    im += v.y;
+  }
+  sk[k] = make_double2(re, im);
+}
+
+// forces: thread t of block (bx, c) owns atom bx*256 + t and the k-vectors of chunk c; the
+// k-vectors and their weighted structure factors (A_k Re S, A_k Im S) are staged in tiles
 struct KW {
   int nx, ny, nz;
   float pad;
@@ -64,14 +85,14 @@ struct KW {
 };
 
 __global__ void __launch_bounds__(256) ewald_force_kernel(const uint4* __restrict__ xq, int n, const KW* __restrict__ kw,
-                                                          int nk, float two_pi_over_L, double pref,
-                                                          double* __restrict__ F) {
+                                                          int nk, int chunk_k, double* __restrict__ part) {
   __shared__ KW tile[kTile];
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const uint4 p = (j < n) ? xq[j] : make_uint4(0u, 0u, 0u, 0u);
+  const int k0 = blockIdx.y * chunk_k, k1 = min(nk, k0 + chunk_k);
   double gx = 0.0, gy = 0.0, gz = 0.0;
-  for (int t0 = 0; t0 < nk; t0 += kTile) {
-    const int m = min(kTile, nk - t0);
+  for (int t0 = k0; t0 < k1; t0 += kTile) {
+    const int m = min(kTile, k1 - t0);
     __syncthreads();
     for (int a = threadIdx.x; a < m; a += blockDim.x) tile[a] = kw[t0 + a];
     __syncthreads();
@@ -91,12 +112,42 @@ __global__ void __launch_bounds__(256) ewald_force_kernel(const uint4* __restric
     gz += (double)fz;
   }
   if (j < n) {
-    const double qj = (double)__uint_as_float(p.w);
-    const double c = pref * qj * (double)two_pi_over_L;  // k = (2 pi / L) n
-    F[3 * j] = c * gx;
-    F[3 * j + 1] = c * gy;
-    F[3 * j + 2] = c * gz;
+    double* o = part + ((size_t)blockIdx.y * n + j) * 3;
+    o[0] = gx;
+    o[1] = gy;
+    o[2] = gz;
   }
+}
+
+__global__ void ewald_force_reduce(const uint4* __restrict__ xq, const double* __restrict__ part, int n,
+                                   int n_chunks, float two_pi_over_L, double pref, double* __restrict__ F) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double gx = 0.0, gy = 0.0, gz = 0.0;
+  for (int c = 0; c < n_chunks; ++c) {
+    const double* o = part + ((size_t)c * n + j) * 3;
+    gx += o[0];
+    gy += o[1];
+    gz += o[2];
+  }
+  const double qj = (double)__uint_as_float(xq[j].w);
+  const double cc = pref * qj * (double)two_pi_over_L;  // k = (2 pi / L) n
+  F[3 * j] = cc * gx;
+  F[3 * j + 1] = cc * gy;
+  F[3 * j + 2] = cc * gz;
+}
+
+// chunks of the second axis (whole 256-wide tiles) so that blocks x chunks covers the GPU
+__host__ inline void chunking(int n_first, int n_second, int* chunk, int* n_chunks) {
+  const int blocks = (n_first + 255) / 256;
+  const int tiles = (n_second + 255) / 256;
+  int want = (kBlocksTarget + blocks - 1) / blocks;
+  if (want < 1) want = 1;
+  if (want > tiles) want = tiles > 0 ? tiles : 1;
+  const int tiles_per_chunk = (tiles + want - 1) / want;
+  *chunk = tiles_per_chunk * 256;
+  *n_chunks = (n_second + *chunk - 1) / *chunk;
+  if (*n_chunks < 1) *n_chunks = 1;
 }
 
 int type_of_host(int a, int nw3) { return a < nw3 ? ((a % 3 == 0) ? 2 : 3) : ((a - nw3) & 1); }
@@ -157,6 +208,11 @@ extern "C" int h4d_ewald_lr(const h4d_params* params, double L, int32_t n_water,
   double2* d_sk = nullptr;
   KW* d_kw = nullptr;
   double* d_F = nullptr;
+  double2* d_psk = nullptr;  // S(k) partials per atom chunk
+  double* d_pF = nullptr;    // force partials per k-vector chunk
+  int chunk_a = 0, nch_a = 0, chunk_k = 0, nch_k = 0;
+  chunking(nk, n, &chunk_a, &nch_a);
+  chunking(n, nk, &chunk_k, &nch_k);
   std::vector<double2> sk(nk);
   std::vector<KW> kw(nk);
   double u = 0.0;
@@ -172,10 +228,13 @@ extern "C" int h4d_ewald_lr(const h4d_params* params, double L, int32_t n_water,
   CKE(cudaMalloc(&d_xq, sizeof(uint4) * n));
   CKE(cudaMalloc(&d_kv, sizeof(KVec) * nk));
   CKE(cudaMalloc(&d_sk, sizeof(double2) * nk));
+  CKE(cudaMalloc(&d_psk, sizeof(double2) * nk * (size_t)nch_a));
   CKE(cudaMemcpy(d_xq, xq.data(), sizeof(uint4) * n, cudaMemcpyHostToDevice));
   CKE(cudaMemcpy(d_kv, kv.data(), sizeof(KVec) * nk, cudaMemcpyHostToDevice));
   CKE(cudaEventRecord(ev[0]));
-  ewald_sk_kernel<<<(nk + 255) / 256, 256>>>(d_xq, n, d_kv, nk, d_sk);
+  ewald_sk_kernel<<<dim3((nk + 255) / 256, nch_a), 256>>>(d_xq, n, d_kv, nk, chunk_a, d_psk);
+  CKE(cudaGetLastError());
+  ewald_sk_reduce<<<(nk + 255) / 256, 256>>>(d_psk, nk, nch_a, d_sk);
   CKE(cudaGetLastError());
   CKE(cudaEventRecord(ev[1]));
   CKE(cudaMemcpy(sk.data(), d_sk, sizeof(double2) * nk, cudaMemcpyDeviceToHost));
@@ -189,11 +248,14 @@ extern "C" int h4d_ewald_lr(const h4d_params* params, double L, int32_t n_water,
   if (F) {
     CKE(cudaMalloc(&d_kw, sizeof(KW) * nk));
     CKE(cudaMalloc(&d_F, sizeof(double) * 3 * n));
+    CKE(cudaMalloc(&d_pF, sizeof(double) * 3 * n * (size_t)nch_k));
     CKE(cudaMemcpy(d_kw, kw.data(), sizeof(KW) * nk, cudaMemcpyHostToDevice));
     // F_j = g (4 pi K q_j / V) sum_{all k} A_k k [Re S sin - Im S cos]: twice the half space
     CKE(cudaEventRecord(ev[2]));
-    ewald_force_kernel<<<(n + 255) / 256, 256>>>(d_xq, n, d_kw, nk, (float)(2.0 * M_PI / L), g * 8.0 * M_PI * K / V,
-                                                 d_F);
+    ewald_force_kernel<<<dim3((n + 255) / 256, nch_k), 256>>>(d_xq, n, d_kw, nk, chunk_k, d_pF);
+    CKE(cudaGetLastError());
+    ewald_force_reduce<<<(n + 255) / 256, 256>>>(d_xq, d_pF, n, nch_k, (float)(2.0 * M_PI / L),
+                                                 g * 8.0 * M_PI * K / V, d_F);
     CKE(cudaGetLastError());
     CKE(cudaEventRecord(ev[3]));
     CKE(cudaMemcpy(F, d_F, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
@@ -209,5 +271,7 @@ done:
   cudaFree(d_sk);
   cudaFree(d_kw);
   cudaFree(d_F);
+  cudaFree(d_psk);
+  cudaFree(d_pF);
   return rc;
 }

@@ -163,3 +163,41 @@ def test_ideal_water_gas_is_poisson_on_gpu():
     pk = np.exp(kk * math.log(lam) - lam - special.gammaln(kk + 1))
     hist = np.bincount(n.astype(int), minlength=25)[:15] / n.size
     assert np.abs(hist - pk).max() < 0.01
+
+
+def test_packed_water_replicas_are_bit_identical_to_each_alone():
+    """Water exchange in a packed launch: twelve aqueous replicas of 40-300 waters (+ 0-2
+    NaCl pairs, short cut-offs so that the small boxes are legal) share CTAs; three trials
+    with every insertion accepted, then three with every deletion accepted, so the ions
+    of every replica move up and down inside its packed slice.  Each replica run alone in
+    a context of its own with the same seed and replica key gives the same records, end
+    state and water count bit for bit."""
+    sizes = [40, 60, 80, 100, 120, 150, 180, 200, 220, 240, 270, 300]
+    cfg = wl.aq_config(0, 0, 12.0, 20, rc_lj=4.0, rc_coul=4.0, exchange="water", n_eq=5, beta_mu=1.0e8)
+    reps = []
+    for k, nw in enumerate(sizes):
+        npair = k % 3
+        Lk = ((nw + 2 * npair) / 0.025) ** (1.0 / 3.0)  # a dilute liquid: lattice spacing near 3 A
+        reps.append(dict(L=Lk, n_pairs=npair, cap_pairs=npair, n_water=nw, cap_water=nw + 8, key=100 + k,
+                         x=wl.aqueous_positions(nw, npair, Lk, 500 + k)))
+
+    def run(rs):
+        ctx = h4d.Context(h4d.make_params(cfg), rs, seed=99)
+        ctx.h4d_run_md(40)
+        ctx.h4d_run_trials(3, cfg["n_eq"])
+        ctx.h4d_set_mu(-1.0e8)
+        ctx.h4d_run_trials(3, cfg["n_eq"])
+        out = [(ctx.h4d_get_work(r, 6), ctx.h4d_get_state(r), ctx.h4d_get_counts(r)["n_water"]) for r in range(len(rs))]
+        ctx.close()
+        return out
+
+    packed = run(reps)
+    moved = 0
+    for k in range(0, len(reps), 3):
+        alone = run([reps[k]])[0]
+        wp, (xp, vp), nwp = packed[k]
+        wa, (xa, va), nwa = alone
+        assert wp.tobytes() == wa.tobytes(), k
+        assert nwp == nwa and np.array_equal(xp, xa) and np.array_equal(vp, va), k
+        moved += int(wp["accepted"].sum())
+    assert moved > 0  # layouts did change
