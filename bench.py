@@ -310,7 +310,8 @@ def run_gpu(args):
     if args.sequential and args.workload == "batched256":
         seq = sequential_baseline(reps, cfg, args.sequential, n_eq)
     equal_se = None
-    if rank == 0 and args.workload in ("lj4000", "nacl_aq"):
+    # (no accepted exchange: <N> has no spread, so there is no common error to reach)
+    if rank == 0 and args.workload in ("lj4000", "nacl_aq") and gc["mean_n"][1] > 0:
         equal_se = plain_at_equal_se(reps[0], cfg, n_eq, stream, secs, gc["mean_n"][1],
                                      int(sum(x["trials"] for x in sums)), accepted)
     e2e = None

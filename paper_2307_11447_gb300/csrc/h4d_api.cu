@@ -580,6 +580,9 @@ static int check_device() {
 // Launch plan.  Every replica is simulated by a group of whole warps; groups are packed
 // into CTAs of kCtaWarps warps (first-fit decreasing) with at most 15 groups (named
 // barriers 1..15) and kCtaSmem bytes of shared memory per CTA, so two CTAs share an SM.
+// A replica whose positions and cell lists need more than kCtaSmem (a large aqueous box)
+// makes every CTA of the plan hold one SM alone: the CTAs then have twice the warps, so
+// the SM still runs all the warps its registers allow.
 // A group's warp count follows the replica's weight (expected work, or the work the
 // autotuner measured), out of the warps the GPU holds at two CTAs per SM, so that
 // uneven replicas finish together.  A group spanning a whole CTA uses __syncthreads.
@@ -611,11 +614,17 @@ static int make_plan(h4d_ctx* c, const std::vector<double>* weight = nullptr) {
     W += w[r];
   }
   const double budget = (double)c->sm_count * kWarpsPerSm;
+  size_t max_smem = 0;
+  for (int r = 0; r < R; ++r)
+    max_smem = std::max(max_smem, group_smem_bytes(c->rep_h[r].cap_atoms, c->rep_h[r].nc, 32 * kCtaWarps));
+  const bool one_per_sm = max_smem > kCtaSmem;
+  const int cta_warps = one_per_sm ? kWarpsPerSm : kCtaWarps;
+  const size_t cta_smem = one_per_sm ? (size_t)227 * 1024 : kCtaSmem;
   struct Item { int rep, nw; size_t smem; };
   std::vector<Item> items(R);
   for (int r = 0; r < R; ++r) {
     int nw = (int)std::ceil(budget * w[r] / W);
-    nw = std::max(1, std::min(kCtaWarps, nw));
+    nw = std::max(1, std::min(cta_warps, nw));
     items[r] = {r, nw, group_smem_bytes(c->rep_h[r].cap_atoms, c->rep_h[r].nc, 32 * nw)};
     if (items[r].smem > 227 * 1024) return H4D_ECAPACITY;
   }
@@ -627,8 +636,8 @@ static int make_plan(h4d_ctx* c, const std::vector<double>* weight = nullptr) {
     int placed = -1;
     for (size_t q = 0; q < ctas.size() && placed < 0; ++q) {
       Cta& t = ctas[q];
-      if (t.warps + it.nw <= kCtaWarps && (int)t.members.size() < kMaxGroupsPerCta &&
-          t.smem + it.smem <= kCtaSmem)
+      if (t.warps + it.nw <= cta_warps && (int)t.members.size() < kMaxGroupsPerCta &&
+          t.smem + it.smem <= cta_smem)
         placed = (int)q;
     }
     if (placed < 0) { ctas.emplace_back(); placed = (int)ctas.size() - 1; }
@@ -644,7 +653,7 @@ static int make_plan(h4d_ctx* c, const std::vector<double>* weight = nullptr) {
     c->cta_groups_h.push_back((int)c->groups_h.size());
     int warp0 = 0, bar = 1;
     size_t off = 0;
-    const bool whole = t.members.size() == 1 && items[t.members[0]].nw == kCtaWarps;
+    const bool whole = t.members.size() == 1 && items[t.members[0]].nw == cta_warps;
     for (int k : t.members) {
       Group g;
       g.rep = items[k].rep;
@@ -661,7 +670,7 @@ static int make_plan(h4d_ctx* c, const std::vector<double>* weight = nullptr) {
   }
   c->cta_groups_h.push_back((int)c->groups_h.size());
   c->n_ctas = (int)ctas.size();
-  c->cta_threads = 32 * kCtaWarps;
+  c->cta_threads = 32 * cta_warps;
   c->smem = smem;
   return H4D_OK;
 }
