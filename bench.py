@@ -129,6 +129,21 @@ def src_hash():
     return h.hexdigest()[:16]
 
 
+def pair_pass_roofline(pairs, tune, tpa_hist, phase, achieved, peak):
+    """The force pass by itself: (1) launched alone by the autotuner (every chain's pass at
+    once, each timed by its group's device global timer; the pass time of the lane count
+    most chains use), (2) inside the persistent kernel (its share of the launch time from
+    the phase timers).  Same algorithmic count as the kernel roofline: 55 flop per pair
+    inside the cut-off, each unordered pair once."""
+    t_most = max(tpa_hist.items(), key=lambda kv: kv[1])[0]
+    us = tune[t_most][0] / 1e3
+    alone = pairs * FLOPS_PER_PAIR / (us * 1e-6) / 1e12
+    inside = achieved / phase["force"] if phase.get("force") else None
+    return {"alone": {"threads_per_atom": int(t_most), "us_per_pass": us, "achieved": alone, "frac": alone / peak},
+            "inside_engine": {"achieved": inside, "frac": inside / peak if inside else None},
+            "unit": "TFLOP/s"}
+
+
 def default_launch(args, cfg):
     """True for the launch the committed traffic figure was scaled to: the 4000-ion
     workload with its own chain count, protocol and skins"""
@@ -357,7 +372,8 @@ def run_gpu(args):
                                        f"nominal {sm_count} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz = "
                                        f"{nominal:.1f} TFLOP/s",
                          "frac_of_nominal": achieved / nominal,
-                         "pairs_in_cutoff": pairs, "flops_per_pair": FLOPS_PER_PAIR},
+                         "pairs_in_cutoff": pairs, "flops_per_pair": FLOPS_PER_PAIR,
+                         "pair_pass": pair_pass_roofline(pairs, tune, tpa_hist, phase, achieved, peak)},
             "grand_canonical": {
                 "beta_mu": cfg["beta_mu"], "trials": int(sum(x["trials"] for x in sums)),
                 "mean_n": gc["mean_n"], "chi_osmotic": gc["chi"], "acceptance": gc["acc"],
