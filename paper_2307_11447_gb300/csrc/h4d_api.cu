@@ -578,20 +578,16 @@ static int check_device() {
 }
 
 // Launch plan.  Every replica is simulated by a group of whole warps; groups are packed
-// into CTAs of kCtaWarps warps (first-fit decreasing) with at most 15 groups (named
-// barriers 1..15) and kCtaSmem bytes of shared memory per CTA, so two CTAs share an SM.
-// A replica whose positions and cell lists need more than kCtaSmem (a large aqueous box)
-// makes every CTA of the plan hold one SM alone: the CTAs then have twice the warps, so
-// the SM still runs all the warps its registers allow.
+// into CTAs (first-fit decreasing; kCtaWarpsLJ or kCtaWarpsAQ warps) with at most 15
+// groups (named barriers 1..15) and kCtaSmem bytes of shared memory per CTA, so two CTAs
+// share an SM.  An aqueous replica whose positions and cell lists need more than kCtaSmem
+// makes every CTA of the plan hold one SM alone: the CTAs then have kMaxCtaWarpsAQ warps,
+// so the SM still runs all the warps its registers allow.  (An LJ replica that large gets
+// an SM to itself with one 12-warp CTA.)
 // A group's warp count follows the replica's weight (expected work, or the work the
 // autotuner measured), out of the warps the GPU holds at two CTAs per SM, so that
 // uneven replicas finish together.  A group spanning a whole CTA uses __syncthreads.
-#ifndef H4D_CTA_WARPS
-#define H4D_CTA_WARPS 16
-#endif
-static const int kCtaWarps = H4D_CTA_WARPS;
-static const int kWarpsPerSm = 32;  // resident warps per SM at the engine's 64 registers
-static const size_t kCtaSmem = (size_t)(kWarpsPerSm / kCtaWarps > 1 ? 113 : 227) * 1024;
+static const size_t kCtaSmem = (size_t)113 * 1024;  // two CTAs per SM
 
 static double default_weight(const Rep& r) {
   // pair count ~ atoms x density
@@ -613,13 +609,15 @@ static int make_plan(h4d_ctx* c, const std::vector<double>* weight = nullptr) {
     w[r] = (weight && (*weight)[r] > 0) ? (*weight)[r] : default_weight(c->rep_h[r]);
     W += w[r];
   }
-  const double budget = (double)c->sm_count * kWarpsPerSm;
   size_t max_smem = 0;
   for (int r = 0; r < R; ++r)
-    max_smem = std::max(max_smem, group_smem_bytes(c->rep_h[r].cap_atoms, c->rep_h[r].nc, 32 * kCtaWarps));
+    max_smem = std::max(max_smem, group_smem_bytes(c->rep_h[r].cap_atoms, c->rep_h[r].nc, 0));
   const bool one_per_sm = max_smem > kCtaSmem;
-  const int cta_warps = one_per_sm ? kWarpsPerSm : kCtaWarps;
+  const bool lj = c->prm.system == H4D_SYS_LJ;
+  const int cta_warps = lj ? kCtaWarpsLJ : (one_per_sm ? kMaxCtaWarpsAQ : kCtaWarpsAQ);
   const size_t cta_smem = one_per_sm ? (size_t)227 * 1024 : kCtaSmem;
+  // resident warps of the GPU under this plan, shared out by weight
+  const double budget = (double)c->sm_count * cta_warps * (one_per_sm ? 1 : 2);
   struct Item { int rep, nw; size_t smem; };
   std::vector<Item> items(R);
   for (int r = 0; r < R; ++r) {

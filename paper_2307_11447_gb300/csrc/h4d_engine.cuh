@@ -20,6 +20,13 @@ namespace h4d {
 
 constexpr int kMaxT = 4;
 constexpr int kMaxGroupsPerCta = 15;  // named barriers 1..15
+// Engine CTA sizes.  The LJ engine runs two 12-warp CTAs per SM, which leaves it about 80
+// registers per thread (at 16 warps and 64 registers it spills more; measured 2-3% slower
+// per cycle); the aqueous engine runs 16-warp CTAs, or a whole 32-warp CTA per SM when a
+// replica needs that SM's shared memory.
+constexpr int kCtaWarpsLJ = 12;
+constexpr int kCtaWarpsAQ = 16;
+constexpr int kMaxCtaWarpsAQ = 32;
 
 struct Pot {
   int sys, ntypes;

@@ -71,7 +71,7 @@ def test_batched_replicas_are_bit_identical_to_each_replica_alone(batch_run):
         ctx.h4d_run_md(100)
         ctx.h4d_run_trials(5, cfg["n_eq"])
         c1 = ctx.h4d_get_counts(0)
-        assert c1["plan_cta_groups"] == 1 and c1["plan_warps"] == 16  # a whole CTA of its own
+        assert c1["plan_cta_groups"] == 1 and c1["plan_warps"] == 12  # a whole (12-warp LJ) CTA of its own
         xa, va = out[r]["state"]
         xb, vb = ctx.h4d_get_state(0)
         assert np.array_equal(xa, xb) and np.array_equal(va, vb), r
