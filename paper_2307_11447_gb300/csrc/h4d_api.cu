@@ -583,7 +583,7 @@ static int check_device() {
 // share an SM.  An aqueous replica whose positions and cell lists need more than kCtaSmem
 // makes every CTA of the plan hold one SM alone: the CTAs then have kMaxCtaWarpsAQ warps,
 // so the SM still runs all the warps its registers allow.  (An LJ replica that large gets
-// an SM to itself with one 12-warp CTA.)
+// an SM to itself with one 16-warp CTA.)
 // A group's warp count follows the replica's weight (expected work, or the work the
 // autotuner measured), out of the warps the GPU holds at two CTAs per SM, so that
 // uneven replicas finish together.  A group spanning a whole CTA uses __syncthreads.

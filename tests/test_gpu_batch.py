@@ -64,14 +64,14 @@ def test_batched_replicas_are_bit_identical_to_each_replica_alone(batch_run):
     sizes = [2 * reps[r]["n_pairs"] for r in SUBSET]
     print(f"\nsubset ions {min(sizes)}-{max(sizes)}; group warps in the batch {warps}; "
           f"{len(shared)} of {len(SUBSET)} share a CTA with other replicas")
-    assert len(shared) >= 4  # the multi-group CTAs of the planner are exercised
+    assert len(shared) >= 3  # the multi-group CTAs of the planner are exercised
     accepted = 0
     for r in SUBSET:
         ctx = h4d.Context(h4d.make_params(cfg), [reps[r]], seed=2024)
         ctx.h4d_run_md(100)
         ctx.h4d_run_trials(5, cfg["n_eq"])
         c1 = ctx.h4d_get_counts(0)
-        assert c1["plan_cta_groups"] == 1 and c1["plan_warps"] == 12  # a whole (12-warp LJ) CTA of its own
+        assert c1["plan_cta_groups"] == 1 and c1["plan_warps"] == 16  # a whole CTA of its own
         xa, va = out[r]["state"]
         xb, vb = ctx.h4d_get_state(0)
         assert np.array_equal(xa, xb) and np.array_equal(va, vb), r
