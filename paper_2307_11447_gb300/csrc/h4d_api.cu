@@ -578,16 +578,19 @@ static int check_device() {
 }
 
 // Launch plan.  Every replica is simulated by a group of whole warps; groups are packed
-// into CTAs (first-fit decreasing; kCtaWarpsLJ or kCtaWarpsAQ warps) with at most 15
-// groups (named barriers 1..15) and kCtaSmem bytes of shared memory per CTA, so two CTAs
-// share an SM.  An aqueous replica whose positions and cell lists need more than kCtaSmem
-// makes every CTA of the plan hold one SM alone: the CTAs then have kMaxCtaWarpsAQ warps,
-// so the SM still runs all the warps its registers allow.  (An LJ replica that large gets
-// an SM to itself with one 16-warp CTA.)
+// into CTAs (first-fit decreasing) with at most 15 groups (named barriers 1..15): two
+// 16-warp CTAs of at most 113 KB shared memory per SM, or one 32-warp CTA per SM when a
+// replica needs more shared memory than that (a large aqueous box) or the replicas are
+// uneven (a batch of sizes more than 2x apart: its largest members can then have twice
+// the warps).  (Measured on one GPU: equal 4000-ion chains run 31% slower as pairs of
+// groups in 32-warp CTAs than in 16-warp CTAs of their own; the uneven batch of 256
+// runs 36% faster in 32-warp CTAs.)
 // A group's warp count follows the replica's weight (expected work, or the work the
-// autotuner measured), out of the warps the GPU holds at two CTAs per SM, so that
-// uneven replicas finish together.  A group spanning a whole CTA uses __syncthreads.
+// autotuner measured), out of the warps one resident wave of CTAs holds, so that uneven
+// replicas finish together; rounding that would spill into a second wave shrinks the
+// budget.  A group spanning a whole CTA uses __syncthreads.
 static const size_t kCtaSmem = (size_t)113 * 1024;  // two CTAs per SM
+static const int kCtaWarps = 16, kMaxCtaWarps = 32;
 
 static double default_weight(const Rep& r) {
   // pair count ~ atoms x density
@@ -610,39 +613,53 @@ static int make_plan(h4d_ctx* c, const std::vector<double>* weight = nullptr) {
     W += w[r];
   }
   size_t max_smem = 0;
-  for (int r = 0; r < R; ++r)
-    max_smem = std::max(max_smem, group_smem_bytes(c->rep_h[r].cap_atoms, c->rep_h[r].nc, 0));
-  const bool one_per_sm = max_smem > kCtaSmem;
-  const bool lj = c->prm.system == H4D_SYS_LJ;
-  const int cta_warps = lj ? kCtaWarpsLJ : (one_per_sm ? kMaxCtaWarpsAQ : kCtaWarpsAQ);
-  const size_t cta_smem = one_per_sm ? (size_t)227 * 1024 : kCtaSmem;
-  // resident warps of the GPU under this plan, shared out by weight
-  const double budget = (double)c->sm_count * cta_warps * (one_per_sm ? 1 : 2);
-  struct Item { int rep, nw; size_t smem; };
-  std::vector<Item> items(R);
+  int min_atoms = 1 << 30, max_atoms = 0;
   for (int r = 0; r < R; ++r) {
-    int nw = (int)std::ceil(budget * w[r] / W);
-    nw = std::max(1, std::min(cta_warps, nw));
-    items[r] = {r, nw, group_smem_bytes(c->rep_h[r].cap_atoms, c->rep_h[r].nc, 32 * nw)};
-    if (items[r].smem > 227 * 1024) return H4D_ECAPACITY;
+    max_smem = std::max(max_smem, group_smem_bytes(c->rep_h[r].cap_atoms, c->rep_h[r].nc, 0));
+    min_atoms = std::min(min_atoms, c->rep_h[r].cap_atoms);
+    max_atoms = std::max(max_atoms, c->rep_h[r].cap_atoms);
   }
-  std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.nw > b.nw; });
+  // One 32-warp CTA per SM when a replica needs more shared memory than half an SM, and
+  // for batches of uneven replicas: their large members then get up to twice the warps,
+  // so the launch no longer waits on them alone.  Equal replicas keep two 16-warp CTAs.
+  const bool uneven = max_atoms > 2 * min_atoms;
+  const bool one_per_sm = max_smem > kCtaSmem || uneven;
+  const int cta_warps = one_per_sm ? kMaxCtaWarps : kCtaWarps;
+  const size_t cta_smem = one_per_sm ? (size_t)227 * 1024 : kCtaSmem;
+  const int max_ctas = c->sm_count * (one_per_sm ? 1 : 2);  // one resident wave
+  struct Item { int rep, nw; size_t smem; };
   struct Cta { int warps = 0; size_t smem = 0; std::vector<int> members; };
+  std::vector<Item> items(R);
   std::vector<Cta> ctas;
-  for (int k = 0; k < R; ++k) {
-    const Item& it = items[k];
-    int placed = -1;
-    for (size_t q = 0; q < ctas.size() && placed < 0; ++q) {
-      Cta& t = ctas[q];
-      if (t.warps + it.nw <= cta_warps && (int)t.members.size() < kMaxGroupsPerCta &&
-          t.smem + it.smem <= cta_smem)
-        placed = (int)q;
+  // resident warps of the GPU under this plan, shared out by weight; if rounding makes
+  // the packing spill into a second wave of CTAs, shrink the budget and pack again
+  double budget = (double)max_ctas * cta_warps;
+  for (int attempt = 0; attempt < 64; ++attempt) {
+    for (int r = 0; r < R; ++r) {
+      int nw = (int)std::ceil(budget * w[r] / W);
+      nw = std::max(1, std::min(cta_warps, nw));
+      items[r] = {r, nw, group_smem_bytes(c->rep_h[r].cap_atoms, c->rep_h[r].nc, 32 * nw)};
+      if (items[r].smem > 227 * 1024) return H4D_ECAPACITY;
     }
-    if (placed < 0) { ctas.emplace_back(); placed = (int)ctas.size() - 1; }
-    Cta& t = ctas[placed];
-    t.members.push_back(k);
-    t.warps += it.nw;
-    t.smem += it.smem;
+    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.nw > b.nw; });
+    ctas.clear();
+    for (int k = 0; k < R; ++k) {
+      const Item& it = items[k];
+      int placed = -1;
+      for (size_t q = 0; q < ctas.size() && placed < 0; ++q) {
+        Cta& t = ctas[q];
+        if (t.warps + it.nw <= cta_warps && (int)t.members.size() < kMaxGroupsPerCta &&
+            t.smem + it.smem <= cta_smem)
+          placed = (int)q;
+      }
+      if (placed < 0) { ctas.emplace_back(); placed = (int)ctas.size() - 1; }
+      Cta& t = ctas[placed];
+      t.members.push_back(k);
+      t.warps += it.nw;
+      t.smem += it.smem;
+    }
+    if ((int)ctas.size() <= max_ctas) break;
+    budget *= 0.95;
   }
   c->groups_h.clear();
   c->cta_groups_h.clear();

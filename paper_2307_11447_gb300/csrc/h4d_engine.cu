@@ -16,7 +16,7 @@
 #include "h4d_prop.cuh"
 
 // Engine launch bounds: threads per CTA and CTAs per SM the register allocation targets
-// launch bounds of the aqueous engine kernels (the LJ ones follow kCtaWarpsLJ)
+// launch bounds of the engine kernels: CTAs of up to 32 warps, 64 registers per thread
 #ifndef H4D_MAXTHREADS
 #define H4D_MAXTHREADS 1024
 #endif
@@ -2438,8 +2438,7 @@ __device__ bool setup_ctx(const Eng& e, char* smem, Ctx& c) {
 }
 
 template <int SYS>
-__global__ void __launch_bounds__(SYS == H4D_SYS_LJ ? 32 * kCtaWarpsLJ : H4D_MAXTHREADS,
-                                  SYS == H4D_SYS_LJ ? 2 : H4D_MINBLOCKS) cycles_kernel(const __grid_constant__ Eng e, long long k_cycles, int n_eq, int do_trial) {
+__global__ void __launch_bounds__(H4D_MAXTHREADS, H4D_MINBLOCKS) cycles_kernel(const __grid_constant__ Eng e, long long k_cycles, int n_eq, int do_trial) {
   extern __shared__ __align__(16) char smem[];
   Ctx c;
   if (!setup_ctx(e, smem, c)) return;
@@ -2588,8 +2587,7 @@ int launch_eval(const Eng& e, int threads, size_t smem, float wbar, double* U, v
 // n_iter equilibrium force passes on the current state (autotuning and profiling of the
 // pair term in isolation); leaves positions and velocities untouched
 template <int SYS>
-__global__ void __launch_bounds__(SYS == H4D_SYS_LJ ? 32 * kCtaWarpsLJ : H4D_MAXTHREADS,
-                                  SYS == H4D_SYS_LJ ? 2 : H4D_MINBLOCKS) forces_kernel(const __grid_constant__ Eng e, int n_iter) {
+__global__ void __launch_bounds__(H4D_MAXTHREADS, H4D_MINBLOCKS) forces_kernel(const __grid_constant__ Eng e, int n_iter) {
   extern __shared__ __align__(16) char smem[];
   Ctx c;
   if (!setup_ctx(e, smem, c)) return;

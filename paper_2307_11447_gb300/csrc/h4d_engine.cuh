@@ -20,14 +20,6 @@ namespace h4d {
 
 constexpr int kMaxT = 4;
 constexpr int kMaxGroupsPerCta = 15;  // named barriers 1..15
-// Engine CTA sizes: two 16-warp CTAs per SM (64 registers per thread), or for aqueous
-// replicas that need a whole SM's shared memory one 32-warp CTA per SM.  (Two 12-warp LJ
-// CTAs, 80 registers and fewer spills, measured on one GPU against 16 warps: +0.7% on the
-// 4000-ion workload, -6 to -8% on the batched one, whose small replicas then get fewer
-// warps.)
-constexpr int kCtaWarpsLJ = 16;
-constexpr int kCtaWarpsAQ = 16;
-constexpr int kMaxCtaWarpsAQ = 32;
 
 struct Pot {
   int sys, ntypes;
