@@ -459,14 +459,19 @@ def _initial_weights(seed):
 
 
 def _fixed_n_sample(ctx, cycles):
-    recs = []
+    """insertion and deletion exponents of every chain's fixed-N trials, per chain"""
+    groups = []
     ctx.h4d_run_trials(cycles, 10)
     for r in range(ctx.R):
         w = ctx.h4d_get_work(r, cycles)
-        recs.append(w[w["status"] == 0])
-    rec = np.concatenate(recs)
-    ins = rec["move"] == 1
-    return rec["x_acc"][ins], rec["x_acc"][~ins]
+        w = w[w["status"] == 0]
+        ins = w["move"] == 1
+        groups.append((w["x_acc"][ins], w["x_acc"][~ins]))
+    return groups
+
+
+def _flat(groups):
+    return np.concatenate([a for a, _ in groups]), np.concatenate([b for _, b in groups])
 
 
 def learned_setup(ctx, cfg, args, stream):
@@ -511,12 +516,18 @@ def learned_setup(ctx, cfg, args, stream):
     t_train = time.perf_counter() - t0
     # production protocol, fixed N: both proposals from the same ensemble
     ctx.h4d_set_protocol(n_f, cfg["w_max"], cfg["dt"], cfg.get("kappa_sr", 0.0), 0)
+    from paper_2307_11447_gb300 import analysis as an
+
     ctx.h4d_proposal(h4d.H4D_PROPOSAL_UNIFORM, args.cell_len, 0.1, 0)
-    ui, ud = _fixed_n_sample(ctx, args.calib_cycles)
+    ug = _fixed_n_sample(ctx, args.calib_cycles)
     ctx.h4d_proposal(h4d.H4D_PROPOSAL_LEARNED, args.cell_len, 0.1, 0)
-    li, ld = _fixed_n_sample(ctx, args.calib_cycles)
+    lg = _fixed_n_sample(ctx, args.calib_cycles)
+    ui, ud = _flat(ug)
+    li, ld = _flat(lg)
     mu = _balanced_mu(ui, ud)
     acc = lambda xi, xd: 0.5 * (np.exp(np.minimum(xi + mu, 0)).mean() + np.exp(np.minimum(xd - mu, 0)).mean())
+    # standard errors by a jackknife over chains (Eq. 21 estimates at the balancing beta mu)
+    acc_se = lambda g: an.jackknife(g, lambda gg: acc(*_flat(gg)))[1]
     ctx.h4d_set_no_accept(0)
     ctx.h4d_set_mu(mu)
     return {
@@ -528,9 +539,11 @@ def learned_setup(ctx, cfg, args, stream):
         "fixed_n_production": {
             "trials_per_proposal": int(len(ui) + len(ud)),
             "uniform": {"median_x_ins": float(np.median(ui)), "median_x_del": float(np.median(ud)),
-                        "mean_acceptance_at_balanced_mu": float(acc(ui, ud))},
+                        "mean_acceptance_at_balanced_mu": float(acc(ui, ud)),
+                        "mean_acceptance_se": float(acc_se(ug))},
             "learned": {"median_x_ins": float(np.median(li)), "median_x_del": float(np.median(ld)),
-                        "mean_acceptance_at_balanced_mu": float(acc(li, ld))},
+                        "mean_acceptance_at_balanced_mu": float(acc(li, ld)),
+                        "mean_acceptance_se": float(acc_se(lg))},
         },
     }
 
