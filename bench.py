@@ -530,6 +530,7 @@ def learned_setup(ctx, cfg, args, stream):
     acc_se = lambda g: an.jackknife(g, lambda gg: acc(*_flat(gg)))[1]
     ctx.h4d_set_no_accept(0)
     ctx.h4d_set_mu(mu)
+    cfg["beta_mu"] = mu  # the timed cycles run at the balancing beta mu
     return {
         "records": int(ok.sum()), "record_n_f": args.record_nf, "cell_len_A": args.cell_len,
         "grid_cells_per_edge": int(max(3, min(32, math.floor(cfg["L"] / args.cell_len)))),
