@@ -288,6 +288,7 @@ static void fill_pot(const h4d_params& p, Pot& P, Proto& pr) {
   P.d_oh2 = p.d_oh * p.d_oh;
   P.d_hh2 = p.d_hh * p.d_hh;
   for (int t = 0; t < 4; ++t) P.q[t] = (t < p.ntypes) ? (float)p.q[t] : 0.f;
+  P.erfcx_fit = p.alpha * p.rc_coul <= 3.2 ? 1 : 0;  // the fit's range (fit_erfcx.py)
   std::memset(&pr, 0, sizeof(pr));
   pr.n_f = p.n_f;
   pr.schedule = p.schedule;

@@ -85,6 +85,23 @@ __device__ __forceinline__ float as_erfc_poly(float x) {
   p = fmaf(t, p, 0.254829592f);
   return p * t;
 }
+// erfcx(x) = e^{x^2} erfc(x) on [0, 3.2] as t sum_k c_k t^k, t = 1/(1 + x/2), with the
+// coefficients printed by fit_erfcx.py (a least-squares fit in relative error, reweighted
+// toward minimax: 1.3e-10 in exact arithmetic, 3.3e-7 in this float32 evaluation)
+__device__ __forceinline__ float erfcx_poly(float x) {
+  const float t = __frcp_rn(fmaf(0.5f, x, 1.0f));
+  float p = 3.845890611e-02f;
+  p = fmaf(p, t, -2.708916664e-01f);
+  p = fmaf(p, t, 7.915914059e-01f);
+  p = fmaf(p, t, -1.178810358e+00f);
+  p = fmaf(p, t, 8.702221513e-01f);
+  p = fmaf(p, t, -3.565987349e-01f);
+  p = fmaf(p, t, 3.224146068e-01f);
+  p = fmaf(p, t, 2.157940567e-01f);
+  p = fmaf(p, t, 2.859359086e-01f);
+  p = fmaf(p, t, 2.818836868e-01f);
+  return p * t;
+}
 __device__ __forceinline__ float exp_neg_sq(float x) {
   // e^{-x^2} = 2^{-x^2 log2 e}
   float y = -x * x * 1.4426950408889634f;
@@ -132,8 +149,17 @@ __device__ __forceinline__ float pair_fr(const Pot& P, const PairCoef<SYS>& c, f
   float ex = exp_neg_sq(x);
   // LJ electrolyte: alpha r <= 1.2, where the A&S form (absolute error 1.5e-7) is ~1e-6
   // relative; aqueous: alpha r reaches 2.5, where only a relatively accurate erfc keeps
-  // the cancelling water Coulomb sums at 1e-5, so the CUDA library erfcf is used there
-  float erfcx = (SYS == H4D_SYS_LJ) ? as_erfc_poly(x) * ex : erfcf(x);
+  // the cancelling water Coulomb sums at 1e-5: e^{-x^2} times the fitted erfcx (relative
+  // error as small as the library erfcf's, and it shares e^{-x^2} with the force term),
+  // or the library erfcf when the cut-off reaches beyond the fit
+  float erfcx;
+  if (SYS == H4D_SYS_LJ) {
+    erfcx = as_erfc_poly(x) * ex;
+  } else if (P.erfcx_fit) {
+    erfcx = ex * erfcx_poly(x);
+  } else {
+    erfcx = erfcf(x);
+  }
   float fr_c = c.kq * g * fmaf(erfcx, rinv, P.two_alpha_sqrtpi * ex) * rinv2;
   fr_c = (r2 < P.rc2_c) ? fr_c : 0.0f;
   return fr_lj + fr_c;

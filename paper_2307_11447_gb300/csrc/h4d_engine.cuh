@@ -33,6 +33,8 @@ struct Pot {
   double d_oh2, d_hh2;  // squared water bond lengths
   double inv_m_d[kMaxT];
   float q[kMaxT];       // charges per type (proposal field feature)
+  int erfcx_fit;        // alpha rc_coul within the range of the fitted erfcx (aqueous pair term)
+  int pad_fit;
 };
 
 struct Proto {
