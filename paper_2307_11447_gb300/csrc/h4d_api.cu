@@ -237,6 +237,66 @@ static double species_rw(const h4d_params& p, double f_w) {
   return 1.0 + 0.5 * (p.sig[0] + p.sig[1]) * f_w / p.w_max;
 }
 
+// Screened-Coulomb force term of the LJ electrolyte as a polynomial.  With x = alpha r,
+//   -du/dr / r = kq g (erfc(x) + 2x/sqrt(pi) e^{-x^2}) / r^3 = kq g (r^-3 + alpha^3 H(x^2)),
+//   H(v) = (erfc(x) + 2x/sqrt(pi) e^{-v} - 1) / x^3 = -(4/sqrt(pi)) sum_n (-v)^n / ((2n + 3) n!),
+// an entire function of v = x^2 (the bracket is 1 - (4/sqrt(pi)) int_0^x t^2 e^{-t^2} dt, odd
+// in x from x^3 on).  C(s) = alpha^3 H(alpha^2 s) is interpolated in s = r^2 at the 8
+// Chebyshev nodes of [0, rc^2]; the kernel then needs one rsqrt per pair and no exp, rcp or
+// erfc.  The float evaluation of r^-3 + C loses 1/G(alpha rc) to cancellation at the
+// cut-off, so the form is used for alpha rc <= 1.3 (relative error of the polynomial below
+// 2e-7 there); otherwise the kernel keeps the erfc form.
+static double coul_H(double v) {
+  double s = 0.0, term = 1.0;  // term = v^n / n!
+  for (int n = 0; n < 400; ++n) {
+    s += ((n & 1) ? -term : term) / (2 * n + 3);
+    term *= v / (n + 1);
+    if (n > 4 && term < 1e-20) break;
+  }
+  return -4.0 / std::sqrt(M_PI) * s;
+}
+
+static void fit_coul_poly(const h4d_params& p, Pot& P) {
+  P.coul_poly = 0;
+  const double a = p.alpha, rc = p.rc_coul;
+  if (p.system != H4D_SYS_LJ || !(rc > 0) || !(a >= 0) || a * rc > 1.3) return;
+  const int D = 8;
+  const double S = rc * rc;
+  double A[D][D + 1];
+  for (int k = 0; k < D; ++k) {  // interpolation conditions in u = s / S, u in [0, 1]
+    const double u = 0.5 * (1.0 - std::cos(M_PI * (k + 0.5) / D));
+    double pw = 1.0;
+    for (int j = 0; j < D; ++j) { A[k][j] = pw; pw *= u; }
+    A[k][D] = a * a * a * coul_H(a * a * u * S);
+  }
+  for (int col = 0; col < D; ++col) {  // Gaussian elimination, partial pivoting
+    int piv = col;
+    for (int r = col + 1; r < D; ++r)
+      if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+    for (int j = 0; j <= D; ++j) std::swap(A[col][j], A[piv][j]);
+    for (int r = 0; r < D; ++r) {
+      if (r == col) continue;
+      const double f = A[r][col] / A[col][col];
+      for (int j = col; j <= D; ++j) A[r][j] -= f * A[col][j];
+    }
+  }
+  double c[D];
+  double sc = 1.0;
+  for (int j = 0; j < D; ++j) { c[j] = A[j][D] / A[j][j] / sc; sc *= S; }
+  // check the interpolant against the series on a fine grid of r in (0, rc]
+  double worst = 0.0;
+  for (int k = 1; k <= 2000; ++k) {
+    const double r = rc * k / 2000.0, s = r * r;
+    double poly = 0.0;
+    for (int j = D - 1; j >= 0; --j) poly = poly * s + c[j];
+    const double exact = 1.0 / (r * r * r) + a * a * a * coul_H(a * a * s);
+    worst = std::max(worst, std::fabs(poly - a * a * a * coul_H(a * a * s)) / std::fabs(exact));
+  }
+  if (!(worst < 2e-7)) return;
+  for (int j = 0; j < D; ++j) P.cpoly[j] = (float)c[j];
+  P.coul_poly = 1;
+}
+
 static void fill_pot(const h4d_params& p, Pot& P, Proto& pr) {
   std::memset(&P, 0, sizeof(P));
   P.sys = p.system;
@@ -289,6 +349,9 @@ static void fill_pot(const h4d_params& p, Pot& P, Proto& pr) {
   P.d_hh2 = p.d_hh * p.d_hh;
   for (int t = 0; t < 4; ++t) P.q[t] = (t < p.ntypes) ? (float)p.q[t] : 0.f;
   P.erfcx_fit = p.alpha * p.rc_coul <= 3.2 ? 1 : 0;  // the fit's range (fit_erfcx.py)
+  fit_coul_poly(p, P);
+  P.lj12 = 12.0f * P.eps4[0];
+  P.lj6 = 6.0f * P.eps4[0];
   std::memset(&pr, 0, sizeof(pr));
   pr.n_f = p.n_f;
   pr.schedule = p.schedule;

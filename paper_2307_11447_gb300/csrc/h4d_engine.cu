@@ -205,6 +205,29 @@ __device__ __forceinline__ float2 pair_fr_lj2(const Pot& P, float2 r2, float2 kq
   return __fadd2_rn(fr_lj, fr_c);
 }
 
+// The same two pair terms with the screened-Coulomb force as r^-3 + C(r^2) (C the degree-7
+// polynomial the host interpolates for this alpha and cut-off, Pot::cpoly): Eqs. 9-11 with
+// the erfc and Gaussian terms folded into C, so one rsqrt is the only special function of
+// a pair.  The LJ term of Eq. 19 takes 12 eps4 and 6 eps4 as constants.  Pairs beyond a
+// cut-off (skin entries, the sentinel at infinite altitude) are dropped by selects, so the
+// polynomial's value there does not matter.
+__device__ __forceinline__ float2 pair_fr_lj2_poly(const Pot& P, float2 r2, float2 kqg) {
+  const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+  const float2 rinv2 = __fmul2_rn(rinv, rinv);
+  const float2 s2 = __fmul2_rn(f2(P.sig2[0]), rinv2);
+  const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
+  float2 fr_lj = __fmul2_rn(__fmul2_rn(s6, __ffma2_rn(f2(P.lj12), s6, f2(-P.lj6))), rinv2);
+  fr_lj.x = (r2.x < P.rc2_lj) ? fr_lj.x : 0.0f;
+  fr_lj.y = (r2.y < P.rc2_lj) ? fr_lj.y : 0.0f;
+  float2 cp = __ffma2_rn(f2(P.cpoly[7]), r2, f2(P.cpoly[6]));
+#pragma unroll
+  for (int k = 5; k >= 0; --k) cp = __ffma2_rn(cp, r2, f2(P.cpoly[k]));
+  float2 fr_c = __fmul2_rn(kqg, __ffma2_rn(rinv2, rinv, cp));
+  fr_c.x = (r2.x < P.rc2_c) ? fr_c.x : 0.0f;
+  fr_c.y = (r2.y < P.rc2_c) ? fr_c.y : 0.0f;
+  return __fadd2_rn(fr_lj, fr_c);
+}
+
 // FP32 pair energy (protocol-work diagnostic only)
 template <int SYS>
 __device__ __forceinline__ float pair_u32(const Pot& P, const PairCoef<SYS>& c, float r2, float g) {
@@ -249,7 +272,8 @@ struct GScal {
   int n_before, accept, inst;  // inst: instantaneous move (early rejection)
   int flag_timeout;            // a bounded iteration (SHAKE, RATTLE, gamma draw) gave up
   int fly2, flyw;              // water exchange: third flying atom, flying water (-1 = none)
-  int nw_trial, pad_t;         // waters in the layout of the running trial
+  int nw_trial;                // waters in the layout of the running trial
+  int n_ord;                   // atoms in the lane order (sorted[0, n_ord)); 0 = no order
   float w_cur, g_scr, pad2, pad3;
   double alpha_th, dW[3], wprot, wprot_c, red_out;
   double ln_u, ustart, kstart, uend, kend;
@@ -418,6 +442,18 @@ __device__ double fixed_order_sum(const Ctx& c, double* buf, int n) {
   return c.v.s->red_out;
 }
 
+// L2 prefetch of a row packet a few packets ahead of the one being loaded: the rows stream
+// from HBM and each lane walks its own, so the next packet alone does not cover the latency
+// (distances in packets, build options; 0 = none)
+#ifndef H4D_PF_FILTER
+#define H4D_PF_FILTER 8
+#endif
+#ifndef H4D_PF_FORCE
+#define H4D_PF_FORCE 4
+#endif
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 __device__ __forceinline__ u64 gtimer() {
   u64 t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -510,6 +546,7 @@ __device__ H4D_PHASE void build_list_impl(const Ctx& cref) {
   GView& v = const_cast<GView&>(c.v);
   const int n = v.s->n_tot;
   const int nc = R.nc;
+  if (c.tid == 0) v.s->n_ord = 0;  // the cell sort below overwrites the lane order
   if (nc > 0) {
     const int ncell = nc * nc * nc;
     for (int k = c.tid; k < ncell; k += c.T) v.cfill[k] = 0;
@@ -690,6 +727,52 @@ __device__ H4D_PHASE void build_list_impl(const Ctx& cref) {
   c.sync();
 }
 
+// Lane order of the force pass and the next refresh: atoms by descending number of Verlet
+// row packets, written to sorted[0, n) (free outside the outer build, which invalidates
+// the order), with a bucket histogram in sorted8.  The lanes of a warp then walk rows of
+// about the same length and finish together.  No result depends on this order: every
+// atom's row is summed in its own slot order, whichever lane holds it, and the kinetic
+// sums are exact integers; so positions within a bucket are taken with atomics.
+constexpr int kOrderBuckets = 64;
+#ifndef H4D_LANE_ORDER
+#define H4D_LANE_ORDER 1
+#endif
+__device__ void lane_order(const Ctx& c, int n) {
+  const Eng& e = *c.e;
+  const GView& v = c.v;
+  if (!H4D_LANE_ORDER || n < kOrderBuckets) {  // small replicas: identity order (and sorted8 may be too short)
+    if (c.tid == 0) v.s->n_ord = 0;
+    c.sync();
+    return;
+  }
+  int* hist = reinterpret_cast<int*>(v.sorted8);
+  const int* cnt = e.ncnt + c.r.atom_off;
+  for (int b = c.tid; b < kOrderBuckets; b += c.T) hist[b] = 0;
+  c.sync();
+  for (int i = c.tid; i < n; i += c.T) atomicAdd(&hist[kOrderBuckets - 1 - min((cnt[i] + 3) >> 2, kOrderBuckets - 1)], 1);
+  c.sync();
+  if (c.tid < 32) {  // exclusive prefix over the buckets
+    const int lane = c.tid;
+    const int a = hist[lane], b = hist[lane + 32];
+    int ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int ya = __shfl_up_sync(0xffffffffu, ia, o), yb = __shfl_up_sync(0xffffffffu, ib, o);
+      if (lane >= o) { ia += ya; ib += yb; }
+    }
+    const int tot_a = __shfl_sync(0xffffffffu, ia, 31);
+    hist[lane] = ia - a;
+    hist[lane + 32] = tot_a + ib - b;
+  }
+  c.sync();
+  for (int i = c.tid; i < n; i += c.T) {
+    const int b = kOrderBuckets - 1 - min((cnt[i] + 3) >> 2, kOrderBuckets - 1);
+    v.sorted[atomicAdd(&hist[b], 1)] = (uint16_t)i;
+  }
+  if (c.tid == 0) v.s->n_ord = n;
+  c.sync();
+}
+
 // Verlet rows filtered from the outer rows: one thread per atom streams its outer row
 // (one 8-byte packet load per four candidates) and keeps the candidates inside r_list, in
 // outer-row order, so the Verlet rows are as deterministic as the outer ones.
@@ -715,6 +798,7 @@ __device__ H4D_PHASE void filter_list_impl(const Ctx& cref) {
     uint2 q = (npk > 0) ? pko[i] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
     for (int p = 0; p < npk; ++p) {
       const uint2 qn = (p + 1 < npk) ? pko[(size_t)(p + 1) * ostride + i] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+      if (H4D_PF_FILTER > 0 && p + H4D_PF_FILTER < npk) prefetch_l2(pko + (size_t)(p + H4D_PF_FILTER) * ostride + i);
       const int jj[4] = {(int)(q.x & 0xFFFFu), (int)(q.x >> 16), (int)(q.y & 0xFFFFu), (int)(q.y >> 16)};
       uint4 pj[4];
 #pragma unroll
@@ -738,6 +822,55 @@ __device__ H4D_PHASE void filter_list_impl(const Ctx& cref) {
   }
   if (overflow) atomicOr(&v.s->flag_overflow, 1);
   c.sync();
+  lane_order(c, n);
+}
+
+// One atom's LJ-electrolyte row on this lane (packets p = 0, 1, ... of its share), four
+// slots per packet, pair terms two at a time on the packed FP32x2 pipe.  Padding slots read
+// the sentinel (its infinite altitude puts it beyond every cut-off), and the charge sign of
+// a pair is the parity of i + j (cations even, anions odd): the same values as the generic
+// loop, with neither a branch nor a table load per slot.  POLY selects the polynomial
+// Coulomb form (pair_fr_lj2_poly) over the erfc form (pair_fr_lj2).
+template <bool NEMD, bool POLY>
+__device__ __forceinline__ void lj_row(const Pot& P, const uint4* __restrict__ pos, const uint2* pk, size_t pstride,
+                                       int npk, uint2 q, unsigned capa, int i, const uint4& pi, float scale, float wi,
+                                       bool wnz_i, float gscr, float& fx, float& fy, float& fz) {
+  const unsigned kq_i = __float_as_uint(P.kq[0]) ^ ((unsigned)i << 31);
+  for (int p = 0; p < npk; ++p) {
+    const uint2 qn = (p + 1 < npk) ? pk[(size_t)(p + 1) * pstride] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+    if (H4D_PF_FORCE > 0 && p + H4D_PF_FORCE < npk) prefetch_l2(pk + (size_t)(p + H4D_PF_FORCE) * pstride);
+    const unsigned jw[4] = {q.x & 0xFFFFu, q.x >> 16, q.y & 0xFFFFu, q.y >> 16};
+    uint4 pj[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) pj[u] = pos[min(jw[u], capa)];
+#pragma unroll
+    for (int h = 0; h < 4; h += 2) {  // slots h and h+1 on the packed FP32x2 pipe
+      const float2 dx = __fmul2_rn(make_float2((float)(int)(pj[h].x - pi.x), (float)(int)(pj[h + 1].x - pi.x)), f2(scale));
+      const float2 dy = __fmul2_rn(make_float2((float)(int)(pj[h].y - pi.y), (float)(int)(pj[h + 1].y - pi.y)), f2(scale));
+      const float2 dz = __fmul2_rn(make_float2((float)(int)(pj[h].z - pi.z), (float)(int)(pj[h + 1].z - pi.z)), f2(scale));
+      float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+      const float2 wj = make_float2(wbits(pj[h]), wbits(pj[h + 1]));  // 0, a flyer's altitude, or +inf
+      float2 kqg = make_float2(__uint_as_float(kq_i ^ (jw[h] << 31)), __uint_as_float(kq_i ^ (jw[h + 1] << 31)));
+      if (NEMD) {
+        const float2 dw = __fadd2_rn(f2(wi), make_float2(-wj.x, -wj.y));
+        r2 = __ffma2_rn(dw, dw, r2);
+        // charge prefactor times the screening g of the generic loop (exact when g = 1)
+        kqg.x = (wnz_i != (wj.x != 0.0f)) ? kqg.x * gscr : kqg.x;
+        kqg.y = (wnz_i != (wj.y != 0.0f)) ? kqg.y * gscr : kqg.y;
+      } else {
+        r2 = __ffma2_rn(wj, wj, r2);  // + 0 for every atom, +inf for the sentinel
+      }
+      const float2 fr = POLY ? pair_fr_lj2_poly(P, r2, kqg) : pair_fr_lj2(P, r2, kqg);
+      // the force sums in slot order, as in the generic loop
+      fx = fmaf(-fr.x, dx.x, fx);
+      fy = fmaf(-fr.x, dy.x, fy);
+      fz = fmaf(-fr.x, dz.x, fz);
+      fx = fmaf(-fr.y, dx.y, fx);
+      fy = fmaf(-fr.y, dy.y, fy);
+      fz = fmaf(-fr.y, dz.y, fz);
+    }
+    q = qn;
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -776,15 +909,22 @@ __device__ H4D_PHASE void force_pass_impl(const Ctx& cref, int mode, float w_pre
   const size_t pstride = (size_t)R.cap_atoms << ltpa;
   long long kin = 0;  // m v^2 of this thread's atoms, fixed point (exact, order-free sum)
   int kbad = 0;
+  // atoms in the lane order of the last list pass (rows of similar length share a warp)
+  const bool use_ord = v.s->n_ord == n;
   for (int a0 = 0; a0 < n; a0 += nsub) {
-    const int i = a0 + sub;
-    const bool active = i < n;
+    const int k = a0 + sub;
+    const bool active = k < n;
+    const int i = (use_ord && active) ? (int)v.sorted[k] : k;
     float fx = 0.f, fy = 0.f, fz = 0.f, dwk = 0.f;
     // aqueous: the per-atom force is a sum of hundreds of large, cancelling Coulomb
     // terms, so it is accumulated with Kahan compensation (cx, cy, cz)
     float cx = 0.f, cy = 0.f, cz = 0.f;
     const bool iflyer = NEMD && active && (i == fly0 || i == fly1 || i == fly2);
     if (active) {
+      if ((mode & 1) && lin == 0) {  // the half kick after the row reads this atom's velocity
+        prefetch_l1(e.vhi + R.atom_off + i);
+        prefetch_l1(e.vlo + R.atom_off + i);
+      }
       const uint4 pi = v.pos[i];
       const int ti = type_t<SYS>(i, R.nw3);
       const float wi = NEMD ? wbits(pi) : 0.0f;
@@ -795,46 +935,10 @@ __device__ H4D_PHASE void force_pass_impl(const Ctx& cref, int mode, float w_pre
       const int npk = (nP > lin) ? (nP - lin + tpa - 1) >> ltpa : 0;
       uint2 q = (npk > 0) ? pk[0] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
       if (SYS == H4D_SYS_LJ) {
-        // LJ electrolyte.  Padding slots read the sentinel (its infinite altitude puts it
-        // beyond every cut-off), and the charge sign of a pair is the parity of i + j
-        // (cations even, anions odd): the same values as the generic loop below, with
-        // neither a branch nor a table load per slot.
-        const unsigned capa = (unsigned)R.cap_atoms;
-        const unsigned kq_i = __float_as_uint(P.kq[0]) ^ ((unsigned)i << 31);
-        for (int p = 0; p < npk; ++p) {
-          const uint2 qn = (p + 1 < npk) ? pk[(size_t)(p + 1) * pstride] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
-          const unsigned jw[4] = {q.x & 0xFFFFu, q.x >> 16, q.y & 0xFFFFu, q.y >> 16};
-          uint4 pj[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) pj[u] = v.pos[min(jw[u], capa)];
-#pragma unroll
-          for (int h = 0; h < 4; h += 2) {  // slots h and h+1 on the packed FP32x2 pipe
-            const float2 dx = __fmul2_rn(make_float2((float)(int)(pj[h].x - pi.x), (float)(int)(pj[h + 1].x - pi.x)), f2(scale));
-            const float2 dy = __fmul2_rn(make_float2((float)(int)(pj[h].y - pi.y), (float)(int)(pj[h + 1].y - pi.y)), f2(scale));
-            const float2 dz = __fmul2_rn(make_float2((float)(int)(pj[h].z - pi.z), (float)(int)(pj[h + 1].z - pi.z)), f2(scale));
-            float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-            const float2 wj = make_float2(wbits(pj[h]), wbits(pj[h + 1]));  // 0, a flyer's altitude, or +inf
-            float2 kqg = make_float2(__uint_as_float(kq_i ^ (jw[h] << 31)), __uint_as_float(kq_i ^ (jw[h + 1] << 31)));
-            if (NEMD) {
-              const float2 dw = __fadd2_rn(f2(wi), make_float2(-wj.x, -wj.y));
-              r2 = __ffma2_rn(dw, dw, r2);
-              // charge prefactor times the screening g of the generic loop (exact when g = 1)
-              kqg.x = (wnz_i != (wj.x != 0.0f)) ? kqg.x * gscr : kqg.x;
-              kqg.y = (wnz_i != (wj.y != 0.0f)) ? kqg.y * gscr : kqg.y;
-            } else {
-              r2 = __ffma2_rn(wj, wj, r2);  // + 0 for every atom, +inf for the sentinel
-            }
-            const float2 fr = pair_fr_lj2(P, r2, kqg);
-            // the force sums in slot order, as in the generic loop
-            fx = fmaf(-fr.x, dx.x, fx);
-            fy = fmaf(-fr.x, dy.x, fy);
-            fz = fmaf(-fr.x, dz.x, fz);
-            fx = fmaf(-fr.y, dx.y, fx);
-            fy = fmaf(-fr.y, dy.y, fy);
-            fz = fmaf(-fr.y, dz.y, fz);
-          }
-          q = qn;
-        }
+        if (P.coul_poly)
+          lj_row<NEMD, true>(P, v.pos, pk, pstride, npk, q, (unsigned)R.cap_atoms, i, pi, scale, wi, wnz_i, gscr, fx, fy, fz);
+        else
+          lj_row<NEMD, false>(P, v.pos, pk, pstride, npk, q, (unsigned)R.cap_atoms, i, pi, scale, wi, wnz_i, gscr, fx, fy, fz);
       } else
       for (int p = 0; p < npk; ++p) {
         const uint2 qn = (p + 1 < npk) ? pk[(size_t)(p + 1) * pstride] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
@@ -2451,7 +2555,7 @@ __device__ bool setup_ctx(const Eng& e, char* smem, Ctx& c) {
   c.v = carve(smem + G.smem_off, R->cap_atoms, R->nc, c.T);
   GScal* S = c.v.s;
   if (c.tid == 0) {
-    S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0; S->flag_timeout = 0;
+    S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0; S->flag_timeout = 0; S->n_ord = 0;
     S->n_tot = R->nw3 + e.proto.unit * R->n_pairs;
     S->fly0 = S->fly1 = S->fly2 = S->flyw = -1;
     S->w_cur = 0.f; S->g_scr = 1.f;
@@ -2578,7 +2682,7 @@ __global__ void __launch_bounds__(1024) eval_kernel(const __grid_constant__ Eng 
   c.v = carve(smem + G.smem_off, R->cap_atoms, R->nc, c.T);
   GScal* S = c.v.s;
   if (c.tid == 0) {
-    S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0; S->flag_timeout = 0;
+    S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0; S->flag_timeout = 0; S->n_ord = 0;
     S->n_tot = R->nw3 + e.proto.unit * R->n_pairs;
     S->fly0 = S->fly1 = S->fly2 = S->flyw = -1;
     S->w_cur = wbar;

@@ -34,7 +34,11 @@ struct Pot {
   double inv_m_d[kMaxT];
   float q[kMaxT];       // charges per type (proposal field feature)
   int erfcx_fit;        // alpha rc_coul within the range of the fitted erfcx (aqueous pair term)
-  int pad_fit;
+  // LJ electrolyte: the screened-Coulomb force term -du/dr / r = kq g (r^-3 + C(r^2)), with
+  // C a degree-7 polynomial in r^2 (coefficients cpoly[0..7], lowest first) when coul_poly
+  int coul_poly;
+  float cpoly[8];
+  float lj12, lj6;      // 12 eps4 and 6 eps4 of the LJ electrolyte (one sigma, one epsilon)
 };
 
 struct Proto {
