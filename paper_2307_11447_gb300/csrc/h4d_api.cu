@@ -483,6 +483,7 @@ static int alloc_all(h4d_ctx* c) {
 static void fill_eng(h4d_ctx* c) {
   Eng& e = c->eng;
   fill_pot(c->prm, e.pot, e.proto);
+  e.rows_by_index = 0;
   e.rep = c->d_rep;
   e.groups = c->d_groups;
   e.cta_groups = c->d_cta_groups;
@@ -1447,6 +1448,7 @@ int h4d_neighbor_pairs(double L, int32_t n, const double* x, double r_list, int3
   rc = alloc_all(c);
   if (rc) { h4d_destroy(c); return rc; }
   fill_eng(c);
+  c->eng.rows_by_index = 1;  // rows read back below by atom index
   // atoms beyond n (odd n) are parked far away from every pair: they are dropped below
   std::vector<uint4> pos(R.cap_atoms);
   for (int a = 0; a < n; ++a)

@@ -273,7 +273,7 @@ struct GScal {
   int flag_timeout;            // a bounded iteration (SHAKE, RATTLE, gamma draw) gave up
   int fly2, flyw;              // water exchange: third flying atom, flying water (-1 = none)
   int nw_trial;                // waters in the layout of the running trial
-  int n_ord;                   // atoms in the lane order (sorted[0, n_ord)); 0 = no order
+  int n_ord;                   // atoms of the current Verlet-row layout (sorted[0, n_ord)); 0 = by index
   float w_cur, g_scr, pad2, pad3;
   double alpha_th, dW[3], wprot, wprot_c, red_out;
   double ln_u, ustart, kstart, uend, kend;
@@ -291,7 +291,8 @@ struct GScal {
   double pZ[2];            // softmax normalisers sum_k exp(l_k - max)
   double lnq;              // log proposal factor of the trial
   int cell_c, cell_a;      // grid cells of the exchanged cation and anion
-  int prec_slot, pad_p;    // training-record slot of the trial (-1 = none)
+  int prec_slot;           // training-record slot of the trial (-1 = none)
+  int n_rank;              // atoms ranked for the next Verlet-row layout (0 = none)
 };
 static_assert(sizeof(GScal) <= 1536, "per-group scalars exceed their shared-memory slot");
 
@@ -546,7 +547,7 @@ __device__ H4D_PHASE void build_list_impl(const Ctx& cref) {
   GView& v = const_cast<GView&>(c.v);
   const int n = v.s->n_tot;
   const int nc = R.nc;
-  if (c.tid == 0) v.s->n_ord = 0;  // the cell sort below overwrites the lane order
+  if (c.tid == 0) { v.s->n_ord = 0; v.s->n_rank = 0; }  // the cell sort below overwrites the row layout
   if (nc > 0) {
     const int ncell = nc * nc * nc;
     for (int k = c.tid; k < ncell; k += c.T) v.cfill[k] = 0;
@@ -727,29 +728,35 @@ __device__ H4D_PHASE void build_list_impl(const Ctx& cref) {
   c.sync();
 }
 
-// Lane order of the force pass and the next refresh: atoms by descending number of Verlet
-// row packets, written to sorted[0, n) (free outside the outer build, which invalidates
-// the order), with a bucket histogram in sorted8.  The lanes of a warp then walk rows of
-// about the same length and finish together.  No result depends on this order: every
-// atom's row is summed in its own slot order, whichever lane holds it, and the kinetic
-// sums are exact integers; so positions within a bucket are taken with atomics.
+// Row layout of the Verlet lists.  Atom i's row is stored at position rank[i], and the
+// passes that walk the rows (forces, FP64 energies, pair counts) take positions k in
+// order with atom ord[k], so the lanes of a warp read adjacent packets (coalesced) and
+// hold rows of about the same length (ranks by descending row length: the lanes finish
+// together).  No result depends on the layout: each atom's row is summed in its own slot
+// order, per-atom results are stored by atom, and the kinetic sums are exact integers, so
+// positions within a length bucket are taken with atomics.  rank lives in sorted8 after
+// a 64-bucket histogram, ord in sorted (both free outside the outer build, which
+// invalidates them); replicas below kOrderMin atoms keep rows by atom index.
 constexpr int kOrderBuckets = 64;
+constexpr int kOrderMin = 128;  // 256 + 2n bytes fit in sorted8 (4 bytes per atom slot)
 #ifndef H4D_LANE_ORDER
 #define H4D_LANE_ORDER 1
 #endif
-__device__ void lane_order(const Ctx& c, int n) {
-  const Eng& e = *c.e;
+__device__ __forceinline__ int* order_hist(const GView& v) { return reinterpret_cast<int*>(v.sorted8); }
+__device__ __forceinline__ uint16_t* order_rank(const GView& v) {
+  return reinterpret_cast<uint16_t*>(v.sorted8) + 2 * kOrderBuckets;
+}
+__device__ __forceinline__ int order_bucket(int cnt) { return kOrderBuckets - 1 - min((cnt + 3) >> 2, kOrderBuckets - 1); }
+
+// rank[i] from the row length of atom i: cnt[at[i]] (at = the current rank: positions of
+// the rows just written) or cnt[i] (at = nullptr: counts by atom)
+__device__ void make_rank(const Ctx& c, int n, const int* cnt, bool by_rank) {
   const GView& v = c.v;
-  if (!H4D_LANE_ORDER || n < kOrderBuckets) {  // small replicas: identity order (and sorted8 may be too short)
-    if (c.tid == 0) v.s->n_ord = 0;
-    c.sync();
-    return;
-  }
-  int* hist = reinterpret_cast<int*>(v.sorted8);
-  const int* cnt = e.ncnt + c.r.atom_off;
+  int* hist = order_hist(v);
+  uint16_t* rank = order_rank(v);
   for (int b = c.tid; b < kOrderBuckets; b += c.T) hist[b] = 0;
   c.sync();
-  for (int i = c.tid; i < n; i += c.T) atomicAdd(&hist[kOrderBuckets - 1 - min((cnt[i] + 3) >> 2, kOrderBuckets - 1)], 1);
+  for (int i = c.tid; i < n; i += c.T) atomicAdd(&hist[order_bucket(cnt[by_rank ? (int)rank[i] : i])], 1);
   c.sync();
   if (c.tid < 32) {  // exclusive prefix over the buckets
     const int lane = c.tid;
@@ -765,11 +772,10 @@ __device__ void lane_order(const Ctx& c, int n) {
     hist[lane + 32] = tot_a + ib - b;
   }
   c.sync();
-  for (int i = c.tid; i < n; i += c.T) {
-    const int b = kOrderBuckets - 1 - min((cnt[i] + 3) >> 2, kOrderBuckets - 1);
-    v.sorted[atomicAdd(&hist[b], 1)] = (uint16_t)i;
-  }
-  if (c.tid == 0) v.s->n_ord = n;
+  // the thread that reads rank[i] also rewrites it (same atom-to-thread mapping as above)
+  for (int i = c.tid; i < n; i += c.T)
+    rank[i] = (uint16_t)atomicAdd(&hist[order_bucket(cnt[by_rank ? (int)rank[i] : i])], 1);
+  if (c.tid == 0) v.s->n_rank = n;
   c.sync();
 }
 
@@ -787,7 +793,14 @@ __device__ H4D_PHASE void filter_list_impl(const Ctx& cref) {
   const uint2* pko = out_packets(e, R);
   const size_t ostride = (size_t)R.cap_atoms;
   int overflow = 0;
+  // layout of the rows written here: the ranks of the previous refresh, or after an outer
+  // build ranks by outer-row length (it follows the same local density)
+  const bool ranked = H4D_LANE_ORDER && n >= kOrderMin && !e.rows_by_index;
+  if (ranked && v.s->n_rank != n) make_rank(c, n, e.ncnt_out + R.atom_off, false);
+  const uint16_t* rank = order_rank(v);
   for (int i = c.tid; i < n; i += c.T) {
+    const int pos = ranked ? (int)rank[i] : i;
+    if (ranked) v.sorted[pos] = (uint16_t)i;
     const uint4 pi = v.pos[i];
     const int cnt_out = e.ncnt_out[R.atom_off + i];
     const int npk = (cnt_out + 3) >> 2;
@@ -809,20 +822,23 @@ __device__ H4D_PHASE void filter_list_impl(const Ctx& cref) {
         rb.put_if(ok, jj[u]);
         cnt += ok ? 1 : 0;
         if (rb.n == 4) {
-          if (cnt <= maxn) nbr2[packet_index(e, R, i, (cnt - 1) >> 2, ltpa)] = rb.packet();
+          if (cnt <= maxn) nbr2[packet_index(e, R, pos, (cnt - 1) >> 2, ltpa)] = rb.packet();
           rb.init();
         }
       }
       q = qn;
     }
-    if (rb.n > 0 && cnt <= maxn) nbr2[packet_index(e, R, i, (cnt - 1) >> 2, ltpa)] = rb.packet();
+    if (rb.n > 0 && cnt <= maxn) nbr2[packet_index(e, R, pos, (cnt - 1) >> 2, ltpa)] = rb.packet();
     if (cnt > maxn) { overflow = 1; cnt = maxn & ~3; }
-    e.ncnt[R.atom_off + i] = cnt;
+    e.ncnt[R.atom_off + pos] = cnt;
     e.ref[R.atom_off + i] = pi;
   }
   if (overflow) atomicOr(&v.s->flag_overflow, 1);
   c.sync();
-  lane_order(c, n);
+  if (c.tid == 0) v.s->n_ord = ranked ? n : 0;
+  // ranks for the next refresh from the row lengths just found
+  if (ranked) make_rank(c, n, e.ncnt + R.atom_off, true);
+  else c.sync();
 }
 
 // One atom's LJ-electrolyte row on this lane (packets p = 0, 1, ... of its share), four
@@ -909,7 +925,7 @@ __device__ H4D_PHASE void force_pass_impl(const Ctx& cref, int mode, float w_pre
   const size_t pstride = (size_t)R.cap_atoms << ltpa;
   long long kin = 0;  // m v^2 of this thread's atoms, fixed point (exact, order-free sum)
   int kbad = 0;
-  // atoms in the lane order of the last list pass (rows of similar length share a warp)
+  // row positions k in order, atom ord[k] (the layout of the last list pass)
   const bool use_ord = v.s->n_ord == n;
   for (int a0 = 0; a0 < n; a0 += nsub) {
     const int k = a0 + sub;
@@ -929,8 +945,8 @@ __device__ H4D_PHASE void force_pass_impl(const Ctx& cref, int mode, float w_pre
       const int ti = type_t<SYS>(i, R.nw3);
       const float wi = NEMD ? wbits(pi) : 0.0f;
       const bool wnz_i = wi != 0.0f;
-      const int cnt = e.ncnt[R.atom_off + i];
-      const uint2* pk = packets + ((size_t)i << ltpa) + lin;
+      const int cnt = e.ncnt[R.atom_off + k];
+      const uint2* pk = packets + ((size_t)k << ltpa) + lin;
       const int nP = (cnt + 3) >> 2;  // packets of the row; this lane owns lin, lin+tpa, ...
       const int npk = (nP > lin) ? (nP - lin + tpa - 1) >> ltpa : 0;
       uint2 q = (npk > 0) ? pk[0] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
@@ -989,7 +1005,7 @@ __device__ H4D_PHASE void force_pass_impl(const Ctx& cref, int mode, float w_pre
         const float wp_i = (i == fly1) ? rw * w_prev : w_prev;
         const float go = __expf(-P.kappa_sr * (0.5f * (1.0f + rw) * w_prev));
         for (int s2 = lin; s2 < cnt; s2 += tpa) {
-          const int j = e.nbr[nbr_index(e, R, i, s2, ltpa)];
+          const int j = e.nbr[nbr_index(e, R, k, s2, ltpa)];
           if (j == fly0 || j == fly1 || j == fly2) continue;
           const uint4 pj = v.pos[j];
           const float dx = (float)(int)(pj.x - pi.x) * scale;
@@ -1382,8 +1398,11 @@ __device__ H4D_PHASE double energy64_impl(const Ctx& cref, int ex0, int ex1, int
   const double scale = R.L * 0x1.0p-32;
   const double gscr = exp(-P.dkappa_sr * (double)v.s->w_cur);
   const double rc2max = P.drc2_lj > P.drc2_c ? P.drc2_lj : P.drc2_c;
-  // per-atom Kahan sums over the row (j > i), then a sum over atoms in a fixed order
-  for (int i = c.tid; i < n; i += c.T) {
+  // per-atom Kahan sums over the row (j > i), then a sum over atoms in a fixed order;
+  // rows are taken by position k (atom ord[k])
+  const bool use_ord = v.s->n_ord == n;
+  for (int k = c.tid; k < n; k += c.T) {
+    const int i = use_ord ? (int)v.sorted[k] : k;
     double acc = 0.0, comp = 0.0;
     if (i == ex0 || i == ex1 || i == ex2) {
       e.red[R.atom_off + i] = 0.0;
@@ -1392,9 +1411,9 @@ __device__ H4D_PHASE double energy64_impl(const Ctx& cref, int ex0, int ex1, int
     const uint4 pi = v.pos[i];
     const int ti = type_of(i, R.nw3);
     const double wi = (double)wbits(pi);
-    const int cnt = e.ncnt[R.atom_off + i];
+    const int cnt = e.ncnt[R.atom_off + k];
     for (int s = 0; s < cnt; ++s) {
-      const int j = e.nbr[nbr_index(e, R, i, s, c.ltpa)];
+      const int j = e.nbr[nbr_index(e, R, k, s, c.ltpa)];
       if (j <= i || j == ex0 || j == ex1 || j == ex2) continue;
       const uint4 pj = v.pos[j];
       const double dx = (double)(int)(pj.x - pi.x) * scale;
@@ -2555,7 +2574,7 @@ __device__ bool setup_ctx(const Eng& e, char* smem, Ctx& c) {
   c.v = carve(smem + G.smem_off, R->cap_atoms, R->nc, c.T);
   GScal* S = c.v.s;
   if (c.tid == 0) {
-    S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0; S->flag_timeout = 0; S->n_ord = 0;
+    S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0; S->flag_timeout = 0; S->n_ord = 0; S->n_rank = 0;
     S->n_tot = R->nw3 + e.proto.unit * R->n_pairs;
     S->fly0 = S->fly1 = S->fly2 = S->flyw = -1;
     S->w_cur = 0.f; S->g_scr = 1.f;
@@ -2647,11 +2666,13 @@ __global__ void __launch_bounds__(1024) count_kernel(const __grid_constant__ Eng
   build_list(c);
   unsigned long long cnt = 0;
   const float scale = R->scale;
-  for (int i = c.tid; i < S->n_tot; i += c.T) {
+  const bool use_ord = S->n_ord == S->n_tot;
+  for (int k = c.tid; k < S->n_tot; k += c.T) {
+    const int i = use_ord ? (int)c.v.sorted[k] : k;
     const uint4 pi = c.v.pos[i];
-    const int m = e.ncnt[R->atom_off + i];
+    const int m = e.ncnt[R->atom_off + k];
     for (int s = 0; s < m; ++s) {
-      const int j = e.nbr[nbr_index(e, c.r, i, s, c.ltpa)];
+      const int j = e.nbr[nbr_index(e, c.r, k, s, c.ltpa)];
       if (j <= i) continue;
       const uint4 pj = c.v.pos[j];
       const float dx = (float)(int)(pj.x - pi.x) * scale;
@@ -2682,7 +2703,7 @@ __global__ void __launch_bounds__(1024) eval_kernel(const __grid_constant__ Eng 
   c.v = carve(smem + G.smem_off, R->cap_atoms, R->nc, c.T);
   GScal* S = c.v.s;
   if (c.tid == 0) {
-    S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0; S->flag_timeout = 0; S->n_ord = 0;
+    S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0; S->flag_timeout = 0; S->n_ord = 0; S->n_rank = 0;
     S->n_tot = R->nw3 + e.proto.unit * R->n_pairs;
     S->fly0 = S->fly1 = S->fly2 = S->flyw = -1;
     S->w_cur = wbar;

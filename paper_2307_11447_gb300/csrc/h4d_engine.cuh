@@ -140,6 +140,8 @@ struct Eng {
   int max_nbr;
   int max_out;
   unsigned long long seed;
+  int rows_by_index;  // 1: Verlet rows stored by atom index (the neighbour-pair export)
+  int pad_e;
 };
 
 // shared-memory bytes a group needs for a replica
