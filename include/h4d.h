@@ -275,6 +275,17 @@ int h4d_set_water_state(h4d_ctx* ctx, int32_t replica, int32_t n_water, int32_t 
                         const double* host_x, const double* host_v);
 int32_t h4d_num_replicas(h4d_ctx* ctx);
 
+/* ---- screened-Coulomb force term of the LJ electrolyte (Eqs. 9-11, host only) ----
+ * The force pass of the LJ electrolyte evaluates -du/dr / r of K q_i q_j erfc(alpha r)/r
+ * as K q_i q_j (r^-3 + C(r^2)), C(s) = alpha^3 H(alpha^2 s) with
+ * H(v) = (erfc(x) + 2x/sqrt(pi) e^{-v} - 1)/x^3 (x^2 = v), an entire function of v.  This
+ * returns the degree-7 interpolant of C in s = r^2 that the engine uses for this alpha and
+ * Coulomb cut-off (coef[0..7], lowest power first; 8 floats written by the callee) and
+ * *used = 1, or zeros and *used = 0 when alpha rc_coul > 1.3 (the cancellation of r^-3 + C
+ * at the cut-off would cost accuracy; the engine then keeps the erfc form).  No GPU
+ * needed; H4D_EINVAL for NULL pointers. */
+int h4d_coulomb_poly(double alpha, double rc_coul, float* coef, int32_t* used);
+
 /* ---- device facts (no paper counterpart; measurement support) ---- */
 /* SM count of the current device, and the compute capability (major*10 + minor, 103 for
  * sm_103a) and PTX version the engine kernel of this build was compiled for, from the

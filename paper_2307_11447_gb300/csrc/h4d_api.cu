@@ -256,10 +256,10 @@ static double coul_H(double v) {
   return -4.0 / std::sqrt(M_PI) * s;
 }
 
-static void fit_coul_poly(const h4d_params& p, Pot& P) {
-  P.coul_poly = 0;
-  const double a = p.alpha, rc = p.rc_coul;
-  if (p.system != H4D_SYS_LJ || !(rc > 0) || !(a >= 0) || a * rc > 1.3) return;
+// fills cp[0..7] and returns 1 when the polynomial form applies to (alpha, rc), else 0
+static int fit_coul_poly(double a, double rc, float* cp) {
+  for (int j = 0; j < 8; ++j) cp[j] = 0.0f;
+  if (!(rc > 0) || !(a >= 0) || a * rc > 1.3) return 0;
   const int D = 8;
   const double S = rc * rc;
   double A[D][D + 1];
@@ -292,9 +292,9 @@ static void fit_coul_poly(const h4d_params& p, Pot& P) {
     const double exact = 1.0 / (r * r * r) + a * a * a * coul_H(a * a * s);
     worst = std::max(worst, std::fabs(poly - a * a * a * coul_H(a * a * s)) / std::fabs(exact));
   }
-  if (!(worst < 2e-7)) return;
-  for (int j = 0; j < D; ++j) P.cpoly[j] = (float)c[j];
-  P.coul_poly = 1;
+  if (!(worst < 2e-7)) return 0;
+  for (int j = 0; j < D; ++j) cp[j] = (float)c[j];
+  return 1;
 }
 
 static void fill_pot(const h4d_params& p, Pot& P, Proto& pr) {
@@ -349,7 +349,7 @@ static void fill_pot(const h4d_params& p, Pot& P, Proto& pr) {
   P.d_hh2 = p.d_hh * p.d_hh;
   for (int t = 0; t < 4; ++t) P.q[t] = (t < p.ntypes) ? (float)p.q[t] : 0.f;
   P.erfcx_fit = p.alpha * p.rc_coul <= 3.2 ? 1 : 0;  // the fit's range (fit_erfcx.py)
-  fit_coul_poly(p, P);
+  P.coul_poly = (p.system == H4D_SYS_LJ) ? fit_coul_poly(p.alpha, p.rc_coul, P.cpoly) : 0;
   P.lj12 = 12.0f * P.eps4[0];
   P.lj6 = 6.0f * P.eps4[0];
   std::memset(&pr, 0, sizeof(pr));
@@ -1168,6 +1168,12 @@ int h4d_count_pairs(h4d_ctx* c, int64_t* n) {
   CK(cudaStreamSynchronize(c->stream));
   *n = (int64_t)v;
   return check_errors(c);
+}
+
+int h4d_coulomb_poly(double alpha, double rc_coul, float* coef, int32_t* used) {
+  if (!coef || !used) return H4D_EINVAL;
+  *used = fit_coul_poly(alpha, rc_coul, coef);
+  return H4D_OK;
 }
 
 int h4d_device_info(int32_t* sm_count, int32_t* binary_version, int32_t* ptx_version) {

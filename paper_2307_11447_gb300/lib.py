@@ -191,6 +191,7 @@ def lib():
             "h4d_proposal_logits": ([vp, i32, vp, vp, i64, ctypes.POINTER(i64)], i32),
             "h4d_train_proposal": ([vp, i64, i32, d, d, ctypes.c_uint64, pd], i32),
             "h4d_proposal_grad": ([pd, i64, vp, vp, pd, pd], i32),
+            "h4d_coulomb_poly": ([d, d, vp, pi32], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -467,6 +468,15 @@ def h4d_proposal_grad(w, feat, tgt):
     _ck(lib().h4d_proposal_grad(_pd(w), f.shape[0], f.ctypes.data, t.ctypes.data, ctypes.byref(loss), _pd(g)),
         "h4d_proposal_grad")
     return loss.value, g
+
+
+def h4d_coulomb_poly(alpha, rc_coul):
+    """(coefficients of C(r^2), lowest first, float32; True when the engine uses the form)"""
+    c = np.zeros(8, np.float32)
+    used = ctypes.c_int32()
+    _ck(lib().h4d_coulomb_poly(ctypes.c_double(alpha), ctypes.c_double(rc_coul), c.ctypes.data,
+                               ctypes.byref(used)), "h4d_coulomb_poly")
+    return c, bool(used.value)
 
 
 def h4d_device_info():
