@@ -169,6 +169,8 @@ struct h4d_ctx {
   uint16_t* d_nbr_out = nullptr;
   int* d_ncnt_out = nullptr;
   uint4* d_ref_out = nullptr;
+  uint16_t* d_lrank = nullptr;  // Verlet-row layout: rank of each atom, atom at each position
+  uint16_t* d_lord = nullptr;
   double* d_red = nullptr;
   h4d_record* d_rec = nullptr;
   double* d_scratch = nullptr;
@@ -461,6 +463,8 @@ static int alloc_all(h4d_ctx* c) {
   CK(cudaMalloc(&c->d_nbr_out, na * (size_t)c->max_out * sizeof(uint16_t)));
   CK(cudaMalloc(&c->d_ncnt_out, na * sizeof(int)));
   CK(cudaMalloc(&c->d_ref_out, na * sizeof(uint4)));
+  CK(cudaMalloc(&c->d_lrank, na * sizeof(uint16_t)));
+  CK(cudaMalloc(&c->d_lord, na * sizeof(uint16_t)));
   CK(cudaMalloc(&c->d_red, na * sizeof(double)));
   CK(cudaMemset(c->d_ncnt_out, 0, na * sizeof(int)));
   CK(cudaMemset(c->d_pos, 0, na * sizeof(uint4)));
@@ -500,6 +504,8 @@ static void fill_eng(h4d_ctx* c) {
   e.nbr_out = c->d_nbr_out;
   e.ncnt_out = c->d_ncnt_out;
   e.ref_out = c->d_ref_out;
+  e.lrank = c->d_lrank;
+  e.lord = c->d_lord;
   e.rec = c->d_rec;
   e.red = c->d_red;
   e.max_nbr = c->max_nbr;
@@ -851,7 +857,8 @@ void h4d_destroy(h4d_ctx* c) {
   if (!c) return;
   void* ptrs[] = {c->d_rep, c->d_groups, c->d_cta_groups, c->d_pos, c->d_vhi, c->d_vlo, c->d_force,
                   c->d_pos_save, c->d_vhi_save, c->d_vlo_save, c->d_ref, c->d_nbr, c->d_ncnt, c->d_rec,
-                  c->d_scratch, c->d_count, c->d_nbr_out, c->d_ncnt_out, c->d_ref_out, c->d_red};
+                  c->d_scratch, c->d_count, c->d_nbr_out, c->d_ncnt_out, c->d_ref_out, c->d_red,
+                  c->d_lrank, c->d_lord};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   prop_free(c->prop);

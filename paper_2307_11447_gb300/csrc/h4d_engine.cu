@@ -292,7 +292,9 @@ struct GScal {
   double lnq;              // log proposal factor of the trial
   int cell_c, cell_a;      // grid cells of the exchanged cation and anion
   int prec_slot;           // training-record slot of the trial (-1 = none)
-  int n_rank;              // atoms ranked for the next Verlet-row layout (0 = none)
+  int n_rank;              // atoms ranked in lrank for the next outer build (0 = none)
+  int n_lay;               // atoms of the outer-row layout in lord (0 = rows by index)
+  int pad_l;
 };
 static_assert(sizeof(GScal) <= 1536, "per-group scalars exceed their shared-memory slot");
 
@@ -512,6 +514,13 @@ __device__ __forceinline__ bool excluded_pair(int i, int j, int nw3) {
   return i < nw3 && j < nw3 && (i / 3) == (j / 3);
 }
 
+// Verlet-row layout by row length (see next_rank): 64 length buckets; replicas of fewer
+// atoms keep rows by index (the bucket histogram uses sorted8, 4 bytes per atom slot)
+constexpr int kOrderBuckets = 64;
+constexpr int kOrderMin = 128;
+#ifndef H4D_LANE_ORDER
+#define H4D_LANE_ORDER 1
+#endif
 __device__ H4D_PHASE void build_list_impl(const Ctx& cref);
 __device__ H4D_PHASE void filter_list_impl(const Ctx& cref);
 // full build: outer rows from the cell grid, then the Verlet rows filtered from them
@@ -547,7 +556,9 @@ __device__ H4D_PHASE void build_list_impl(const Ctx& cref) {
   GView& v = const_cast<GView&>(c.v);
   const int n = v.s->n_tot;
   const int nc = R.nc;
-  if (c.tid == 0) { v.s->n_ord = 0; v.s->n_rank = 0; }  // the cell sort below overwrites the row layout
+  // rows of home atom i go to position lrank[i] when the last filter ranked these n atoms
+  const bool use_rank = H4D_LANE_ORDER && e.lrank && !e.rows_by_index && n >= kOrderMin && v.s->n_rank == n;
+  if (c.tid == 0) v.s->n_ord = 0;  // the cell sort below overwrites the shared copy of lord
   if (nc > 0) {
     const int ncell = nc * nc * nc;
     for (int k = c.tid; k < ncell; k += c.T) v.cfill[k] = 0;
@@ -653,6 +664,7 @@ __device__ H4D_PHASE void build_list_impl(const Ctx& cref) {
       const int ih = (hq < h1) ? ((nc > 0) ? (int)v.sorted[hq] : hq) : (int)kNoAtom;
       const bool act = ih != (int)kNoAtom;
       const int i = act ? ih : 0;
+      const int pos = use_rank ? (int)e.lrank[R.atom_off + i] : i;  // where this atom's rows go
       const uint4 pi = v.pos[i];
       const unsigned pi8 = pack8(pi);
       int cnt = 0;
@@ -704,7 +716,7 @@ __device__ H4D_PHASE void build_list_impl(const Ctx& cref) {
             cnt += ok ? 1 : 0;
             if (rb.n == 4) {
               if (cnt <= maxo)
-                reinterpret_cast<uint2*>(e.nbr_out)[out_packet_index(e, R, i, (cnt - 1) >> 2)] = rb.packet();
+                reinterpret_cast<uint2*>(e.nbr_out)[out_packet_index(e, R, pos, (cnt - 1) >> 2)] = rb.packet();
               rb.init();
             }
           }
@@ -712,10 +724,11 @@ __device__ H4D_PHASE void build_list_impl(const Ctx& cref) {
       }
       if (act) {
         if (rb.n > 0 && cnt <= maxo)  // last partial packet, padded with kNoAtom
-          reinterpret_cast<uint2*>(e.nbr_out)[out_packet_index(e, R, i, (cnt - 1) >> 2)] = rb.packet();
+          reinterpret_cast<uint2*>(e.nbr_out)[out_packet_index(e, R, pos, (cnt - 1) >> 2)] = rb.packet();
         if (cnt > maxo) { overflow = 1; cnt = maxo & ~3; }
-        e.ncnt_out[R.atom_off + i] = cnt;
+        e.ncnt_out[R.atom_off + pos] = cnt;
         e.ref_out[R.atom_off + i] = pi;
+        if (use_rank) e.lord[R.atom_off + pos] = (uint16_t)i;
       }
     }
   }
@@ -724,39 +737,34 @@ __device__ H4D_PHASE void build_list_impl(const Ctx& cref) {
   if (c.tid == 0) {
     c.R->builds++;
     v.s->flag_rebuild = 0;
+    v.s->n_lay = use_rank ? n : 0;
   }
   c.sync();
 }
 
-// Row layout of the Verlet lists.  Atom i's row is stored at position rank[i], and the
-// passes that walk the rows (forces, FP64 energies, pair counts) take positions k in
-// order with atom ord[k], so the lanes of a warp read adjacent packets (coalesced) and
-// hold rows of about the same length (ranks by descending row length: the lanes finish
-// together).  No result depends on the layout: each atom's row is summed in its own slot
-// order, per-atom results are stored by atom, and the kinetic sums are exact integers, so
-// positions within a length bucket are taken with atomics.  rank lives in sorted8 after
-// a 64-bucket histogram, ord in sorted (both free outside the outer build, which
-// invalidates them); replicas below kOrderMin atoms keep rows by atom index.
-constexpr int kOrderBuckets = 64;
-constexpr int kOrderMin = 128;  // 256 + 2n bytes fit in sorted8 (4 bytes per atom slot)
-#ifndef H4D_LANE_ORDER
-#define H4D_LANE_ORDER 1
-#endif
-__device__ __forceinline__ int* order_hist(const GView& v) { return reinterpret_cast<int*>(v.sorted8); }
-__device__ __forceinline__ uint16_t* order_rank(const GView& v) {
-  return reinterpret_cast<uint16_t*>(v.sorted8) + 2 * kOrderBuckets;
-}
+// Row layout.  An outer build stores atom i's outer row at position lrank[i] (ranks by
+// descending Verlet-row length at the last filter) and records lord[k], the atom at
+// position k; the filter reads outer rows and writes Verlet rows at the same positions, and
+// the passes that walk the Verlet rows (forces, FP64 energies, pair counts) take positions
+// k in order with atom ord[k] (lord copied to shared memory).  The lanes of a warp then
+// read adjacent packets (coalesced) and hold rows of about the same length.  No result
+// depends on the layout: each row is summed in its own slot order, per-atom results are
+// stored by atom, and the kinetic sums are exact integers, so positions within a length
+// bucket are taken with atomics.  The ranks live in global memory (the cell sort of the
+// outer build reuses the shared buffers); replicas below kOrderMin atoms, callers without
+// rank arrays and the neighbour-pair export keep rows by atom index.
 __device__ __forceinline__ int order_bucket(int cnt) { return kOrderBuckets - 1 - min((cnt + 3) >> 2, kOrderBuckets - 1); }
 
-// rank[i] from the row length of atom i: cnt[at[i]] (at = the current rank: positions of
-// the rows just written) or cnt[i] (at = nullptr: counts by atom)
-__device__ void make_rank(const Ctx& c, int n, const int* cnt, bool by_rank) {
+// lrank for the next outer build from the Verlet-row lengths at positions k (atom lord[k]
+// when lay, else k); the histogram uses sorted8, free outside the outer build
+__device__ void next_rank(const Ctx& c, int n, bool lay) {
+  const Eng& e = *c.e;
   const GView& v = c.v;
-  int* hist = order_hist(v);
-  uint16_t* rank = order_rank(v);
+  const int off = c.r.atom_off;
+  int* hist = reinterpret_cast<int*>(v.sorted8);
   for (int b = c.tid; b < kOrderBuckets; b += c.T) hist[b] = 0;
   c.sync();
-  for (int i = c.tid; i < n; i += c.T) atomicAdd(&hist[order_bucket(cnt[by_rank ? (int)rank[i] : i])], 1);
+  for (int k = c.tid; k < n; k += c.T) atomicAdd(&hist[order_bucket(e.ncnt[off + k])], 1);
   c.sync();
   if (c.tid < 32) {  // exclusive prefix over the buckets
     const int lane = c.tid;
@@ -772,9 +780,10 @@ __device__ void make_rank(const Ctx& c, int n, const int* cnt, bool by_rank) {
     hist[lane + 32] = tot_a + ib - b;
   }
   c.sync();
-  // the thread that reads rank[i] also rewrites it (same atom-to-thread mapping as above)
-  for (int i = c.tid; i < n; i += c.T)
-    rank[i] = (uint16_t)atomicAdd(&hist[order_bucket(cnt[by_rank ? (int)rank[i] : i])], 1);
+  for (int k = c.tid; k < n; k += c.T) {
+    const int i = lay ? (int)e.lord[off + k] : k;
+    e.lrank[off + i] = (uint16_t)atomicAdd(&hist[order_bucket(e.ncnt[off + k])], 1);
+  }
   if (c.tid == 0) v.s->n_rank = n;
   c.sync();
 }
@@ -793,25 +802,24 @@ __device__ H4D_PHASE void filter_list_impl(const Ctx& cref) {
   const uint2* pko = out_packets(e, R);
   const size_t ostride = (size_t)R.cap_atoms;
   int overflow = 0;
-  // layout of the rows written here: the ranks of the previous refresh, or after an outer
-  // build ranks by outer-row length (it follows the same local density)
-  const bool ranked = H4D_LANE_ORDER && n >= kOrderMin && !e.rows_by_index;
-  if (ranked && v.s->n_rank != n) make_rank(c, n, e.ncnt_out + R.atom_off, false);
-  const uint16_t* rank = order_rank(v);
-  for (int i = c.tid; i < n; i += c.T) {
-    const int pos = ranked ? (int)rank[i] : i;
-    if (ranked) v.sorted[pos] = (uint16_t)i;
+  // positions k of the outer rows' layout (atom lord[k], or k when rows are by index): the
+  // outer rows are read and the Verlet rows written at the same position, both coalesced
+  const bool lay = v.s->n_lay == n;
+  for (int k = c.tid; k < n; k += c.T) {
+    const int i = lay ? (int)e.lord[R.atom_off + k] : k;
+    if (lay) v.sorted[k] = (uint16_t)i;
+    const int pos = k;
     const uint4 pi = v.pos[i];
-    const int cnt_out = e.ncnt_out[R.atom_off + i];
+    const int cnt_out = e.ncnt_out[R.atom_off + pos];
     const int npk = (cnt_out + 3) >> 2;
     int cnt = 0;
     RowBuf rb;
     rb.init();
     uint2* nbr2 = reinterpret_cast<uint2*>(e.nbr);
-    uint2 q = (npk > 0) ? pko[i] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+    uint2 q = (npk > 0) ? pko[pos] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
     for (int p = 0; p < npk; ++p) {
-      const uint2 qn = (p + 1 < npk) ? pko[(size_t)(p + 1) * ostride + i] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
-      if (H4D_PF_FILTER > 0 && p + H4D_PF_FILTER < npk) prefetch_l2(pko + (size_t)(p + H4D_PF_FILTER) * ostride + i);
+      const uint2 qn = (p + 1 < npk) ? pko[(size_t)(p + 1) * ostride + pos] : make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+      if (H4D_PF_FILTER > 0 && p + H4D_PF_FILTER < npk) prefetch_l2(pko + (size_t)(p + H4D_PF_FILTER) * ostride + pos);
       const int jj[4] = {(int)(q.x & 0xFFFFu), (int)(q.x >> 16), (int)(q.y & 0xFFFFu), (int)(q.y >> 16)};
       uint4 pj[4];
 #pragma unroll
@@ -835,9 +843,9 @@ __device__ H4D_PHASE void filter_list_impl(const Ctx& cref) {
   }
   if (overflow) atomicOr(&v.s->flag_overflow, 1);
   c.sync();
-  if (c.tid == 0) v.s->n_ord = ranked ? n : 0;
-  // ranks for the next refresh from the row lengths just found
-  if (ranked) make_rank(c, n, e.ncnt + R.atom_off, true);
+  if (c.tid == 0) v.s->n_ord = lay ? n : 0;
+  // ranks for the next outer build from the row lengths just found
+  if (H4D_LANE_ORDER && e.lrank && !e.rows_by_index && n >= kOrderMin) next_rank(c, n, lay);
   else c.sync();
 }
 
@@ -2574,7 +2582,7 @@ __device__ bool setup_ctx(const Eng& e, char* smem, Ctx& c) {
   c.v = carve(smem + G.smem_off, R->cap_atoms, R->nc, c.T);
   GScal* S = c.v.s;
   if (c.tid == 0) {
-    S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0; S->flag_timeout = 0; S->n_ord = 0; S->n_rank = 0;
+    S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0; S->flag_timeout = 0; S->n_ord = 0; S->n_rank = 0; S->n_lay = 0;
     S->n_tot = R->nw3 + e.proto.unit * R->n_pairs;
     S->fly0 = S->fly1 = S->fly2 = S->flyw = -1;
     S->w_cur = 0.f; S->g_scr = 1.f;
@@ -2703,7 +2711,7 @@ __global__ void __launch_bounds__(1024) eval_kernel(const __grid_constant__ Eng 
   c.v = carve(smem + G.smem_off, R->cap_atoms, R->nc, c.T);
   GScal* S = c.v.s;
   if (c.tid == 0) {
-    S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0; S->flag_timeout = 0; S->n_ord = 0; S->n_rank = 0;
+    S->flag_rebuild = 1; S->flag_overflow = 0; S->flag_nan = 0; S->flag_timeout = 0; S->n_ord = 0; S->n_rank = 0; S->n_lay = 0;
     S->n_tot = R->nw3 + e.proto.unit * R->n_pairs;
     S->fly0 = S->fly1 = S->fly2 = S->flyw = -1;
     S->w_cur = wbar;

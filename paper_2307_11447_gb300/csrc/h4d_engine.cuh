@@ -142,6 +142,11 @@ struct Eng {
   unsigned long long seed;
   int rows_by_index;  // 1: Verlet rows stored by atom index (the neighbour-pair export)
   int pad_e;
+  // row layout (per replica, at atom_off): lrank[i] = row position of atom i at the next
+  // outer build (from the row lengths of the last filter), lord[k] = atom whose rows are at
+  // position k since the last outer build; NULL where the caller keeps rows by index
+  uint16_t* lrank;
+  uint16_t* lord;
 };
 
 // shared-memory bytes a group needs for a replica
